@@ -1,0 +1,236 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test fixes the oracle to something other than itself: the byte strings
+printed in Table 1 and Fig. 1, closed forms that follow from the format's
+definition (Sec. 1), exhaustive enumeration on small ranges, numpy's own
+cumulative sum for the differential rule, and the special cases Algorithm 1
+(Sec. 2) fixes for the fifth byte.  A plausible slip in the oracle -- reversed
+byte order, inverted continuation bit, a dropped 7-bit group, a wrong shift,
+an off-by-one in the running sum -- fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from paper_1503_07387_gb300 import inputs
+
+MASK32 = (1 << 32) - 1
+
+
+def _hex(bs):
+    return bytes(int(x, 16) for x in bs)
+
+
+# ------------------------------------------------------------ printed values --
+
+def test_table1_encodings():
+    """Table 1 (Sec. 1): the printed VByte forms of 1, 2, 4, 128, ..., 32768."""
+    rows = read_golden("table1.txt")
+    assert len(rows) == 8
+    for row in rows:
+        v, expect = int(row[0]), _hex(row[1:])
+        assert oracle.encode_one(v) == expect
+        assert oracle.encode([v]).tobytes() == expect
+        assert oracle.decode(expect).tolist() == [v]
+
+
+def test_table1_as_one_stream():
+    rows = read_golden("table1.txt")
+    vals = [int(r[0]) for r in rows]
+    stream = b"".join(_hex(r[1:]) for r in rows)
+    assert oracle.encode(vals).tobytes() == stream
+    assert oracle.decode(stream).tolist() == vals
+
+
+def test_fig1_example():
+    """Fig. 1 (Sec. 4): 80 01 82 03 10 20 -> 128, 386, 16, 32."""
+    rows = {r[0]: r[1:] for r in read_golden("fig1.txt")}
+    data = _hex(rows["bytes"])
+    vals = [int(x) for x in rows["values"]]
+    assert oracle.decode(data).tolist() == vals
+    assert oracle.encode(vals).tobytes() == data
+    assert oracle.validate(data, 4) == 0
+
+
+# ------------------------------------------------------------- closed forms --
+
+def _length_closed_form(v):
+    """Sec. 1: [0,2^7) -> 1 byte, [2^7,2^14) -> 2 bytes, and so on."""
+    v = np.asarray(v, dtype=np.uint64)
+    return (1 + (v >= 1 << 7).astype(int) + (v >= 1 << 14) + (v >= 1 << 21)
+            + (v >= 1 << 28))
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
+def test_powers_of_128(k):
+    """2^(7k) is k continuation bytes 0x80 followed by 0x01."""
+    v = 1 << (7 * k)
+    assert oracle.encode_one(v) == b"\x80" * k + b"\x01"
+    assert oracle.decode(b"\x80" * k + b"\x01").tolist() == [v]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_powers_of_128_minus_one(k):
+    """2^(7k) - 1 is k-1 bytes 0xFF followed by 0x7F."""
+    v = (1 << (7 * k)) - 1
+    assert oracle.encode_one(v) == b"\xff" * (k - 1) + b"\x7f"
+    assert oracle.decode(b"\xff" * (k - 1) + b"\x7f").tolist() == [v]
+
+
+def test_max_uint32():
+    """2^32 - 1: four full groups then the top four bits, 0x0F."""
+    assert oracle.encode_one(MASK32) == b"\xff\xff\xff\xff\x0f"
+    assert oracle.decode(b"\xff\xff\xff\xff\x0f").tolist() == [MASK32]
+
+
+def test_brute_force_21_bits():
+    """Every v in [0, 2^21): length rule, continuation bits, and the round trip."""
+    v = np.arange(1 << 21, dtype=np.uint32)
+    enc = oracle.encode(v)
+    lens = _length_closed_form(v)
+    assert enc.size == int(lens.sum())
+    # continuation bit set on exactly the non-final byte of each integer
+    ends = np.cumsum(lens) - 1
+    msb = (enc >> 7).astype(bool)
+    assert not msb[ends].any()
+    assert msb.sum() == enc.size - v.size
+    dec = oracle.decode(enc)
+    assert np.array_equal(dec, v)
+
+
+@pytest.mark.parametrize("lo,hi", [(1 << 21, 1 << 28), (1 << 28, 1 << 32)])
+def test_random_round_trip_long_codes(lo, hi):
+    rng = np.random.default_rng(7)
+    v = rng.integers(lo, hi, size=200_000, dtype=np.uint64).astype(np.uint32)
+    v[:4] = [lo, lo + 1, hi - 2, hi - 1]
+    enc = oracle.encode(v)
+    assert enc.size == int(_length_closed_form(v).sum())
+    assert np.array_equal(oracle.decode(enc), v)
+
+
+def test_group_sum_definition_small():
+    """For a few thousand values, the bytes satisfy v = sum (b_k mod 128) 2^(7k)
+    with Python integers, independently of Algorithm 1's loop structure."""
+    rng = np.random.default_rng(3)
+    for v in rng.integers(0, 1 << 32, size=3000, dtype=np.uint64).tolist():
+        bs = oracle.encode_one(v)
+        assert sum((b & 127) << (7 * k) for k, b in enumerate(bs)) == v
+
+
+def test_round_trip_all_code_lengths_mixed():
+    v = inputs.uniform_bits(200_000, seed=11)
+    assert np.array_equal(oracle.decode(oracle.encode(v)), v)
+
+
+# ------------------------------------------------- Algorithm 1 special cases --
+
+def test_fifth_byte_keeps_low_four_bits():
+    """Algorithm 1 appends c + b * 2^28 into a 32-bit array: only b's low four
+    bits survive, and the fifth byte's high bit is never tested."""
+    assert oracle.decode(b"\x80\x80\x80\x80\x7f").tolist() == [0xF0000000]
+    assert oracle.decode(b"\x81\x82\x83\x84\x10").tolist() == [
+        (1 + (2 << 7) + (3 << 14) + (4 << 21)) & MASK32]
+    # fifth byte with the high bit set: still consumed as the last byte
+    assert oracle.decode(b"\x80\x80\x80\x80\xff\x05").tolist() == [0xF0000000, 5]
+    assert oracle.validate(b"\x80\x80\x80\x80\xff\x05", 2) & oracle.ERR_MALFORMED_LONG
+
+
+def test_overlong_zero():
+    """Non-canonical 0x80 0x00 decodes to 0 under Algorithm 1."""
+    assert oracle.decode(b"\x80\x00").tolist() == [0]
+
+
+def test_truncated_tail_drops_partial_integer():
+    assert oracle.decode(b"\x05\x80").tolist() == [5]
+    assert oracle.validate(b"\x05\x80", 1) == oracle.ERR_TRUNCATED
+    assert oracle.decode(b"").tolist() == []
+    assert oracle.validate(b"", 0) == 0
+
+
+def test_validation_contract():
+    assert oracle.validate(b"\x01\x02", 2) == 0
+    assert oracle.validate(b"\x01\x02", 3) == oracle.ERR_COUNT_MISMATCH
+    # four continuation bytes are fine, five are malformed
+    assert oracle.validate(b"\x80\x80\x80\x80\x01", 1) == 0
+    assert oracle.validate(b"\x80\x80\x80\x80\x80\x01", 1) & oracle.ERR_MALFORMED_LONG
+    assert oracle.validate(b"\x01\x80\x80\x80\x80\x80", 1) == (
+        oracle.ERR_MALFORMED_LONG | oracle.ERR_TRUNCATED)
+
+
+# ------------------------------------------------------ differential coding --
+
+def test_delta_equals_numpy_cumsum():
+    """Sec. 1/2: decoding gaps with the running value equals the inclusive
+    cumulative sum modulo 2^32 (numpy's cumsum in uint64, then wrapped)."""
+    g = inputs.uniform_gaps(300_000, lo=0, hi=5_000_000, seed=5)
+    ref = (np.cumsum(g.astype(np.uint64)) & MASK32).astype(np.uint32)
+    assert np.array_equal(oracle.decode_delta(oracle.encode(g)), ref)
+    assert int(g.astype(np.uint64).sum()) > MASK32  # the running sum really wraps
+
+
+def test_delta_prev_seed():
+    g = np.array([5, 1, 300, 0, 2**32 - 1], dtype=np.uint32)
+    out = oracle.decode_delta(oracle.encode(g), prev=1000)
+    ref = (1000 + np.cumsum(g.astype(np.uint64))) & MASK32
+    assert out.tolist() == ref.tolist()
+
+
+def test_fig1_as_gaps():
+    rows = {r[0]: r[1:] for r in read_golden("fig1.txt")}
+    assert oracle.decode_delta(_hex(rows["bytes"])).tolist() == [128, 514, 530, 562]
+
+
+def test_encode_delta_round_trip_sorted_ids():
+    ids, vo = inputs.posting_lists(num_lists=20, universe=1 << 30, cap=20_000, seed=2)
+    x = ids[int(vo[0]):int(vo[1])]
+    enc = oracle.encode_delta(x)
+    gaps = np.diff(x.astype(np.int64), prepend=0).astype(np.uint32)
+    assert np.array_equal(enc, oracle.encode(gaps))
+    assert np.array_equal(oracle.decode_delta(enc), x)
+
+
+def test_delta_wraps_modulo_2_32():
+    x = np.array([2**32 - 10, 5, 7], dtype=np.uint32)  # not increasing: gaps wrap
+    enc = oracle.encode_delta(x)
+    assert np.array_equal(oracle.decode_delta(enc), x)
+
+
+# ------------------------------------------------------------------ batched --
+
+def test_batched_matches_per_list_and_concatenation():
+    ids, vo = inputs.length_class_lists(300, max_class=10, seed=4)
+    enc, bo = oracle.encode_batched(ids, vo, delta=True)
+    out, st = oracle.decode_batched(enc, bo, vo, delta=True)
+    assert st == 0
+    assert np.array_equal(out, ids)
+    for j in range(0, 300, 37):
+        seg = enc[int(bo[j]):int(bo[j + 1])]
+        assert np.array_equal(oracle.decode_delta(seg), ids[int(vo[j]):int(vo[j + 1])])
+    # plain mode: decoding the concatenation as one stream is the same thing
+    penc, pbo = oracle.encode_batched(ids, vo, delta=False)
+    pout, pst = oracle.decode_batched(penc, pbo, vo, delta=False)
+    assert pst == 0
+    assert np.array_equal(pout, oracle.decode(penc))
+
+
+def test_batched_prev_and_threads():
+    ids, vo = inputs.length_class_lists(64, max_class=8, seed=9)
+    prev = np.arange(64, dtype=np.uint32) * 7
+    shifted = ids.copy()
+    for j in range(64):
+        shifted[int(vo[j]):int(vo[j + 1])] += prev[j]
+    enc, bo = oracle.encode_batched(shifted, vo, delta=True, prev=prev)
+    out1, st = oracle.decode_batched(enc, bo, vo, delta=True, prev=prev)
+    out4, _ = oracle.decode_batched(enc, bo, vo, delta=True, prev=prev, threads=4)
+    assert st == 0
+    assert np.array_equal(out1, shifted)
+    assert np.array_equal(out4, shifted)
+
+
+def test_batched_count_mismatch_per_list():
+    enc = np.frombuffer(b"\x01\x02\x03", dtype=np.uint8)
+    bo = np.array([0, 1, 3], dtype=np.uint64)
+    vo = np.array([0, 2, 3], dtype=np.uint64)   # list 0 claims 2 values, holds 1
+    _, st = oracle.decode_batched(enc, bo, vo, delta=False)
+    assert st == oracle.ERR_COUNT_MISMATCH
