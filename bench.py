@@ -1,0 +1,457 @@
+"""Benchmark: VByte decoding throughput on GB300 (Gints/s and % of HBM roofline).
+
+Default workload (one "step" = one pass of the whole hot path over one batch):
+differential decoding of two single streams of 2^26 uint32 each --
+  stream A: gaps 1 + Geometric(0.1) (first gap 0), almost all one-byte codes;
+  stream B: gaps uniform in [1, 300], a dense mix of one- and two-byte codes --
+VByte-encoded on the host, resident in HBM, decoded and prefix-summed back to
+document ids (uint32 wrap-around).  Inputs plus outputs exceed the 129 MB L2,
+so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload differential_2x2^26 | ...]
+
+Under torchrun (N > 1) every rank decodes its own replica of the workload
+(the path shards into independent streams; no data-path collective); rank 0
+prints one JSON line with the whole-job throughput.  ``--impl reference`` times
+the CPU oracle (Algorithm 1, one core) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1503_07387_gb300 import inputs  # noqa: E402
+
+METRIC = "Gints/s decoded + % of HBM roofline"
+UNIT = "Gints/s"
+PROFILE_FILE = os.path.join(ROOT, "profiles", "decode_delta_differential_2x2^26.md")
+
+
+# ------------------------------------------------------------------ workloads --
+
+def workload(name: str):
+    """Returns a list of (label, values_to_encode, delta) streams."""
+    if name == "differential_2x2^26":
+        return [("geometric_gaps", inputs.geometric_gaps(1 << 26, seed=0), True),
+                ("uniform_gaps_1_300", inputs.uniform_gaps(1 << 26, seed=1), True)]
+    if name == "plain_uniform_bits_1e6":
+        return [("uniform_bits", inputs.uniform_bits(1_000_000, seed=0), False)]
+    if name == "plain_one_two_2^28":
+        return [("one_two_byte_mix", inputs.one_two_byte_mix(1 << 28, seed=0), False)]
+    if name == "delta_one_two_2^28":
+        return [("one_two_byte_mix", inputs.one_two_byte_mix(1 << 28, seed=0), True)]
+    if name == "plain_full_range_2^28":
+        return [("full_range", inputs.full_range(1 << 28, seed=0), False)]
+    if name == "delta_full_range_2^28":
+        return [("full_range", inputs.full_range(1 << 28, seed=0), True)]
+    raise SystemExit(f"unknown workload {name}")
+
+
+WORKLOADS = ["differential_2x2^26", "plain_uniform_bits_1e6", "plain_one_two_2^28",
+             "delta_one_two_2^28", "plain_full_range_2^28", "delta_full_range_2^28"]
+
+
+# --------------------------------------------------------------- environment --
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1503_07387_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the kernel source that is built now (else None)."""
+    try:
+        text = open(PROFILE_FILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
+    m_traffic = re.search(r"dram bytes per launch \(full workload\):\s*([0-9.eE+]+)", text)
+    if m_hash and m_traffic and m_hash.group(1) == src_hash:
+        return float(m_traffic.group(1))
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampler running while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.rows = []
+        self.t_start = self.t_end = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", f"-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, "t_" + which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        rows = [r for t, r in self.rows if self.t_start <= t <= self.t_end + 0.15]
+        window = "timed region"
+        if not rows:
+            rows = [r for _, r in self.rows]
+            window = "whole run (timed region shorter than the sampling period)"
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs),
+                "reasons": sorted(reasons), "samples": len(sms), "window": window}
+
+
+# --------------------------------------------------------------------- GPU arm --
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1503_07387_gb300 import vbyte
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vbyte.load()
+
+    streams = []
+    for label, vals, delta in workload(args.workload):
+        # values are the integers to code; for differential streams they are the gaps
+        data = vbyte.encode(vals)
+        streams.append(dict(label=label, n=int(vals.size), delta=delta, host=data,
+                            d_in=torch.from_numpy(data).cuda(),
+                            d_out=torch.empty(vals.size, dtype=torch.uint32, device="cuda")))
+        del vals
+    torch.cuda.synchronize()
+    total_vals = sum(s["n"] for s in streams)
+    algo_bytes = sum(s["host"].size + 4 * s["n"] for s in streams)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for i, s in enumerate(streams):
+            if events is not None:
+                events[i][0].record(stream)
+            if s["delta"]:
+                vbyte.decode_delta(s["d_in"], s["n"], out=s["d_out"], stream=stream)
+            else:
+                vbyte.decode(s["d_in"], s["n"], out=s["d_out"], stream=stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if vbyte.get_status() != 0:
+        raise SystemExit("data error during warm-up")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    per_launch = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+                   for _ in streams] for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark("start")
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(per_launch[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark("end")
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    launch_ms = [[ev[0].elapsed_time(ev[1]) for ev in row] for row in per_launch]
+    status = vbyte.get_status()
+
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    # ---- end to end through the public host-buffer call (copies inside)
+    pinned_in = [torch.from_numpy(s["host"]).pin_memory() for s in streams]
+    pinned_out = [torch.empty(s["n"], dtype=torch.int32).pin_memory() for s in streams]
+    h_in = [p.numpy() for p in pinned_in]
+    h_out = [p.numpy().view(np.uint32) for p in pinned_out]
+    e2e_steps = max(3, min(args.steps, 20))
+    for i, s in enumerate(streams):
+        vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
+    if ws > 1:
+        dist.barrier()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, s in enumerate(streams):
+            vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
+    e2e_s = time.perf_counter() - te
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    status |= vbyte.get_status()
+
+    # ---- CPU baseline (rank 0, N = 1 only): the oracle as it stands
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(streams, budget_s=args.cpu_seconds)
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    peak_gbs = peaks["hbm_gbs"] if peaks else 6800.0
+    launches = [x for row in launch_ms for x in row]
+    avg_launch_ms = sum(launches) / len(launches)
+    bytes_per_launch = algo_bytes / len(streams)
+    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+    src_hash = kernel_source_hash()
+    traffic = profiled_traffic(src_hash)
+    value = ws * total_vals * args.steps / (elapsed_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8->u32",
+        "data": "synthetic (seeded generators shaped like the paper's posting lists)",
+        "config": {
+            "workload": args.workload,
+            "streams": [{"label": s["label"], "n": s["n"], "nbytes": int(s["host"].size),
+                         "mode": "differential" if s["delta"] else "plain"} for s in streams],
+            "values_per_step": total_vals,
+            "l2": "inputs and outputs larger than the 129 MB L2; no flush",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+        },
+        "roofline": {
+            "bound": "hbm",
+            "achieved": round(achieved, 1),
+            "peak": peak_gbs,
+            "unit": "GB/s",
+            "frac": round(achieved / peak_gbs, 4),
+            "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
+            "traffic": traffic,
+            "kernel": "decode_kernel<delta>" if all(s["delta"] for s in streams) else "decode_kernel",
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": round(avg_launch_ms, 5),
+            "kernel_source_hash": src_hash,
+        },
+        "e2e": {
+            "value": round(ws * total_vals * e2e_steps / e2e_s / 1e9, 3),
+            "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(s["host"].size for s in streams)),
+            "d2h_bytes_per_step": int(4 * total_vals),
+            "api": "vbyte_decode_host (pinned host buffers, copies inside the call)",
+        },
+        "gpu_launches": len(streams) * args.steps,
+        "status": status,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(streams, budget_s=10.0):
+    """The oracle (scalar Algorithm 1, one core) over the same streams, repeated
+    until about budget_s seconds of CPU work."""
+    import oracle
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        for s in streams:
+            if s["delta"]:
+                oracle.decode_delta(s["host"], s["n"])
+            else:
+                oracle.decode(s["host"], s["n"])
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    total = reps * sum(s["n"] for s in streams)
+    return {"value": round(total / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full pass(es) over every stream of the workload "
+                      f"({total} values, {dt:.1f} s, single thread)"}
+
+
+# --------------------------------------------------------------- reference arm --
+
+def _prefix_bytes(data: np.ndarray, m: int) -> int:
+    """Byte length of the first m integers of a well-formed stream."""
+    if m <= 0:
+        return 0
+    ends = np.flatnonzero(data < 128)
+    return int(ends[m - 1]) + 1
+
+
+def run_reference(args):
+    """The CPU oracle (scalar Algorithm 1, one core) on the same workload.  Each
+    step decodes a bounded prefix of every stream, sized so that the whole
+    --steps/--warmup run stays within about args.ref_seconds."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1503_07387_gb300 import vbyte
+    oracle.build()
+    streams = []
+    for label, vals, delta in workload(args.workload):
+        streams.append(dict(label=label, n=int(vals.size), delta=delta, host=vbyte.encode(vals)))
+    # calibrate the oracle's speed on the first 2^20 values of each stream
+    t0 = time.perf_counter()
+    cal = 0
+    for s in streams:
+        m = min(s["n"], 1 << 20)
+        nb = _prefix_bytes(s["host"], m)
+        (oracle.decode_delta if s["delta"] else oracle.decode)(s["host"][:nb], m)
+        cal += m
+    rate = cal / max(time.perf_counter() - t0, 1e-6)
+    per_step = args.ref_seconds / (args.steps + args.warmup)
+    frac = min(1.0, per_step * rate / sum(s["n"] for s in streams))
+    for s in streams:
+        s["m"] = max(1, int(s["n"] * frac))
+        s["nb"] = _prefix_bytes(s["host"], s["m"])
+
+    def step():
+        for s in streams:
+            (oracle.decode_delta if s["delta"] else oracle.decode)(s["host"][:s["nb"]], s["m"])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    per = sum(s["m"] for s in streams)
+    total = args.steps * per
+    value = total / dt / 1e9
+    sample = (f"each step decodes the first {frac:.4f} of every stream ({per} values), "
+              f"single thread")
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8->u32",
+        "data": "synthetic (seeded generators shaped like the paper's posting lists)",
+        "config": {"workload": args.workload,
+                   "streams": [{"label": s["label"], "n": s["n"], "nbytes": int(s["host"].size),
+                                "mode": "differential" if s["delta"] else "plain"} for s in streams]},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=WORKLOADS, default="differential_2x2^26")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,135 @@
+/*
+ * libvbyte -- GPU decoding of VByte-compressed uint32 streams on GB300
+ * (sm_103a).
+ *
+ * The operation follows Plaisance, Kurz, Lemire, "Vectorized VByte Decoding"
+ * (arXiv 1503.07387):
+ *   - format (Sec. 1, Table 1): each integer is written seven bits at a time,
+ *     least significant group first; the high bit of every byte is 1 except
+ *     on the integer's last byte.  Integers in [0,2^7) take one byte,
+ *     [2^7,2^14) two, ... up to five bytes for uint32;
+ *   - decoding (Sec. 2, Algorithm 1): the result is exactly what the
+ *     conventional byte-at-a-time decoder appends, with uint32 arithmetic
+ *     (a fifth byte contributes b * 2^28 modulo 2^32);
+ *   - differential coding (Sec. 1 "Differential coding", Sec. 2 and Sec. 4
+ *     "Differential Coding"): the stream holds gaps x_i - x_{i-1} with
+ *     x_0 = prev, and decoding returns the prefix sums x_i modulo 2^32.
+ *
+ * Conventions for every entry point below:
+ *   - "d_" pointers are device memory owned by the caller; "h_" pointers are
+ *     host memory owned by the caller (page-locked memory gives the fastest
+ *     copies).  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Device work is queued on it and the call returns without
+ *     synchronising, except where an entry point says otherwise.
+ *   - The library keeps one small workspace per (device, stream): a status
+ *     word, a tile counter and the look-back descriptors of the single-pass
+ *     scan (16 bytes per 4 KiB of input).  It grows on demand with
+ *     cudaMallocAsync on that stream; a call made while the stream is being
+ *     captured into a CUDA graph never allocates and returns VBYTE_ENOMEM if
+ *     the workspace is too small (run the same call once before capture).
+ *   - Return codes are synchronous argument/launch checks (VBYTE_OK ...).
+ *     Errors that depend on the data are recorded asynchronously in the
+ *     per-stream status word (VBYTE_ERR_* bits) and read with
+ *     vbyte_get_status(); the decode path never synchronises to look.
+ *   - Output writes are always clamped to [0, n).  When a data error is
+ *     recorded, output slots the stream does not define are unspecified.
+ */
+#ifndef VBYTE_H
+#define VBYTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- synchronous return codes ------------------------------------------ */
+#define VBYTE_OK 0
+#define VBYTE_EINVAL 1 /* null pointer with a nonzero size, misaligned output */
+#define VBYTE_ECUDA 2  /* a CUDA runtime call or kernel launch failed */
+#define VBYTE_ENOMEM 3 /* workspace could not be grown */
+
+/* ---- data-error bits of the per-stream status word --------------------- */
+/* A run of five or more consecutive bytes with the high bit set: Algorithm 1
+ * would consume a fifth byte whose high bit it never tests (Sec. 2). */
+#define VBYTE_ERR_MALFORMED_LONG 1u
+/* The last byte of a stream (or list) has the high bit set: the input ends
+ * inside an integer. */
+#define VBYTE_ERR_TRUNCATED 2u
+/* The number of terminator bytes (high bit clear) differs from the expected
+ * count n (or from val_off[j+1]-val_off[j] for list j). */
+#define VBYTE_ERR_COUNT_MISMATCH 4u
+/* A cross-tile look-back wait gave up after its time limit (about two
+ * seconds); the outputs of that call are unspecified. */
+#define VBYTE_ERR_TIMEOUT 8u
+
+/* ---- host-side encoding (input generation) ----------------------------- */
+
+/* Upper bound on the encoded size of n uint32 values: 5*n bytes (Sec. 1). */
+size_t vbyte_max_encoded_size(size_t n);
+
+/* Encode n values (Sec. 1, Table 1) into h_out, which must hold
+ * vbyte_max_encoded_size(n) bytes.  Returns the number of bytes written.
+ * Host memory only; no CUDA call. */
+size_t vbyte_encode(const uint32_t *h_in, size_t n, uint8_t *h_out);
+
+/* Differential coding (Sec. 1): encode the gaps h_in[i] - h_in[i-1] modulo
+ * 2^32 with h_in[-1] = prev.  Returns the number of bytes written. */
+size_t vbyte_encode_delta(const uint32_t *h_in, size_t n, uint32_t prev,
+                          uint8_t *h_out);
+
+/* Encode num_lists lists laid end to end: list j is
+ * h_in[h_val_off[j] .. h_val_off[j+1]).  With delta != 0 each list is
+ * differentially coded on its own, starting from h_prev[j] (0 when h_prev is
+ * NULL).  Writes h_byte_off[0..num_lists] (h_byte_off[0] = 0) and returns the
+ * total number of bytes.  h_out must hold vbyte_max_encoded_size(total). */
+size_t vbyte_encode_batched(const uint32_t *h_in, const uint64_t *h_val_off,
+                            size_t num_lists, int delta, const uint32_t *h_prev,
+                            uint8_t *h_out, uint64_t *h_byte_off);
+
+/* ---- single-stream GPU decoding ----------------------------------------- */
+
+/* Decode the nbytes-byte stream at d_in (any alignment) into the n uint32 at
+ * d_out (4-byte aligned), exactly as Algorithm 1 (Sec. 2) would.  n is the
+ * number of values the caller expects (e.g. the posting-list length); a
+ * different terminator count sets VBYTE_ERR_COUNT_MISMATCH.  n = 0 with
+ * nbytes = 0 is a no-op.  Returns VBYTE_EINVAL for a null pointer with a
+ * nonzero size or a d_out that is not 4-byte aligned. */
+int vbyte_decode(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size_t n,
+                 void *stream);
+
+/* As vbyte_decode, then undo differential coding: d_out[i] = prev + g_0 +
+ * ... + g_i modulo 2^32 where g_i are the decoded gaps (Sec. 1, Sec. 2,
+ * Sec. 4 "Differential Coding").  Passing the last value of one piece as prev
+ * for the next decodes a stream piece by piece. */
+int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
+                       size_t n, uint32_t prev, void *stream);
+
+/* End-to-end form of the two calls above for data in host memory: copies
+ * h_in to the device, decodes (differentially when delta != 0) and copies the
+ * n values back to h_out, through library-owned device buffers kept per
+ * stream.  Synchronises the stream before returning.  The data-error status
+ * is still read with vbyte_get_status(). */
+int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out,
+                      size_t n, int delta, uint32_t prev, void *stream);
+
+/* ---- status ---------------------------------------------------------- */
+
+/* Synchronise `stream`, return the OR of the VBYTE_ERR_* bits recorded by
+ * every call on it since the last vbyte_get_status(), and clear them. */
+int vbyte_get_status(void *stream, uint32_t *status_out);
+
+/* A static English description of a return code. */
+const char *vbyte_strerror(int code);
+
+/* Bytes of workspace a call on an nbytes-byte input needs (for planning
+ * graph capture); the library allocates it itself on first use. */
+size_t vbyte_workspace_size(size_t nbytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBYTE_H */

@@ -1,0 +1,183 @@
+"""Python binding of libvbyte (ctypes).  Argument marshalling only.
+
+Every step of decoding runs in the library's CUDA kernels; PyTorch supplies
+device memory (tensors) and streams.  There is no CPU fallback: if the shared
+library cannot be built or loaded, every call raises.
+
+Names mirror the C ABI in ``include/vbyte.h``:
+
+    encode / encode_delta / encode_batched      host encoder (numpy in, numpy out)
+    decode(d_bytes, n)                          Algorithm 1 on the GPU (Sec. 2)
+    decode_delta(d_bytes, n, prev)              ... plus the prefix sum of Sec. 1/4
+    decode_host(h_bytes, n, delta, prev)        host buffers in and out
+    get_status()                                data-error bits of a stream
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import _build
+
+OK, EINVAL, ECUDA, ENOMEM = 0, 1, 2, 3
+ERR_MALFORMED_LONG = 1
+ERR_TRUNCATED = 2
+ERR_COUNT_MISMATCH = 4
+ERR_TIMEOUT = 8
+
+HEADER = os.path.join(_build.INCLUDE, "vbyte.h")
+
+_lib = None
+
+
+class VByteError(RuntimeError):
+    pass
+
+
+def _signatures(lib):
+    P, S, U32, I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_int
+    sig = {
+        "vbyte_max_encoded_size": ([S], S),
+        "vbyte_encode": ([P, S, P], S),
+        "vbyte_encode_delta": ([P, S, U32, P], S),
+        "vbyte_encode_batched": ([P, P, S, I, P, P, P], S),
+        "vbyte_decode": ([P, S, P, S, P], I),
+        "vbyte_decode_delta": ([P, S, P, S, U32, P], I),
+        "vbyte_decode_host": ([P, S, P, S, I, U32, P], I),
+        "vbyte_get_status": ([P, P], I),
+        "vbyte_strerror": ([I], ctypes.c_char_p),
+        "vbyte_workspace_size": ([S], S),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+
+
+def load(build: bool = True):
+    """Load (building first if needed) the in-tree libvbyte.so."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise VByteError(f"libvbyte.so not found at {_build.LIB}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    _signatures(lib)
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/vbyte.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vbyte_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        msg = load().vbyte_strerror(rc).decode()
+        raise VByteError(f"{what} failed: {msg} (code {rc})")
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else None
+
+
+# ------------------------------------------------------------------ encoder --
+
+def encode(values) -> np.ndarray:
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    out = np.empty(max(5 * v.size, 1), dtype=np.uint8)
+    nb = load().vbyte_encode(_np_ptr(v), v.size, _np_ptr(out))
+    return out[:nb]
+
+
+def encode_delta(values, prev: int = 0) -> np.ndarray:
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    out = np.empty(max(5 * v.size, 1), dtype=np.uint8)
+    nb = load().vbyte_encode_delta(_np_ptr(v), v.size, ctypes.c_uint32(prev & 0xFFFFFFFF), _np_ptr(out))
+    return out[:nb]
+
+
+def encode_batched(values, val_off, delta: bool, prev=None):
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    vo = np.ascontiguousarray(val_off, dtype=np.uint64)
+    L = vo.size - 1
+    pv = None if prev is None else np.ascontiguousarray(prev, dtype=np.uint32)
+    out = np.empty(max(5 * v.size, 1), dtype=np.uint8)
+    bo = np.empty(L + 1, dtype=np.uint64)
+    nb = load().vbyte_encode_batched(_np_ptr(v), _np_ptr(vo), L, int(delta),
+                                     None if pv is None else _np_ptr(pv), _np_ptr(out), _np_ptr(bo))
+    return out[:nb], bo
+
+
+# ------------------------------------------------------------------ decoder --
+
+def _device_args(data, n, out):
+    import torch
+    if not isinstance(data, torch.Tensor) or data.dtype != torch.uint8 or not data.is_cuda:
+        raise TypeError("data must be a CUDA uint8 tensor")
+    if not data.is_contiguous():
+        raise ValueError("data must be contiguous")
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint32, device=data.device)
+    elif out.dtype not in (torch.uint32, torch.int32) or not out.is_contiguous() or out.numel() < n:
+        raise ValueError("out must be a contiguous 32-bit CUDA tensor with at least n elements")
+    return out
+
+
+def decode(data, n: int, out=None, stream=None):
+    """Decode the VByte stream in the CUDA uint8 tensor `data` into n uint32."""
+    out = _device_args(data, n, out)
+    rc = load().vbyte_decode(ctypes.c_void_p(data.data_ptr()), data.numel(),
+                             ctypes.c_void_p(out.data_ptr()), n, _stream_handle(stream))
+    _check(rc, "vbyte_decode")
+    return out
+
+
+def decode_delta(data, n: int, prev: int = 0, out=None, stream=None):
+    """Decode gaps and return their prefix sums from prev (uint32 wrap-around)."""
+    out = _device_args(data, n, out)
+    rc = load().vbyte_decode_delta(ctypes.c_void_p(data.data_ptr()), data.numel(),
+                                   ctypes.c_void_p(out.data_ptr()), n,
+                                   ctypes.c_uint32(prev & 0xFFFFFFFF), _stream_handle(stream))
+    _check(rc, "vbyte_decode_delta")
+    return out
+
+
+def decode_host(data: np.ndarray, n: int, delta: bool = False, prev: int = 0, out=None, stream=None):
+    """Host bytes in, host uint32 out (copies in both directions inside the call)."""
+    b = np.ascontiguousarray(data, dtype=np.uint8)
+    if out is None:
+        out = np.empty(n, dtype=np.uint32)
+    rc = load().vbyte_decode_host(_np_ptr(b), b.size, _np_ptr(out), n, int(delta),
+                                  ctypes.c_uint32(prev & 0xFFFFFFFF), _stream_handle(stream))
+    _check(rc, "vbyte_decode_host")
+    return out
+
+
+def get_status(stream=None) -> int:
+    """Synchronise the stream, return and clear its data-error bits."""
+    v = ctypes.c_uint32(0)
+    rc = load().vbyte_get_status(_stream_handle(stream), ctypes.byref(v))
+    _check(rc, "vbyte_get_status")
+    return int(v.value)
+
+
+def workspace_size(nbytes: int) -> int:
+    return int(load().vbyte_workspace_size(nbytes))

@@ -1,0 +1,62 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every symbol
+the public header declares, and its host encoder agrees byte for byte with
+the oracle's (no GPU needed: the encoder is host code)."""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_07387_gb300 import _build, inputs, vbyte
+
+
+def test_library_builds_and_loads():
+    lib = vbyte.load()
+    assert isinstance(lib, ctypes.CDLL)
+
+
+def test_every_declared_symbol_is_exported():
+    names = vbyte.declared_symbols()
+    assert "vbyte_decode" in names and "vbyte_decode_delta" in names
+    lib = vbyte.load()
+    for name in names:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+
+
+def test_strerror_and_sizes():
+    lib = vbyte.load()
+    assert lib.vbyte_strerror(0) == b"ok"
+    assert b"invalid" in lib.vbyte_strerror(1)
+    assert lib.vbyte_max_encoded_size(10) == 50
+    assert vbyte.workspace_size(0) >= 512
+    assert vbyte.workspace_size(1 << 30) >= 16 * ((1 << 30) // 4096)
+
+
+@pytest.mark.parametrize("gen", ["uniform_bits", "geometric_gaps", "uniform_gaps",
+                                 "one_two_byte_mix", "full_range"])
+def test_host_encoder_matches_oracle(gen):
+    v = getattr(inputs, gen)(100_000, seed=3)
+    assert np.array_equal(vbyte.encode(v), oracle.encode(v))
+
+
+def test_host_encoder_boundaries():
+    v = np.array([0, 1, 127, 128, 16383, 16384, 2**21 - 1, 2**21, 2**28 - 1, 2**28,
+                  2**32 - 1], dtype=np.uint32)
+    assert np.array_equal(vbyte.encode(v), oracle.encode(v))
+    assert vbyte.encode(np.zeros(0, np.uint32)).size == 0
+
+
+def test_host_delta_and_batched_encoders_match_oracle():
+    ids, vo = inputs.length_class_lists(200, max_class=9, seed=1)
+    x = ids[int(vo[3]):int(vo[4])]
+    assert np.array_equal(vbyte.encode_delta(x, prev=17), oracle.encode_delta(x, prev=17))
+    prev = np.arange(200, dtype=np.uint32)
+    for delta in (False, True):
+        b1, o1 = vbyte.encode_batched(ids, vo, delta, prev if delta else None)
+        b2, o2 = oracle.encode_batched(ids, vo, delta, prev if delta else None)
+        assert np.array_equal(b1, b2) and np.array_equal(o1, o2)
