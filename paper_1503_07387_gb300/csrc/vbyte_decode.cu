@@ -6,31 +6,33 @@
 // -- optionally followed by the prefix sum that undoes differential coding
 // (Sec. 1 "Differential coding", Sec. 4 "Differential Coding").
 //
-// GPU design (one kernel, one pass over the input, persistent CTAs):
+// GPU design (one kernel, one pass over the input, persistent CTAs that take
+// tiles from an atomic counter and prefetch the next tile while decoding):
 //   (a) terminator mask + slot assignment.  A tile is 4 KiB of input aligned
 //       to 16 bytes in absolute address space.  Each thread loads 16 bytes
 //       with one vector load, forms a 16-bit mask of terminator bytes (high
 //       bit clear -- the GPU counterpart of pmovmskb in Sec. 3/4) and counts
-//       them.  A block scan gives every thread its first slot inside the
-//       tile; a decoupled look-back over per-tile descriptors gives the
-//       tile's first global slot.  A tile owns exactly the integers whose
-//       terminator byte lies inside it; the 16 bytes before the tile are
-//       staged too, so an integer that starts in the previous tile (at most
-//       four bytes earlier) is assembled by the tile holding its terminator.
+//       them; a block scan gives every thread its first rank inside the tile.
+//       A tile owns exactly the integers whose terminator byte lies inside
+//       it; the 16 bytes before the tile are staged too, so an integer that
+//       starts up to four bytes before the tile is assembled by the tile
+//       holding its terminator.
 //   (b) value assembly.  Integers are assembled branch-free from the (up to)
 //       five bytes ending at their terminator.  The work is split by the
 //       longest code in the tile, the GPU counterpart of the paper's case
-//       split on the 12-bit mask (Sec. 4): class A (every byte a
-//       terminator: values are the bytes themselves), class B (codes of at
-//       most two bytes: a SWAR byte-pair merge over 4-byte words) and class
-//       C (any length: per-terminator assembly from shared memory).
-//       Values are staged in shared memory at their tile rank, shifted so
-//       that every output quad is 16-byte aligned in global memory.
-//   (c) fused delta prefix sum.  Staged gaps are scanned in registers (four
-//       consecutive values per thread, then a warp scan, then a block scan of
-//       warp totals) and the tile's carry-in comes from a second decoupled
-//       look-back on gap sums, seeded with `prev` (uint32 wrap-around).
-//   Output quads leave with 16-byte stores, clamped to [0, n).
+//       split on the 12-bit mask (Sec. 4): class A (every byte a terminator:
+//       values are the bytes themselves), class B (codes of at most two
+//       bytes: a SWAR byte-pair merge over 4-byte words) and class C (any
+//       length: per-terminator assembly from shared memory).  Values are
+//       staged in shared memory at their tile rank.
+//   (c) fused delta prefix sum.  Staged gaps are scanned in place (four
+//       consecutive values per thread, then a warp scan), and the per-warp
+//       totals give each (round, warp) entry its offset inside the tile.
+//   The tile's exclusive (count, gap sum) prefix comes from a two-level
+//   decoupled look-back (tiles grouped 32 at a time through atomic group
+//   accumulators), seeded with `prev`.  Output leaves in 16-byte aligned
+//   quads; the alignment shift is applied with one lane shuffle, and every
+//   write is clamped to [0, n).
 //
 // Every cross-tile wait is bounded by the global timer (about two seconds);
 // on expiry the status word gets VBYTE_ERR_TIMEOUT and the kernel carries on.
@@ -52,12 +54,12 @@ constexpr int kBPT = 16;                      // input bytes per thread
 constexpr int kTile = kThreads * kBPT;        // input bytes per tile (4 KiB)
 constexpr int kHalo = 16;                     // bytes staged before the tile
 constexpr int kRoundVals = kThreads * 4;      // values per copy-out round
-constexpr int kMaxRounds = (kTile + 3 + kRoundVals - 1) / kRoundVals;
-constexpr int kValStage = kTile + 16;         // staged values (+ alignment shift)
+constexpr int kGroup = 32;                    // tiles per look-back group
 
 constexpr uint64_t kStateAgg = 1ull << 62;    // descriptor holds the tile aggregate
 constexpr uint64_t kStateIncl = 2ull << 62;   // descriptor holds the inclusive prefix
 constexpr uint64_t kPayload = (1ull << 62) - 1;
+constexpr uint64_t kMask48 = (1ull << 48) - 1;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 enum : uint32_t { kClassA = 0, kClassB = 1, kClassC = 2 };
@@ -69,8 +71,9 @@ struct Params {
     uint64_t n;
     uint64_t ntiles;
     uintptr_t base;            // 16-byte aligned address of tile 0
-    uint64_t *dcnt;            // per-tile terminator-count descriptors
-    uint64_t *dsum;            // per-tile gap-sum descriptors (delta mode)
+    uint64_t *tdesc;           // per tile: [state|count], [state|gap sum]
+    unsigned long long *gacc;  // per group: atomic (contributors << 48 | count), (... | sum)
+    uint64_t *gdesc;           // per group: [state|count], [state|gap sum]
     unsigned long long *ctr;   // dynamic tile counter
     uint32_t *status;          // data-error bits
     uint32_t prev;             // x_0 for differential decoding
@@ -141,47 +144,34 @@ __device__ __forceinline__ uint32_t assemble(uint32_t lo4, uint32_t x, int L)
     return __funnelshift_r(u | (x << 28), x >> 4, 35 - 7 * L);
 }
 
-// Decoupled look-back (one warp).  Lane i inspects descriptor t-1-i; the warp
-// waits until every descriptor up to the nearest inclusive one has been
-// published, adds their payloads and repeats 32 tiles further back if none
-// of them was inclusive.  Descriptors before tile 0 count as inclusive zero.
-__device__ uint64_t lookback(const uint64_t *desc, unsigned long long t, uint32_t *status)
+// Volatile 16-byte descriptor access: each 64-bit word is a single-copy
+// atomic access with its own state bits, so a reader that sees one word
+// published and the other not yet simply waits.
+__device__ __forceinline__ void ld_pair(const uint64_t *p, uint64_t &a, uint64_t &b)
 {
-    const int lane = threadIdx.x & 31;
-    uint64_t acc = 0;
-    long long hi = static_cast<long long>(t) - 1;
-    uint64_t t0 = 0;
-    bool timed_out = false;
-    for (;;) {
-        const long long idx = hi - lane;
-        uint64_t w;
-        unsigned incl, need;
-        for (;;) {
-            w = idx >= 0 ? ld_relaxed(desc + idx) : kStateIncl;
-            const unsigned st = static_cast<unsigned>(w >> 62);
-            incl = __ballot_sync(~0u, st == 2u);
-            const unsigned empty = __ballot_sync(~0u, st == 0u);
-            need = incl ? (((incl & (0u - incl)) << 1) - 1u) : ~0u;
-            if (!(empty & need) || timed_out) break;
-            const uint64_t now = global_ns();
-            if (t0 == 0) t0 = now;
-            if (now - t0 > kWaitLimitNs) {
-                timed_out = true;
-                if (lane == 0) atomicOr(status, VBYTE_ERR_TIMEOUT);
-            }
-            __nanosleep(32);
-        }
-        uint64_t v = ((need >> lane) & 1u) ? (w & kPayload) : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
-        acc += v;
-        if (incl || timed_out) break;
-        hi -= 32;
-    }
-    return acc;
+    asm volatile("ld.volatile.global.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
-// Exclusive warp scan helper: returns the inclusive scan of x over lanes.
+__device__ __forceinline__ void st_pair(uint64_t *p, uint64_t a, uint64_t b)
+{
+    asm volatile("st.volatile.global.v2.u64 [%0], {%1,%2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
+    return v;
+}
+
+// Lanes 0..k where k is the lowest lane whose bit is set in `incl` (all lanes
+// when none is): the descriptors that must be present before summing.
+__device__ __forceinline__ unsigned through_first(unsigned incl)
+{
+    return incl ? (((incl & (0u - incl)) << 1) - 1u) : ~0u;
+}
+
+// Inclusive warp scan of x over lanes.
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
 {
 #pragma unroll
@@ -192,21 +182,201 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
     return x;
 }
 
-// ------------------------------------------------------------------ kernel --
+// ------------------------------------------------------------- look-back --
+//
+// Exclusive prefix (terminator count, gap sum) of a tile, by one warp, with a
+// two-level decoupled look-back.  Tiles are grouped kGroup at a time:
+//   - each tile publishes its aggregate in its own descriptor (tdesc) and
+//     adds it to its group's atomic accumulators; the tile whose addition
+//     completes the group publishes the group aggregate (gdesc, state AGG),
+//     and once its own prefix is known upgrades it to INCL;
+//   - a tile's prefix is the sum of the aggregates of the earlier tiles of
+//     its group (one descriptor per lane) plus the prefix of its group, found
+//     by looking back over group descriptors 32 at a time until an INCL one.
+// The inclusive frontier thus advances 32 * kGroup tiles per L2 round trip.
+// Every tile publishes before it waits, and waits only on earlier tiles, so
+// every wait ends; each wait is also bounded by the global timer.
+
+struct LbLoads {
+    uint64_t ta, tb;   // this lane's intra-group tile descriptor
+    uint64_t ga, gb;   // this lane's group descriptor (first window)
+};
+
+// Issue the descriptor loads of tile u's look-back early; lb_finish re-polls
+// only what was not yet published when these loads returned.
+__device__ __forceinline__ LbLoads lb_issue(const Params &p, uint64_t u, int lane)
+{
+    LbLoads l;
+    l.ta = l.tb = l.ga = l.gb = 0;
+    const uint64_t g = u / kGroup;
+    const uint64_t j = g * kGroup + lane;
+    if (j < u) ld_pair(p.tdesc + 2 * j, l.ta, l.tb);
+    const long long gi = static_cast<long long>(g) - 1 - lane;
+    if (gi >= 0) ld_pair(p.gdesc + 2 * gi, l.ga, l.gb);
+    return l;
+}
+
+struct Prefix {
+    uint64_t cnt;    // values decoded before the tile
+    uint32_t sum;    // running x value before the tile's first gap
+    uint64_t gcnt;   // values decoded before the tile's group
+    uint32_t gsum;   // running x value before the tile's group
+};
 
 template <bool kDelta>
-__global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
+__device__ Prefix lb_finish(const Params &p, uint64_t u, LbLoads l, int lane)
 {
-    __shared__ __align__(16) uint8_t s_bytes[kHalo + kTile + 16];
-    __shared__ __align__(16) uint32_t s_vals[kValStage];
+    const uint64_t g = u / kGroup;
+    const uint64_t g0 = g * kGroup;
+    uint64_t t_start = 0;
+    bool timed_out = false;
+    auto expired = [&]() -> bool {
+        if (timed_out) return true;
+        const uint64_t now = global_ns();
+        if (t_start == 0) t_start = now;
+        if (now - t_start > kWaitLimitNs) {
+            timed_out = true;
+            if (lane == 0) atomicOr(p.status, VBYTE_ERR_TIMEOUT);
+        }
+        return timed_out;
+    };
+
+    // earlier tiles of the same group
+    const uint64_t j = g0 + lane;
+    const bool mine = j < u;
+    for (int spin = 0;; ++spin) {
+        const bool ready = !mine || ((l.ta >> 62) != 0 && (!kDelta || (l.tb >> 62) != 0));
+        if (__all_sync(~0u, ready) || expired()) break;
+        if (spin > 8) __nanosleep(100);
+        if (mine) ld_pair(p.tdesc + 2 * j, l.ta, l.tb);
+    }
+    const uint64_t ec = warp_sum64(mine ? (l.ta & kPayload) : 0ull);
+    const uint64_t es = warp_sum64(mine ? (l.tb & 0xFFFFFFFFull) : 0ull);
+
+    // earlier groups; the virtual group before group 0 is inclusive (0, prev)
+    uint64_t pc = 0, ps = 0;
+    bool done_c = false, done_s = !kDelta;
+    long long hi = static_cast<long long>(g) - 1;
+    uint64_t a = l.ga, b = l.gb;
+    for (bool fresh = true; !(done_c && done_s); fresh = false) {
+        const long long idx = hi - lane;
+        unsigned need_c, need_s, inc_c, inc_s;
+        for (int spin = 0;; ++spin) {
+            if (!(fresh && spin == 0)) {
+                if (idx >= 0) ld_pair(p.gdesc + 2 * idx, a, b);
+            }
+            if (idx < 0) {
+                a = kStateIncl;
+                b = kStateIncl | (idx == -1 ? p.prev : 0u);
+            }
+            inc_c = __ballot_sync(~0u, (a >> 62) == 2u);
+            inc_s = __ballot_sync(~0u, (b >> 62) == 2u);
+            const unsigned emp_c = __ballot_sync(~0u, (a >> 62) == 0u);
+            const unsigned emp_s = __ballot_sync(~0u, (b >> 62) == 0u);
+            need_c = done_c ? 0u : through_first(inc_c);
+            need_s = done_s ? 0u : through_first(inc_s);
+            if ((!(emp_c & need_c) && !(emp_s & need_s)) || expired()) break;
+            if (spin > 8) __nanosleep(100);
+        }
+        pc += warp_sum64(((need_c >> lane) & 1u) ? (a & kPayload) : 0ull);
+        ps += warp_sum64(((need_s >> lane) & 1u) ? (b & 0xFFFFFFFFull) : 0ull);
+        if (need_c && inc_c) done_c = true;
+        if (need_s && inc_s) done_s = true;
+        if (timed_out) break;
+        hi -= 32;
+    }
+    Prefix r;
+    r.cnt = (pc + ec) & kPayload;
+    r.sum = static_cast<uint32_t>(ps + es);
+    r.gcnt = pc & kPayload;
+    r.gsum = static_cast<uint32_t>(ps);
+    return r;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Bit j set iff byte va + j lies inside [lo, hi).
+__device__ __forceinline__ uint32_t slice_valid(uintptr_t va, uintptr_t lo, uintptr_t hi)
+{
+    if (va >= lo && va + kBPT <= hi) return 0xFFFFu;
+    const long long a = static_cast<long long>(lo) - static_cast<long long>(va);
+    const long long z = static_cast<long long>(hi) - static_cast<long long>(va);
+    const int first = a > 0 ? (a > kBPT ? kBPT : static_cast<int>(a)) : 0;
+    const int last = z > 0 ? (z > kBPT ? kBPT : static_cast<int>(z)) : 0;
+    if (last <= first) return 0u;
+    return ((1u << last) - 1u) & ~((1u << first) - 1u);
+}
+
+// Stage tile t into `bytes`: bytes[16 + 16*tid ..] gets tid's 16-byte slice
+// (zero bytes outside the stream), bytes[0..16) the 16 bytes before the tile
+// (zero before tile 0, i.e. terminators of earlier, uncounted integers; for
+// t > 0 they always lie inside the stream).  Whole slices travel with
+// cp.async; the ragged first and last slices of the stream are loaded byte
+// by byte.  The caller commits and later waits for the copies.
+__device__ __forceinline__ void stage_tile(const Params &p, uint64_t t, int tid, uint8_t *bytes)
+{
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+    uint8_t *dst = bytes + kHalo + tid * kBPT;
+    if (va >= lo && va + kBPT <= hi) {
+        cp_async16(dst, reinterpret_cast<const void *>(va));
+    } else {
+        uint32_t wb[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const uintptr_t ad = va + j;
+            if (ad >= lo && ad < hi)
+                wb[j >> 2] |= static_cast<uint32_t>(*reinterpret_cast<const uint8_t *>(ad))
+                              << (8 * (j & 3));
+        }
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+    }
+    if (tid == 0) {
+        if (t > 0)
+            cp_async16(bytes, reinterpret_cast<const void *>(tstart - 16));
+        else
+            *reinterpret_cast<uint4 *>(bytes) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == kThreads - 1)
+        *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// ------------------------------------------------------------------ kernel --
+//
+// Per CTA, iteration k handles two tiles: it decodes tile T (taken from the
+// counter in iteration k-1, its bytes copied asynchronously then) and
+// publishes T's aggregate, then finishes tile U (decoded in iteration k-1):
+// resolves U's prefix -- whose descriptor loads were issued at the top of the
+// iteration -- and writes U's values out.  Input bytes rotate through three
+// shared-memory buffers (T, U, and the prefetch of the next tile), staged
+// values through two (T and U).
+
+constexpr int kByteBuf = kHalo + kTile + 16;
+constexpr int kValBuf = 4 + kTile + 16;   // vals[4 + k]: tile rank k
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kThreads, 4) decode_kernel(const Params p)
+{
+    __shared__ __align__(16) uint8_t s_bytes[3][kByteBuf];
+    __shared__ __align__(16) uint32_t s_vals[2][kValBuf];
     __shared__ uint32_t s_wcnt[kWarps];
     __shared__ uint32_t s_wflag[kWarps];
-    __shared__ uint32_t s_woff[kWarps];
-    __shared__ uint32_t s_rtot[64];
-    __shared__ unsigned long long s_tile;
-    __shared__ unsigned long long s_R0;
-    __shared__ uint32_t s_tcnt;
-    __shared__ uint32_t s_class;
+    __shared__ uint32_t s_rtot[32];
+    __shared__ uint32_t s_off[2][32];
+    __shared__ unsigned long long s_R0[2];
+    __shared__ uint32_t s_tcnt[2];
+    __shared__ uint32_t s_cls[2];
+    __shared__ unsigned long long s_next;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -214,254 +384,279 @@ __global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
     const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
-    uint32_t *const sw = reinterpret_cast<uint32_t *>(s_bytes);
 
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(p.ctr, 1ull);
-        __syncthreads();
-        const unsigned long long t = s_tile;
-        if (t >= p.ntiles) break;
-        const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
-        const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+    if (tid == 0) s_next = atomicAdd(p.ctr, 1ull);
+    __syncthreads();
+    unsigned long long t = s_next;     // tile decoded this iteration (T)
+    unsigned long long u = ~0ull;      // tile finished this iteration (U)
+    if (t < p.ntiles) stage_tile(p, t, tid, s_bytes[0]);
+    cp_async_commit();
+    // warp 0, lane 0: whether U completed its group, and the group aggregate
+    bool u_last_c = false, u_last_s = false;
+    uint64_t u_gc = 0;
+    uint32_t u_gs = 0;
+    int rb = 0;   // byte buffer of T; U's is (rb + 2) % 3, the prefetch's (rb + 1) % 3
 
-        // ---- stage the tile (and the 16 bytes before it) in shared memory
-        uint4 w;
-        uint32_t valid;
-        if (va >= lo && va + kBPT <= hi) {
-            w = ld_stream16(reinterpret_cast<const void *>(va));
-            valid = 0xFFFFu;
-        } else {
-            uint32_t wb[4] = {0u, 0u, 0u, 0u};
-            valid = 0u;
-#pragma unroll
-            for (int j = 0; j < kBPT; ++j) {
-                const uintptr_t ad = va + j;
-                if (ad >= lo && ad < hi) {
-                    wb[j >> 2] |= static_cast<uint32_t>(*reinterpret_cast<const uint8_t *>(ad))
-                                  << (8 * (j & 3));
-                    valid |= 1u << j;
-                }
-            }
-            w = make_uint4(wb[0], wb[1], wb[2], wb[3]);
-        }
-        *reinterpret_cast<uint4 *>(s_bytes + kHalo + tid * kBPT) = w;
-        if (tid == 0) {
-            // The 16 bytes before tile t > 0 always lie inside the stream; before
-            // tile 0 they read as zero bytes, i.e. as terminators of earlier,
-            // uncounted integers.
-            uint4 h = make_uint4(0u, 0u, 0u, 0u);
-            if (t > 0) h = ld_stream16(reinterpret_cast<const void *>(tstart - 16));
-            *reinterpret_cast<uint4 *>(s_bytes) = h;
-        }
-        if (tid == kThreads - 1)
-            *reinterpret_cast<uint4 *>(s_bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
-        __syncthreads();
+    for (int k = 0;; ++k) {
+        const bool cur = t < p.ntiles;
+        const bool fin = u < p.ntiles;
+        if (!cur && !fin) break;
+        const int vb = k & 1;
+        uint32_t *const sw = reinterpret_cast<uint32_t *>(s_bytes[rb]);
+        uint32_t *const sv = s_vals[vb] + 4;
+
+        cp_async_wait_all();
+        __syncthreads();   // T's bytes are staged; last iteration's readers are done
+        LbLoads ll;
+        if (warp == 0 && fin) ll = lb_issue(p, u, lane);
+        if (cur && tid == 0) s_next = atomicAdd(p.ctr, 1ull);
 
         // ---- (a) terminator masks, counts, data checks, tile class
-        const uint32_t wprev = sw[(kHalo + tid * kBPT) / 4 - 1];
-        const uint32_t tl = term4(w.x) | (term4(w.y) << 4) | (term4(w.z) << 8) | (term4(w.w) << 12);
-        const uint32_t t20 = term4(wprev) | (tl << 4);   // bits 0..3: the 4 bytes before mine
-        const uint32_t tc = tl & valid;                   // terminators inside the stream
-        const uint32_t cnt = __popc(tc);
-        const uint32_t c20 = ~t20 & 0xFFFFFu;             // continuation bytes
-        if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
-            atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
-        if (hi - 1 >= va && hi - 1 < va + kBPT && !((tl >> (hi - 1 - va)) & 1u))
-            atomicOr(p.status, VBYTE_ERR_TRUNCATED);
-        const bool edge = valid != 0xFFFFu;
-        const bool notA = edge || (c20 & 0xFFFF8u);
-        const bool notB = edge || (c20 & (c20 << 1) & 0xFFFF8u);
-
-        const uint32_t inc = warp_incl_scan(cnt, lane);
-        const unsigned fa = __ballot_sync(~0u, notA);
-        const unsigned fb = __ballot_sync(~0u, notB);
-        if (lane == 31) s_wcnt[warp] = inc;
-        if (lane == 0) s_wflag[warp] = (fa ? 1u : 0u) | (fb ? 2u : 0u);
+        const uintptr_t va = p.base + static_cast<uintptr_t>(t) * kTile + static_cast<uintptr_t>(tid) * kBPT;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t tl = 0, t20 = 0, tc = 0, cnt = 0, inc = 0, wprev = 0;
+        if (cur) {
+            w = *reinterpret_cast<const uint4 *>(s_bytes[rb] + kHalo + tid * kBPT);
+            wprev = sw[(kHalo + tid * kBPT) / 4 - 1];
+            tl = term4(w.x) | (term4(w.y) << 4) | (term4(w.z) << 8) | (term4(w.w) << 12);
+            t20 = term4(wprev) | (tl << 4);   // bits 0..3: the 4 bytes before mine
+            const uint32_t valid = slice_valid(va, lo, hi);
+            tc = tl & valid;                  // terminators inside the stream
+            cnt = __popc(tc);
+            const uint32_t c20 = ~t20 & 0xFFFFFu;   // continuation bytes
+            if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
+                atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
+            if (hi - 1 >= va && hi - 1 < va + kBPT && !((tl >> (hi - 1 - va)) & 1u))
+                atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+            const bool edge = valid != 0xFFFFu;
+            const bool notA = edge || (c20 & 0xFFFF8u);
+            const bool notB = edge || (c20 & (c20 << 1) & 0xFFFF8u);
+            inc = warp_incl_scan(cnt, lane);
+            const unsigned fa = __ballot_sync(~0u, notA);
+            const unsigned fb = __ballot_sync(~0u, notB);
+            if (lane == 31) s_wcnt[warp] = inc;
+            if (lane == 0) s_wflag[warp] = (fa ? 1u : 0u) | (fb ? 2u : 0u);
+        }
         __syncthreads();
 
-        if (warp == 0) {
-            const uint32_t wc = lane < kWarps ? s_wcnt[lane] : 0u;
-            uint32_t wi = wc;
+        uint32_t tcnt = 0, cls = kClassC;
+        unsigned long long tn = ~0ull;
+        if (cur) {
+            uint32_t wbase = 0, fl = 0;
 #pragma unroll
-            for (int o = 1; o < kWarps; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(~0u, wi, o);
-                if (lane >= o) wi += y;
+            for (int q = 0; q < kWarps; ++q) {
+                const uint32_t c = s_wcnt[q];
+                wbase += (q < warp) ? c : 0u;
+                tcnt += c;
+                fl |= s_wflag[q];
             }
-            const uint32_t tcnt = __shfl_sync(~0u, wi, kWarps - 1);
-            const uint32_t fl = __reduce_or_sync(~0u, lane < kWarps ? s_wflag[lane] : 0u);
-            if (lane < kWarps) s_woff[lane] = wi - wc;
-            uint64_t excl = 0;
-            if (t == 0) {
-                if (lane == 0) st_relaxed(p.dcnt, kStateIncl | tcnt);
-            } else {
-                if (lane == 0) st_relaxed(p.dcnt + t, kStateAgg | tcnt);
-                excl = lookback(p.dcnt, t, p.status);
-                if (lane == 0) st_relaxed(p.dcnt + t, kStateIncl | ((excl + tcnt) & kPayload));
+            cls = (fl & 2u) ? kClassC : ((fl & 1u) ? kClassB : kClassA);
+            if (tid == 0) {
+                s_tcnt[vb] = tcnt;
+                s_cls[vb] = cls;
+            }
+            const uint32_t mybase = wbase + inc - cnt;
+
+            // prefetch the tile of the next iteration
+            tn = s_next;
+            if (tn < p.ntiles) stage_tile(p, tn, tid, s_bytes[rb == 2 ? 0 : rb + 1]);
+
+            // ---- (b) value assembly into the staging buffer, at tile rank
+            if (cls == kClassC) {
+                uint32_t *dst = sv + mybase;
+                uint32_t m = tl;
+                int prevo = 27 - __clz(t20 & 0xFu);   // last terminator before my bytes (-5: none)
+                while (m) {
+                    const int o = __ffs(m) - 1;
+                    m &= m - 1u;
+                    const int L = min(o - prevo, 5);
+                    prevo = o;
+                    if ((tc >> o) & 1u) {
+                        const int q = kHalo + tid * kBPT + o;   // staging byte of the terminator
+                        const uint32_t A = sw[(q >> 2) - 1];
+                        const uint32_t B = sw[q >> 2];
+                        const uint32_t lo4 = __funnelshift_r(A, B, 8 * q);
+                        const uint32_t x = (B >> (8 * (q & 3))) & 0xFFu;
+                        *dst++ = assemble(lo4, x, L);
+                    }
+                }
+            } else if (cls == kClassB) {
+                uint32_t *dst = sv + mybase;
+                const uint32_t cur4[4] = {w.x, w.y, w.z, w.w};
+                uint32_t wp = wprev;
+                int q = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t c = cur4[j];
+                    const uint32_t s = __funnelshift_l(wp, c, 8);   // byte i: the byte before byte i
+                    const uint32_t cm = prmt(s, 0u, 0xBA98u);        // 0xFF where that byte continues
+                    const uint32_t lob = (s & 0x7F7F7F7Fu & cm) | (c & ~cm);
+                    const uint32_t hib = c & cm;
+                    uint32_t q01 = prmt(lob, hib, 0x5140u);
+                    uint32_t q23 = prmt(lob, hib, 0x7362u);
+                    q01 -= (q01 & 0xFF00FF00u) >> 1;
+                    q23 -= (q23 & 0xFF00FF00u) >> 1;
+                    const uint32_t v4[4] = {q01 & 0xFFFFu, q01 >> 16, q23 & 0xFFFFu, q23 >> 16};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if ((tc >> (4 * j + i)) & 1u) dst[q++] = v4[i];
+                    wp = c;
+                }
+            }
+        }
+        cp_async_commit();
+        __syncthreads();
+
+        // ---- (c) delta: scan T's gaps in place, per (round, warp) entry
+        if (kDelta && cur) {
+            const uint32_t nr1 = (tcnt + kRoundVals - 1) / kRoundVals;
+            for (uint32_t r = 0; r < nr1; ++r) {
+                const int idx = static_cast<int>(r * kRoundVals) + 4 * tid;
+                uint4 v;
+                if (cls == kClassA) {
+                    const uint32_t x = sw[(kHalo + idx) >> 2];
+                    v = make_uint4(prmt(x, 0u, 0x4440u), prmt(x, 0u, 0x4441u), prmt(x, 0u, 0x4442u),
+                                   prmt(x, 0u, 0x4443u));
+                } else {
+                    v = *reinterpret_cast<const uint4 *>(sv + idx);
+                }
+                if (static_cast<uint32_t>(idx) + 4 > tcnt) {
+                    if (static_cast<uint32_t>(idx) + 0 >= tcnt) v.x = 0u;
+                    if (static_cast<uint32_t>(idx) + 1 >= tcnt) v.y = 0u;
+                    if (static_cast<uint32_t>(idx) + 2 >= tcnt) v.z = 0u;
+                    if (static_cast<uint32_t>(idx) + 3 >= tcnt) v.w = 0u;
+                }
+                v.y += v.x;
+                v.z += v.y;
+                v.w += v.z;
+                const uint32_t ws = warp_incl_scan(v.w, lane);
+                const uint32_t ex = ws - v.w;
+                v.x += ex;
+                v.y += ex;
+                v.z += ex;
+                v.w += ex;
+                *reinterpret_cast<uint4 *>(sv + idx) = v;
+                if (lane == 31) s_rtot[r * kWarps + warp] = ws;
+            }
+        }
+        if (kDelta) __syncthreads();
+
+        // ---- warp 0: publish T's aggregate, then resolve U's prefix
+        if (warp == 0) {
+            unsigned long long oc = 0, os = 0;
+            uint64_t gt = 0, gsize = 0;
+            uint32_t tsum = 0;
+            if (cur) {
+                if (kDelta) {
+                    const uint32_t ne = ((tcnt + kRoundVals - 1) / kRoundVals) * kWarps;
+                    const uint32_t e = static_cast<uint32_t>(lane) < ne ? s_rtot[lane] : 0u;
+                    const uint32_t ie = warp_incl_scan(e, lane);
+                    tsum = __shfl_sync(~0u, ie, 31);
+                    s_off[vb][lane] = ie - e;   // tile-local; T's prefix is added next iteration
+                }
+                gt = t / kGroup;
+                const uint64_t g0t = gt * kGroup;
+                gsize = (p.ntiles - g0t < kGroup) ? (p.ntiles - g0t) : static_cast<uint64_t>(kGroup);
+                if (lane == 0) {
+                    st_pair(p.tdesc + 2 * t, kStateAgg | tcnt, kStateAgg | tsum);
+                    oc = atomicAdd(p.gacc + 2 * gt, (1ull << 48) | tcnt);
+                    if (kDelta) os = atomicAdd(p.gacc + 2 * gt + 1, (1ull << 48) | tsum);
+                }
+            }
+            if (fin) {
+                const Prefix pre = lb_finish<kDelta>(p, u, ll, lane);
+                if (kDelta) s_off[vb ^ 1][lane] += pre.sum;
+                if (lane == 0) {
+                    s_R0[vb ^ 1] = pre.cnt;
+                    const uint64_t gu = u / kGroup;
+                    if (u_last_c) st_relaxed(p.gdesc + 2 * gu, kStateIncl | ((pre.gcnt + u_gc) & kPayload));
+                    if (kDelta && u_last_s)
+                        st_relaxed(p.gdesc + 2 * gu + 1, kStateIncl | static_cast<uint32_t>(pre.gsum + u_gs));
+                    if (u == p.ntiles - 1 && pre.cnt + s_tcnt[vb ^ 1] != p.n)
+                        atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+                }
             }
             if (lane == 0) {
-                s_R0 = excl;
-                s_tcnt = tcnt;
-                s_class = (fl & 2u) ? kClassC : ((fl & 1u) ? kClassB : kClassA);
-                if (t == p.ntiles - 1 && excl + tcnt != p.n)
-                    atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
-            }
-        }
-        __syncthreads();
-
-        const unsigned long long R0 = s_R0;
-        const uint32_t tcnt = s_tcnt;
-        const uint32_t cls = s_class;
-        // staging index sh holds tile rank 0; it is chosen so that staging index
-        // 4k maps to a 16-byte aligned output address
-        const uint32_t sh = (out_word + static_cast<uint32_t>(R0)) & 3u;
-        const uint32_t mybase = s_woff[warp] + inc - cnt;
-
-        // ---- (b) value assembly into the staging buffer
-        if (cls == kClassC) {
-            uint32_t *dst = s_vals + sh + mybase;
-            uint32_t m = tl;
-            int prevo = 27 - __clz(t20 & 0xFu);   // last terminator before my bytes (-5: none)
-            while (m) {
-                const int o = __ffs(m) - 1;
-                m &= m - 1u;
-                const int L = min(o - prevo, 5);
-                prevo = o;
-                if ((tc >> o) & 1u) {
-                    const int q = kHalo + tid * kBPT + o;   // staging byte of the terminator
-                    const uint32_t A = sw[(q >> 2) - 1];
-                    const uint32_t B = sw[q >> 2];
-                    const uint32_t lo4 = __funnelshift_r(A, B, 8 * q);
-                    const uint32_t x = (B >> (8 * (q & 3))) & 0xFFu;
-                    *dst++ = assemble(lo4, x, L);
-                }
-            }
-        } else if (cls == kClassB) {
-            uint32_t *dst = s_vals + sh + mybase;
-            const uint32_t cur4[4] = {w.x, w.y, w.z, w.w};
-            uint32_t wp = wprev;
-            int k = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t cur = cur4[j];
-                const uint32_t s = __funnelshift_l(wp, cur, 8);  // byte i: the byte before byte i
-                const uint32_t cm = prmt(s, 0u, 0xBA98u);         // 0xFF where that byte continues
-                const uint32_t lob = (s & 0x7F7F7F7Fu & cm) | (cur & ~cm);
-                const uint32_t hib = cur & cm;
-                uint32_t q01 = prmt(lob, hib, 0x5140u);
-                uint32_t q23 = prmt(lob, hib, 0x7362u);
-                q01 -= (q01 & 0xFF00FF00u) >> 1;
-                q23 -= (q23 & 0xFF00FF00u) >> 1;
-                const uint32_t v4[4] = {q01 & 0xFFFFu, q01 >> 16, q23 & 0xFFFFu, q23 >> 16};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if ((tc >> (4 * j + i)) & 1u) dst[k++] = v4[i];
-                wp = cur;
-            }
-        }
-        __syncthreads();
-
-        // ---- copy-out (c: with the fused prefix sum in delta mode)
-        const uint32_t lim = sh + tcnt;                        // staged indices [sh, lim)
-        const long long gb = static_cast<long long>(R0) - sh;  // global rank of index 0
-        const uint32_t nr = (lim + kRoundVals - 1) / kRoundVals;
-
-        auto load_quad = [&](uint32_t idx) -> uint4 {
-            if (cls == kClassA) {
-                // every byte is a one-byte integer: tile rank k is tile byte k
-                const int q0 = kHalo + static_cast<int>(idx) - static_cast<int>(sh);
-                const uint32_t x = __funnelshift_r(sw[q0 >> 2], sw[(q0 >> 2) + 1], 8 * q0);
-                return make_uint4(prmt(x, 0u, 0x4440u), prmt(x, 0u, 0x4441u),
-                                  prmt(x, 0u, 0x4442u), prmt(x, 0u, 0x4443u));
-            }
-            return *reinterpret_cast<const uint4 *>(s_vals + idx);
-        };
-        auto store_quad = [&](uint32_t idx, uint4 v) {
-            const long long g0 = gb + idx;
-            if (idx >= sh && idx + 4 <= lim && g0 + 4 <= static_cast<long long>(p.n)) {
-                st_quad(p.out + g0, v);
-            } else {
-                const uint32_t e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (idx + j >= sh && idx + j < lim && g0 + j < static_cast<long long>(p.n))
-                        p.out[g0 + j] = e[j];
-            }
-        };
-
-        if (!kDelta) {
-            for (uint32_t r = 0; r < nr; ++r) {
-                const uint32_t idx = r * kRoundVals + 4 * tid;
-                if (idx < lim) store_quad(idx, load_quad(idx));
-            }
-        } else {
-            uint4 vv[kMaxRounds];
-#pragma unroll
-            for (int r = 0; r < kMaxRounds; ++r) {
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (r < static_cast<int>(nr)) {
-                    const uint32_t idx = r * kRoundVals + 4 * tid;
-                    if (idx < lim) {
-                        v = load_quad(idx);
-                        if (idx < sh || idx + 4 > lim) {
-                            if (idx + 0 < sh || idx + 0 >= lim) v.x = 0u;
-                            if (idx + 1 < sh || idx + 1 >= lim) v.y = 0u;
-                            if (idx + 2 < sh || idx + 2 >= lim) v.z = 0u;
-                            if (idx + 3 < sh || idx + 3 >= lim) v.w = 0u;
-                        }
-                    }
-                    v.y += v.x;
-                    v.z += v.y;
-                    v.w += v.z;
-                    const uint32_t ws = warp_incl_scan(v.w, lane);
-                    const uint32_t ex = ws - v.w;
-                    v.x += ex;
-                    v.y += ex;
-                    v.z += ex;
-                    v.w += ex;
-                    if (lane == 31) s_rtot[r * kWarps + warp] = ws;
-                }
-                vv[r] = v;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                const uint32_t ne = nr * kWarps;
-                const uint32_t e0 = static_cast<uint32_t>(lane) < ne ? s_rtot[lane] : 0u;
-                const uint32_t e1 = static_cast<uint32_t>(lane) + 32 < ne ? s_rtot[lane + 32] : 0u;
-                const uint32_t i0 = warp_incl_scan(e0, lane);
-                const uint32_t c0 = __shfl_sync(~0u, i0, 31);
-                const uint32_t i1 = warp_incl_scan(e1, lane);
-                const uint32_t tsum = c0 + __shfl_sync(~0u, i1, 31);
-                uint32_t excl;
-                if (t == 0) {
-                    excl = p.prev;
-                    if (lane == 0) st_relaxed(p.dsum, kStateIncl | static_cast<uint32_t>(excl + tsum));
-                } else {
-                    if (lane == 0) st_relaxed(p.dsum + t, kStateAgg | tsum);
-                    excl = static_cast<uint32_t>(lookback(p.dsum, t, p.status));
-                    if (lane == 0)
-                        st_relaxed(p.dsum + t, kStateIncl | static_cast<uint32_t>(excl + tsum));
-                }
-                s_rtot[lane] = excl + i0 - e0;
-                s_rtot[lane + 32] = excl + c0 + i1 - e1;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < kMaxRounds; ++r) {
-                if (r < static_cast<int>(nr)) {
-                    const uint32_t idx = r * kRoundVals + 4 * tid;
-                    if (idx < lim) {
-                        const uint32_t off = s_rtot[r * kWarps + warp];
-                        uint4 v = vv[r];
-                        v.x += off;
-                        v.y += off;
-                        v.z += off;
-                        v.w += off;
-                        store_quad(idx, v);
+                u_last_c = false;
+                u_last_s = false;
+                if (cur) {
+                    u_last_c = (oc >> 48) + 1 == gsize;
+                    u_gc = (oc + tcnt) & kMask48;
+                    if (u_last_c) st_relaxed(p.gdesc + 2 * gt, kStateAgg | u_gc);
+                    if (kDelta) {
+                        u_last_s = (os >> 48) + 1 == gsize;
+                        u_gs = static_cast<uint32_t>(os + tsum);
+                        if (u_last_s) st_relaxed(p.gdesc + 2 * gt + 1, kStateAgg | u_gs);
                     }
                 }
             }
         }
+        __syncthreads();
+
+        // ---- copy-out of U: 16-byte aligned output quads, alignment fixed by
+        // a one-lane shuffle of the staged quads
+        if (fin) {
+            const uint32_t *const pw = reinterpret_cast<const uint32_t *>(s_bytes[rb == 0 ? 2 : rb - 1]);
+            const uint32_t *const pv = s_vals[vb ^ 1] + 4;
+            const uint32_t ucnt = s_tcnt[vb ^ 1];
+            const uint32_t ucls = s_cls[vb ^ 1];
+            const unsigned long long R0 = s_R0[vb ^ 1];
+            auto rank_quad = [&](int idx) -> uint4 {   // idx >= -4
+                if (!kDelta && ucls == kClassA) {
+                    const uint32_t x = pw[(kHalo + idx) >> 2];
+                    return make_uint4(prmt(x, 0u, 0x4440u), prmt(x, 0u, 0x4441u), prmt(x, 0u, 0x4442u),
+                                      prmt(x, 0u, 0x4443u));
+                }
+                uint4 v = *reinterpret_cast<const uint4 *>(pv + idx);
+                if (kDelta) {
+                    const uint32_t off = s_off[vb ^ 1][min(max(idx, 0) / 128, 31)];
+                    v.x += off;
+                    v.y += off;
+                    v.z += off;
+                    v.w += off;
+                }
+                return v;
+            };
+            const uint32_t sh = (out_word + static_cast<uint32_t>(R0)) & 3u;
+            const long long rho0 = static_cast<long long>(R0) - sh;   // output rank of quad 0
+            const uint32_t nr2 = (ucnt + sh + kRoundVals - 1) / kRoundVals;
+            for (uint32_t r = 0; r < nr2; ++r) {
+                const int idx = static_cast<int>(r * kRoundVals) + 4 * tid;
+                const int ridx = min(idx, kTile);   // keep reads inside the buffers
+                const uint4 qc = rank_quad(ridx);
+                uint4 qp;
+                qp.x = __shfl_up_sync(~0u, qc.x, 1);
+                qp.y = __shfl_up_sync(~0u, qc.y, 1);
+                qp.z = __shfl_up_sync(~0u, qc.z, 1);
+                qp.w = __shfl_up_sync(~0u, qc.w, 1);
+                if (lane == 0 && sh != 0u) qp = rank_quad(ridx - 4);
+                uint4 o;
+                switch (sh) {
+                case 0: o = qc; break;
+                case 1: o = make_uint4(qp.w, qc.x, qc.y, qc.z); break;
+                case 2: o = make_uint4(qp.z, qp.w, qc.x, qc.y); break;
+                default: o = make_uint4(qp.y, qp.z, qp.w, qc.x); break;
+                }
+                const int k0 = idx - static_cast<int>(sh);   // tile rank of o.x
+                const long long g0 = rho0 + idx;             // output rank of o.x
+                if (k0 >= 0 && k0 + 4 <= static_cast<int>(ucnt) && g0 + 4 <= static_cast<long long>(p.n)) {
+                    st_quad(p.out + g0, o);
+                } else if (k0 + 4 > 0 && k0 < static_cast<int>(ucnt)) {
+                    const uint32_t e4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (k0 + j >= 0 && k0 + j < static_cast<int>(ucnt) &&
+                            g0 + j < static_cast<long long>(p.n))
+                            p.out[g0 + j] = e4[j];
+                }
+            }
+        }
+
+        u = cur ? t : ~0ull;
+        t = cur ? tn : ~0ull;
+        rb = rb == 2 ? 0 : rb + 1;
     }
+    cp_async_wait_all();
 }
 
 __global__ void set_status_kernel(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
@@ -469,7 +664,9 @@ __global__ void set_status_kernel(uint32_t *status, uint32_t bits) { atomicOr(st
 // ------------------------------------------------------------- workspace --
 
 // Workspace layout: [0,4) status word, [256,264) tile counter, [512, ...)
-// count descriptors (8 bytes per tile) then sum descriptors (8 bytes per tile).
+// tile descriptors (16 bytes per tile), group accumulators (16 bytes per
+// group), group descriptors (16 bytes per group).  Everything past the status
+// word is cleared before each launch.
 constexpr size_t kWsCounter = 256;
 constexpr size_t kWsDesc = 512;
 
@@ -495,7 +692,12 @@ std::map<std::pair<int, uintptr_t>, Workspace> g_ws;
 std::map<std::pair<int, uintptr_t>, HostBuffers> g_hb;
 std::map<int, DeviceInfo> g_dev;
 
-size_t ws_bytes(uint64_t ntiles) { return kWsDesc + 16 * static_cast<size_t>(ntiles); }
+uint64_t num_groups(uint64_t ntiles) { return (ntiles + kGroup - 1) / kGroup; }
+
+size_t ws_bytes(uint64_t ntiles)
+{
+    return kWsDesc + 16 * static_cast<size_t>(ntiles) + 32 * static_cast<size_t>(num_groups(ntiles));
+}
 
 bool capturing(cudaStream_t s)
 {
@@ -578,8 +780,9 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     p.ntiles = ntiles;
     p.base = a & ~static_cast<uintptr_t>(15);
     p.ctr = reinterpret_cast<unsigned long long *>(w->ptr + kWsCounter);
-    p.dcnt = reinterpret_cast<uint64_t *>(w->ptr + kWsDesc);
-    p.dsum = p.dcnt + ntiles;
+    p.tdesc = reinterpret_cast<uint64_t *>(w->ptr + kWsDesc);
+    p.gacc = reinterpret_cast<unsigned long long *>(p.tdesc + 2 * ntiles);
+    p.gdesc = reinterpret_cast<uint64_t *>(p.gacc + 2 * num_groups(ntiles));
     p.status = status;
     p.prev = prev;
     const uint64_t grid = std::min<uint64_t>(ntiles, static_cast<uint64_t>(di.sms) * di.occ[delta]);
