@@ -13,19 +13,21 @@
 //     (high bit clear) lies inside it; the 16 bytes before the tile are
 //     staged too, so an integer that starts up to four bytes earlier is
 //     assembled by the tile holding its terminator.
-//   * Tiles are grouped into chunks of kChunkTiles (32 MiB).  Launch c counts
-//     the tiles of chunk c and decodes the tiles of chunk c-1; CTAs alternate
-//     between the two roles, one tile per CTA.
+//   * Tiles are grouped into chunks of kChunkTiles (8 MiB).  Persistent CTAs
+//     take tickets; ticket k counts tile k and, after the first chunk and a
+//     slack, also decodes tile k - (kChunkTiles + kLeadSlack), so a tile is
+//     decoded a little over one chunk after it was counted.
 //   * (a) count: a CTA forms the terminator mask of its tile (the GPU
 //     counterpart of pmovmskb, Sec. 3/4), its terminator count and, in delta
 //     mode, the sum of its gaps; publishes both in the tile's descriptor and
 //     adds them to its group's accumulators (32 tiles per group).  The CTA
 //     that finishes a chunk last scans the chunk's group aggregates into
-//     group prefixes.  This pass checks the data-error contract.
-//   * (b, c) decode: a CTA's tile prefix is its group prefix plus the
-//     aggregates of the earlier tiles of its group (one L2 round trip).  It
-//     re-reads its tile -- from L2: the count pass of the launch before read
-//     it shortly before -- and assembles every integer branch-free
+//     group prefixes and raises the chunk's ready flag.  This pass checks the
+//     data-error contract.
+//   * (b, c) decode: once its chunk is ready, a CTA's tile prefix is its
+//     group prefix plus the aggregates of the earlier tiles of its group (one
+//     L2 round trip).  It re-reads its tile -- from L2: the count read it one
+//     chunk earlier -- and assembles every integer branch-free
 //     from the (up to) five bytes ending at its terminator.  The work splits
 //     by the longest code, the GPU counterpart of the paper's case split on
 //     the 12-bit mask (Sec. 4): tiles of one-byte integers only (class A)
@@ -35,9 +37,9 @@
 //     wrap-around, seeded with `prev`), are staged in shared memory at their
 //     rank shifted so that output quads are 16-byte aligned, and leave with
 //     16-byte stores clamped to [0, n).
-//   * Launches are stream ordered, so launch c sees everything launch c-1
-//     wrote.
-// No CTA ever waits on another CTA inside a launch.
+// The only waits are on chunk ready flags raised by CTAs holding earlier
+// tickets (counting never waits, except a chunk's last CTA on the chunk
+// before), so every wait ends; each is bounded by the global timer.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,11 +59,13 @@ constexpr int kTile = kThreads * kBPT;        // input bytes per tile (4 KiB)
 constexpr int kHalo = 16;                     // bytes staged before the tile
 constexpr int kRoundVals = kThreads * 4;      // values per copy-out round
 constexpr int kGroup = 32;                    // tiles per group
-constexpr uint64_t kChunkTiles = 8192;        // tiles per chunk (32 MiB)
-constexpr int kGroupsPerChunk = static_cast<int>(kChunkTiles / kGroup);   // 256
+constexpr uint64_t kChunkTiles = 2048;        // tiles per chunk (8 MiB)
+constexpr int kGroupsPerChunk = static_cast<int>(kChunkTiles / kGroup);   // 64
 constexpr int kByteBuf = kHalo + kTile + 16;
 constexpr int kValBuf = kTile + 16;
-static_assert(kGroupsPerChunk == kThreads, "the chunk scan uses one thread per group");
+constexpr uint64_t kLeadSlack = 1024;         // extra tickets between a chunk's last count and first decode
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+static_assert(kGroupsPerChunk <= kThreads && kGroupsPerChunk % 32 == 0, "chunk scan: one thread per group");
 
 enum : uint32_t { kClassA = 0, kClassB = 1, kClassC = 2 };
 
@@ -77,11 +81,11 @@ struct Params {
     uint64_t *gpre;            // per group: exclusive prefix count, running x before it
     uint64_t *cnext;           // per chunk: prefix count and running x after it
     unsigned int *cdone;       // per chunk: CTAs that finished counting
+    unsigned int *cready;      // per chunk: group prefixes published
+    unsigned long long *ctr;   // work tickets
     uint32_t *status;          // data-error bits
     uint32_t prev;             // x_0 for differential decoding
-    uint64_t count_chunk;      // chunk counted by this launch (if any)
-    uint64_t c0, c1;           // tiles counted by this launch: [c0, c1)
-    uint64_t d0, d1;           // tiles decoded by this launch: [d0, d1)
+    uint64_t lead;             // tickets [0, lead) only count; ticket k >= lead also decodes k - lead
 };
 
 // ---------------------------------------------------------------- helpers --
@@ -105,9 +109,58 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 
-__device__ __forceinline__ void cp_async_wait_all()
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most one committed group of this thread is still in flight.
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Fire-and-forget increment with release semantics: every global write this
+// thread made before is visible to whoever observes the new value.
+__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v)
 {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// One thread waits (acquire) until *flag != 0, bounded by the global timer;
+// on expiry the status word gets VBYTE_ERR_TIMEOUT and the caller carries on.
+__device__ __forceinline__ void spin_flag(const unsigned int *flag, uint32_t *status)
+{
+    uint64_t t0 = 0;
+    for (int spin = 0; ld_acquire_u32(flag) == 0u; ++spin) {
+        const uint64_t now = global_ns();
+        if (t0 == 0) t0 = now;
+        if (now - t0 > kWaitLimitNs) {
+            atomicOr(status, VBYTE_ERR_TIMEOUT);
+            break;
+        }
+        if (spin > 4) __nanosleep(200);
+    }
+}
+
+// Thread 0 waits until *flag != 0 (bounded by the global timer; on expiry the
+// status word gets VBYTE_ERR_TIMEOUT and the caller carries on), then the CTA
+// syncs.  The flag is set after __threadfence() by a CTA that holds a ticket
+// taken before the waiter's, so the wait always ends.
+__device__ __forceinline__ void wait_flag(const unsigned int *flag, uint32_t *status)
+{
+    if (threadIdx.x == 0) spin_flag(flag, status);
+    __syncthreads();
 }
 
 // Bit i of the result is 1 iff byte i of w has its high bit clear (a
@@ -251,8 +304,8 @@ __device__ __forceinline__ uint32_t slice_valid(uintptr_t va, uintptr_t lo, uint
 // (zero before tile 0, i.e. terminators of earlier, uncounted integers; for
 // t > 0 they always lie inside the stream).  Whole slices travel with
 // cp.async; the ragged first and last slices of the stream are loaded byte
-// by byte.  Returns after the copies have landed and the CTA has synced.
-__device__ __forceinline__ void stage_tile(const Params &p, uint64_t t, int tid, uint8_t *bytes)
+// by byte.  The caller commits, waits for the copies and syncs the CTA.
+__device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid, uint8_t *bytes)
 {
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
@@ -280,8 +333,6 @@ __device__ __forceinline__ void stage_tile(const Params &p, uint64_t t, int tid,
     }
     if (tid == kThreads - 1)
         *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
-    cp_async_wait_all();
-    __syncthreads();
 }
 
 // Terminator masks of tid's 16-byte slice of a staged tile.
@@ -305,6 +356,29 @@ __device__ __forceinline__ SliceMasks slice_masks(const uint8_t *bt, int tid, bo
     return m;
 }
 
+// Sum of the values whose terminators lie in a thread's slice, for a thread
+// whose codes are at most two bytes (every continuation byte is followed by
+// its terminator): the 7-bit payloads of the bytes of those values plus 127
+// times each two-byte value's high byte.  The byte before the slice belongs
+// to my first value when it is a continuation byte; my last byte belongs to
+// the next slice's first value when it is one.
+__device__ __forceinline__ uint32_t sum_le2_fast(uint4 w, uint32_t wprev)
+{
+    const uint32_t c4[4] = {w.x, w.y, w.z, w.w};
+    uint32_t s = 0, hi = 0, wp = wprev;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t c = c4[j];
+        s = __dp4a(c & 0x7F7F7F7Fu, 0x01010101u, s);
+        const uint32_t sh = __funnelshift_l(wp, c, 8);      // byte i: the byte before byte i
+        hi = __dp4a(c & prmt(sh, 0u, 0xBA98u), 0x01010101u, hi);
+        wp = c;
+    }
+    if (wprev & 0x80000000u) s += (wprev >> 24) & 0x7Fu;   // my first value started earlier
+    if (w.w & 0x80000000u) s -= (w.w >> 24) & 0x7Fu;       // my last byte starts the next value
+    return s + 127u * hi;
+}
+
 // Per-thread count and (delta) value sum of the integers ending in its slice.
 template <bool kDelta>
 __device__ __forceinline__ void slice_count_sum(const SliceMasks &m, const uint32_t *sw, int tid, bool interior,
@@ -319,7 +393,7 @@ __device__ __forceinline__ void slice_count_sum(const SliceMasks &m, const uint3
         if (!notA) {
             vsum = byte_sum4(m.w);
         } else if (!notB) {
-            vsum = sum_le2(m.w, m.wprev, m.tc);
+            vsum = interior ? sum_le2_fast(m.w, m.wprev) : sum_le2(m.w, m.wprev, m.tc);
         } else {
             assemble_all(sw, tid, m.tl, m.t20, m.tc, [&](uint32_t v) { vsum += v; });
         }
@@ -327,42 +401,62 @@ __device__ __forceinline__ void slice_count_sum(const SliceMasks &m, const uint3
 }
 
 struct Shared {
-    uint8_t bytes[kByteBuf];
+    uint8_t cbytes[2][kByteBuf];     // staged tiles to count (double-buffered)
+    uint8_t dbytes[2][kByteBuf];     // staged tiles to decode (double-buffered)
     uint32_t vals[kValBuf];          // decode: staged values at rank + sh
-    uint32_t wcnt[kWarps];
+    uint32_t wcnt[kWarps];           // count: per-warp partials
     uint32_t wsum[kWarps];
+    uint32_t dcnt[kWarps];           // decode: per-warp partials
+    uint32_t dsum[kWarps];
     unsigned long long R0;           // decode: values before the tile
     uint32_t S0;                     // decode: running x before the tile
-    uint32_t last;                   // count: this CTA finished its chunk
     unsigned long long gsc[kWarps];  // chunk scan: per-warp count totals
     uint32_t gss[kWarps];            // chunk scan: per-warp sum totals
+    unsigned long long tnext;        // the ticket after the prefetched one
+    unsigned long long pR0[2];       // prefetched tile prefixes (per buffer)
+    uint32_t pS0[2];
+    uint32_t pok[2];                 // prefetch valid
 };
 
 // --------------------------------------------------------------- counting --
 
 template <bool kDelta>
-__device__ void count_tile(const Params &p, uint64_t t, Shared &S)
+__device__ void count_tile(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
-    stage_tile(p, t, tid, S.bytes);
 
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
     const bool interior = tstart >= lo && tstart + kTile <= hi;
-    const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
-    const SliceMasks m = slice_masks(S.bytes, tid, interior, va, lo, hi);
-    uint32_t cnt, vsum;
-    bool notB;
-    slice_count_sum<kDelta>(m, reinterpret_cast<const uint32_t *>(S.bytes), tid, interior, cnt, vsum, notB);
-    // the data-error contract, checked once per byte here
-    const uint32_t c20 = ~m.t20 & 0xFFFFFu;
-    if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
-        atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
-    if (t == p.ntiles - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((m.tl >> (hi - 1 - va)) & 1u))
-        atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+    const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
+    const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
+    uint32_t cnt, vsum = 0;
+    if (interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u)) {
+        // one-byte integers only
+        cnt = kBPT;
+        if (kDelta) vsum = byte_sum4(w0);
+    } else {
+        const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+        const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
+        cnt = __popc(m.tc);
+        // the data-error contract, checked once per byte here
+        const uint32_t c20 = ~m.t20 & 0xFFFFFu;   // continuation bytes
+        if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
+            atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
+        if (t == p.ntiles - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((m.tl >> (hi - 1 - va)) & 1u))
+            atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+        if (kDelta) {
+            if (interior && !(c20 & (c20 << 1) & 0xFFFF8u)) {
+                vsum = sum_le2_fast(m.w, m.wprev);
+            } else {
+                assemble_all(reinterpret_cast<const uint32_t *>(bytes), tid, m.tl, m.t20, m.tc,
+                             [&](uint32_t v) { vsum += v; });
+            }
+        }
+    }
 
     const uint32_t wc = __reduce_add_sync(~0u, cnt);
     const uint32_t wsm = kDelta ? __reduce_add_sync(~0u, vsum) : 0u;
@@ -372,40 +466,63 @@ __device__ void count_tile(const Params &p, uint64_t t, Shared &S)
     }
     __syncthreads();
     if (warp == 0) {
-        const uint32_t c = lane < kWarps ? S.wcnt[lane] : 0u;
-        const uint32_t sm = lane < kWarps ? S.wsum[lane] : 0u;
-        const uint32_t tcnt = __reduce_add_sync(~0u, c);
-        const uint32_t tsum = __reduce_add_sync(~0u, sm);
+        const uint32_t cw = lane < kWarps ? S.wcnt[lane] : 0u;
+        const uint32_t sw = lane < kWarps ? S.wsum[lane] : 0u;
+        const uint32_t tcnt = __reduce_add_sync(~0u, cw);
+        const uint32_t tsum = __reduce_add_sync(~0u, sw);
         if (lane == 0) {
             const uint64_t g = t / kGroup;
             p.tdesc[2 * t] = tcnt;
             p.tdesc[2 * t + 1] = tsum;
             atomicAdd(p.gagg + 2 * g, static_cast<unsigned long long>(tcnt));
             if (kDelta) atomicAdd(p.gagg + 2 * g + 1, static_cast<unsigned long long>(tsum));
-            __threadfence();
-            const unsigned ntile = static_cast<unsigned>(p.c1 - p.c0);
-            S.last = atomicAdd(p.cdone + p.count_chunk, 1u) == ntile - 1;
+            red_release_add(p.cdone + t / kChunkTiles, 1u);
         }
     }
-    __syncthreads();
-    if (!S.last) return;
+}
 
-    // ---- the chunk's last CTA: group aggregates -> group prefixes (the
-    // running totals before this chunk come from the previous launch, which
-    // has completed: launches are stream ordered)
-    __threadfence();
-    const uint64_t g0 = p.c0 / kGroup;
-    const uint64_t g1 = (p.c1 + kGroup - 1) / kGroup;
+// The group prefixes of chunk c, computed by the CTA that decodes the chunk's
+// first tile: wait until every tile of the chunk has been counted and the
+// chunk before has been scanned (both by CTAs holding earlier tickets), scan
+// the chunk's group aggregates, publish, and raise the chunk's ready flag.
+template <bool kDelta>
+__device__ void chunk_scan(const Params &p, uint64_t c, Shared &S)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const uint64_t c0 = c * kChunkTiles;
+    const uint64_t c1 = (c0 + kChunkTiles < p.ntiles) ? c0 + kChunkTiles : p.ntiles;
+    if (tid == 0) {
+        uint64_t t0 = 0;
+        for (int spin = 0;; ++spin) {
+            unsigned int done;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(done) : "l"(p.cdone + c) : "memory");
+            if (done >= static_cast<unsigned int>(c1 - c0)) break;
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            if (now - t0 > kWaitLimitNs) {
+                atomicOr(p.status, VBYTE_ERR_TIMEOUT);
+                break;
+            }
+            if (spin > 4) __nanosleep(200);
+        }
+    }
     uint64_t pc = 0;
     uint32_t ps = p.prev;
-    if (p.count_chunk > 0) {
-        pc = *reinterpret_cast<volatile uint64_t *>(p.cnext + 2 * (p.count_chunk - 1));
-        ps = static_cast<uint32_t>(*reinterpret_cast<volatile uint64_t *>(p.cnext + 2 * (p.count_chunk - 1) + 1));
+    if (c > 0) {
+        wait_flag(p.cready + (c - 1), p.status);
+        pc = *reinterpret_cast<volatile uint64_t *>(p.cnext + 2 * (c - 1));
+        ps = static_cast<uint32_t>(*reinterpret_cast<volatile uint64_t *>(p.cnext + 2 * (c - 1) + 1));
+    } else {
+        __syncthreads();
     }
-    const uint64_t g = g0 + tid;   // one group per thread
+    const uint64_t g0 = c * kGroupsPerChunk;
+    const uint64_t ng = (p.ntiles + kGroup - 1) / kGroup;
+    const uint64_t g = g0 + tid;
     uint64_t ac = 0;
     uint32_t as = 0;
-    if (g < g1) {
+    if (tid < kGroupsPerChunk && g < ng) {
         ac = *reinterpret_cast<volatile unsigned long long *>(p.gagg + 2 * g);
         as = static_cast<uint32_t>(*reinterpret_cast<volatile unsigned long long *>(p.gagg + 2 * g + 1));
     }
@@ -419,27 +536,72 @@ __device__ void count_tile(const Params &p, uint64_t t, Shared &S)
     uint64_t wc0 = 0, tc_all = 0;
     uint32_t ws0 = 0, ts_all = 0;
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) {
+    for (int q = 0; q < kGroupsPerChunk / 32; ++q) {
         wc0 += (q < warp) ? S.gsc[q] : 0ull;
         ws0 += (q < warp) ? S.gss[q] : 0u;
         tc_all += S.gsc[q];
         ts_all += S.gss[q];
     }
-    if (g < g1) {
+    if (tid < kGroupsPerChunk && g < ng) {
         p.gpre[2 * g] = pc + wc0 + ic - ac;
         p.gpre[2 * g + 1] = static_cast<uint32_t>(ps + ws0 + is - as);
     }
+    __syncthreads();
     if (tid == 0) {
-        p.cnext[2 * p.count_chunk] = pc + tc_all;
-        p.cnext[2 * p.count_chunk + 1] = static_cast<uint32_t>(ps + ts_all);
-        if (p.c1 == p.ntiles && pc + tc_all != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        p.cnext[2 * c] = pc + tc_all;
+        p.cnext[2 * c + 1] = static_cast<uint32_t>(ps + ts_all);
+        if (c1 == p.ntiles && pc + tc_all != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        __threadfence();
+        *reinterpret_cast<volatile unsigned int *>(p.cready + c) = 1u;
     }
+    __syncthreads();
 }
 
 // --------------------------------------------------------------- decoding --
 
+// Warp 0's loads of a tile's prefix: the group prefix (lane 0) and the
+// aggregates of the earlier tiles of the group (one per lane).
+struct PrefixLoads {
+    uint64_t pa, pb, ga, gb;
+    bool ok;   // loaded after the tile's chunk was seen ready (warp-uniform)
+};
+
+__device__ __forceinline__ PrefixLoads load_prefix(const Params &p, uint64_t t, int lane)
+{
+    PrefixLoads r;
+    r.pa = r.pb = r.ga = r.gb = 0;
+    r.ok = true;
+    const uint64_t g = t / kGroup;
+    const uint64_t j = g * kGroup + lane;
+    if (j < t) {
+        r.pa = *reinterpret_cast<const volatile uint64_t *>(p.tdesc + 2 * j);
+        r.pb = *reinterpret_cast<const volatile uint64_t *>(p.tdesc + 2 * j + 1);
+    }
+    if (lane == 0) {
+        r.ga = *reinterpret_cast<const volatile uint64_t *>(p.gpre + 2 * g);
+        r.gb = *reinterpret_cast<const volatile uint64_t *>(p.gpre + 2 * g + 1);
+    }
+    return r;
+}
+
+// Warp 0: if tile t's chunk is already published (and t is not the chunk's
+// first tile, whose CTA scans the chunk), issue its prefix loads now, to be
+// consumed an iteration later.
+__device__ __forceinline__ PrefixLoads try_prefetch_prefix(const Params &p, uint64_t t, int lane)
+{
+    PrefixLoads r;
+    r.pa = r.pb = r.ga = r.gb = 0;
+    r.ok = false;
+    if (t >= p.ntiles || t % kChunkTiles == 0) return r;
+    unsigned int ready = 0;
+    if (lane == 0) ready = ld_acquire_u32(p.cready + t / kChunkTiles);
+    ready = __shfl_sync(~0u, ready, 0);   // the warp sync orders lane 0's acquire before the loads
+    if (!ready) return r;
+    return load_prefix(p, t, lane);
+}
+
 template <bool kDelta>
-__device__ void decode_tile(const Params &p, uint64_t t, Shared &S)
+__device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes, int b)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -448,34 +610,43 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S)
     const uintptr_t hi = lo + p.nbytes;
     const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
 
-    // tile prefix: group prefix + the earlier tiles of the group (one round trip)
-    uint64_t pa = 0, pb = 0, ga = 0, gb = 0;
-    const uint64_t g = t / kGroup;
-    if (warp == 0) {
-        const uint64_t j = g * kGroup + lane;
-        if (j < t) {
-            pa = p.tdesc[2 * j];
-            pb = p.tdesc[2 * j + 1];
-        }
-        if (lane == 0) {
-            ga = p.gpre[2 * g];
-            gb = p.gpre[2 * g + 1];
-        }
+    // tile prefix: group prefix + the earlier tiles of the group, once the
+    // chunk's group prefixes are published -- usually prefetched an iteration
+    // ago into S.pR0 / S.pS0; otherwise warp 0 loads it now and folds it into
+    // S.R0 / S.S0 before the CTA's second barrier.
+    PrefixLoads pre;
+    pre.pa = pre.pb = pre.ga = pre.gb = 0;
+    const bool prefetched = S.pok[b] != 0u && t % kChunkTiles != 0;
+    if (t % kChunkTiles == 0) {
+        chunk_scan<kDelta>(p, t / kChunkTiles, S);
+        if (warp == 0) pre = load_prefix(p, t, lane);
+    } else if (warp == 0 && !prefetched) {
+        if (lane == 0) spin_flag(p.cready + t / kChunkTiles, p.status);
+        __syncwarp();
+        pre = load_prefix(p, t, lane);
     }
-    stage_tile(p, t, tid, S.bytes);
-    if (warp == 0) {
-        const uint64_t ec = warp_sum64(pa);
-        const uint64_t es = warp_sum64(pb & 0xFFFFFFFFull);
-        if (lane == 0) {
-            S.R0 = ga + ec;
-            S.S0 = static_cast<uint32_t>(gb + es);
+    auto fold_prefix = [&]() {
+        if (warp == 0) {
+            if (prefetched) {
+                if (lane == 0) {
+                    S.R0 = S.pR0[b];
+                    S.S0 = S.pS0[b];
+                }
+            } else {
+                const uint64_t ec = warp_sum64(pre.pa);
+                const uint64_t es = warp_sum64(pre.pb & 0xFFFFFFFFull);
+                if (lane == 0) {
+                    S.R0 = pre.ga + ec;
+                    S.S0 = static_cast<uint32_t>(pre.gb + es);
+                }
+            }
         }
-    }
+    };
 
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
     const bool interior = tstart >= lo && tstart + kTile <= hi;
-    const uint4 w0 = *reinterpret_cast<const uint4 *>(S.bytes + kHalo + tid * kBPT);
-    const uint32_t wp0 = reinterpret_cast<const uint32_t *>(S.bytes)[(kHalo + tid * kBPT) / 4 - 1];
+    const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
+    const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
     const bool mineA = interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u);
 
     if (!__syncthreads_or(!mineA)) {
@@ -483,14 +654,18 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S)
         // my byte i.  I rebuild the 3 values before my bytes as well, so every
         // aligned output quad that starts among my ranks is complete here.
         uint32_t base = 0;
+        uint32_t mine = 0, incs = 0;
         if (kDelta) {
-            const uint32_t mine = byte_sum4(w0);
-            const uint32_t incs = warp_incl_scan(mine, lane);
-            if (lane == 31) S.wsum[warp] = incs;
-            __syncthreads();
+            mine = byte_sum4(w0);
+            incs = warp_incl_scan(mine, lane);
+            if (lane == 31) S.dsum[warp] = incs;
+        }
+        fold_prefix();
+        __syncthreads();
+        if (kDelta) {
             uint32_t wsbase = 0;
 #pragma unroll
-            for (int q = 0; q < kWarps; ++q) wsbase += (q < warp) ? S.wsum[q] : 0u;
+            for (int q = 0; q < kWarps; ++q) wsbase += (q < warp) ? S.dsum[q] : 0u;
             base = S.S0 + wsbase + incs - mine;
         }
         const unsigned long long R0 = S.R0;
@@ -570,24 +745,25 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S)
 
     // ---- general tiles: ranks and (delta) gap offsets by block scans
     const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
-    const uint32_t *const sw = reinterpret_cast<const uint32_t *>(S.bytes);
-    const SliceMasks m = slice_masks(S.bytes, tid, interior, va, lo, hi);
+    const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
+    const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
     uint32_t cnt, vsum;
     bool notB;
     slice_count_sum<kDelta>(m, sw, tid, interior, cnt, vsum, notB);
     const uint32_t inc = warp_incl_scan(cnt, lane);
     const uint32_t incs = kDelta ? warp_incl_scan(vsum, lane) : 0u;
     if (lane == 31) {
-        S.wcnt[warp] = inc;
-        S.wsum[warp] = incs;
+        S.dcnt[warp] = inc;
+        S.dsum[warp] = incs;
     }
+    fold_prefix();
     __syncthreads();
     uint32_t wbase = 0, wsbase = 0, tcnt = 0;
 #pragma unroll
     for (int q = 0; q < kWarps; ++q) {
-        const uint32_t c = S.wcnt[q];
+        const uint32_t c = S.dcnt[q];
         wbase += (q < warp) ? c : 0u;
-        if (kDelta) wsbase += (q < warp) ? S.wsum[q] : 0u;
+        if (kDelta) wsbase += (q < warp) ? S.dsum[q] : 0u;
         tcnt += c;
     }
     const unsigned long long R0 = S.R0;
@@ -653,43 +829,75 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S)
 
 // ----------------------------------------------------------------- kernel --
 //
-// One launch: count the tiles [c0, c1) of chunk count_chunk and decode the
-// tiles [d0, d1) of the chunk before it, one tile per CTA, alternating roles
-// so that the HBM reads of counting and the writes of decoding overlap.
+// Persistent CTAs take tickets.  Ticket k counts tile k and, from ticket
+// `lead` (one chunk plus kLeadSlack) on, also decodes tile k - lead, whose
+// chunk was counted by tickets at least kLeadSlack earlier: a tile is read
+// from HBM by its count and again, about 12 MiB of input later, from L2 by
+// its decode.
 
 template <bool kDelta>
-__global__ void __launch_bounds__(kThreads) interval_kernel(const Params p)
+__global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
 {
     __shared__ __align__(16) Shared S;
-    const uint64_t nc = p.c1 - p.c0;
-    const uint64_t nd = p.d1 - p.d0;
-    const uint64_t mboth = nc < nd ? nc : nd;
-    const uint64_t b = blockIdx.x;
-    bool counting;
-    uint64_t idx;
-    if (b < 2 * mboth) {
-        counting = (b & 1) == 0;
-        idx = b >> 1;
-    } else {
-        counting = nc > mboth;
-        idx = mboth + (b - 2 * mboth);
+    const int tid = threadIdx.x;
+    const uint64_t total = p.ntiles + p.lead;
+    // Tickets run two ahead: while ticket k is processed, the tiles of the next
+    // ticket are in flight to the other buffers and the one after is taken.
+    if (tid == 0) {
+        S.R0 = atomicAdd(p.ctr, 1ull);
+        S.tnext = atomicAdd(p.ctr, 1ull);
     }
-    if (counting) {
-        count_tile<kDelta>(p, p.c0 + idx, S);
-    } else {
-        decode_tile<kDelta>(p, p.d0 + idx, S);
+    __syncthreads();
+    uint64_t k = S.R0;
+    uint64_t kn = S.tnext;
+    auto stage = [&](uint64_t tk, int b) {
+        if (tk < p.ntiles) issue_stage(p, tk, tid, S.cbytes[b]);
+        if (tk >= p.lead && tk < total) issue_stage(p, tk - p.lead, tid, S.dbytes[b]);
+        cp_async_commit();
+    };
+    stage(k, 0);
+    if (tid == 0) S.pok[0] = 0u;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int b = 0; k < total; b ^= 1) {
+        unsigned long long knn = 0;
+        if (tid == 0) knn = atomicAdd(p.ctr, 1ull);
+        stage(kn, b ^ 1);
+        // warp 0 issues the prefix loads of kn's decode tile now (if its chunk is
+        // ready) and folds them into S.pR0 / S.pS0 at the end of the iteration
+        PrefixLoads pn;
+        pn.pa = pn.pb = pn.ga = pn.gb = 0;
+        pn.ok = false;
+        if (warp == 0 && kn >= p.lead && kn < total) pn = try_prefetch_prefix(p, kn - p.lead, lane);
+        cp_async_wait_prior();
+        __syncthreads();   // ticket k's tiles are staged
+        if (k < p.ntiles) count_tile<kDelta>(p, k, S, S.cbytes[b]);
+        if (k >= p.lead) decode_tile<kDelta>(p, k - p.lead, S, S.dbytes[b], b);
+        if (warp == 0) {
+            const uint64_t ec = warp_sum64(pn.pa);
+            const uint64_t es = warp_sum64(pn.pb & 0xFFFFFFFFull);
+            if (lane == 0) {
+                S.pR0[b ^ 1] = pn.ga + ec;
+                S.pS0[b ^ 1] = static_cast<uint32_t>(pn.gb + es);
+                S.pok[b ^ 1] = pn.ok ? 1u : 0u;
+                S.tnext = knn;
+            }
+        }
+        __syncthreads();   // buffers b are free; the next ticket is known
+        k = kn;
+        kn = S.tnext;
     }
+    cp_async_wait_all();
 }
 
 __global__ void set_status_kernel(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
 
 // ------------------------------------------------------------- workspace --
 
-// Workspace layout: [0,4) status word; [256, ...) per chunk two words of
-// cnext, then per chunk one word of cdone, then per group two words of gagg
-// and two of gpre, then per tile two words of tdesc.  The chunk and gagg
-// areas are cleared before each decode; gpre and tdesc are written before
-// they are read.
+// Workspace layout: [0,4) status word; [256, ...) the ticket counter, per
+// chunk two words of cnext and one each of cdone and cready, then per group
+// two words of gagg and two of gpre, then per tile two words of tdesc.  All
+// but gpre and tdesc (written before they are read) is cleared before each
+// decode.
 constexpr size_t kWsHead = 256;
 
 struct Workspace {
@@ -710,7 +918,7 @@ std::map<std::pair<int, uintptr_t>, HostBuffers> g_hb;
 
 struct Layout {
     uint64_t ntiles, ngroups, nchunks;
-    size_t cnext, cdone, gagg, gpre, tdesc, total, clear;
+    size_t ctr, cnext, cdone, cready, gagg, gpre, tdesc, total, clear;
 };
 
 Layout layout(uint64_t ntiles)
@@ -719,13 +927,15 @@ Layout layout(uint64_t ntiles)
     L.ntiles = ntiles;
     L.ngroups = (ntiles + kGroup - 1) / kGroup;
     L.nchunks = (ntiles + kChunkTiles - 1) / kChunkTiles;
-    L.cnext = kWsHead;
+    L.ctr = kWsHead;
+    L.cnext = L.ctr + 16;
     L.cdone = L.cnext + 16 * L.nchunks;
-    L.gagg = (L.cdone + 4 * L.nchunks + 15) / 16 * 16;
+    L.cready = L.cdone + 4 * L.nchunks;
+    L.gagg = (L.cready + 4 * L.nchunks + 15) / 16 * 16;
     L.gpre = L.gagg + 16 * L.ngroups;
     L.tdesc = L.gpre + 16 * L.ngroups;
     L.total = L.tdesc + 16 * ntiles;
-    L.clear = L.gpre - L.cnext;   // cnext, cdone and gagg
+    L.clear = L.gpre - L.ctr;   // ticket counter, chunk words and gagg
     return L;
 }
 
@@ -764,11 +974,27 @@ int get_workspace(cudaStream_t s, size_t need, Workspace **out)
     return VBYTE_OK;
 }
 
-template <bool kDelta>
-cudaError_t launch_interval(const Params &p, uint64_t blocks, cudaStream_t s)
+struct DeviceInfo {
+    int sms = 0;
+    int occ[2] = {0, 0};
+};
+std::map<int, DeviceInfo> g_dev;
+
+int device_info(DeviceInfo *di)
 {
-    interval_kernel<kDelta><<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(p);
-    return cudaGetLastError();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VBYTE_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceInfo &d = g_dev[dev];
+    if (d.sms == 0) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return VBYTE_ECUDA;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], decode_kernel<false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], decode_kernel<true>, kThreads, 0);
+        for (int &o : d.occ) o = std::max(o, 1);
+    }
+    *di = d;
+    return VBYTE_OK;
 }
 
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
@@ -788,7 +1014,10 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
         set_status_kernel<<<1, 1, 0, s>>>(status, VBYTE_ERR_COUNT_MISMATCH);
         return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
     }
-    if (cudaMemsetAsync(w->ptr + L.cnext, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
+    DeviceInfo di;
+    rc = device_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    if (cudaMemsetAsync(w->ptr + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
     Params p;
     p.in = in;
     p.nbytes = nbytes;
@@ -801,22 +1030,17 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     p.gpre = reinterpret_cast<uint64_t *>(w->ptr + L.gpre);
     p.cnext = reinterpret_cast<uint64_t *>(w->ptr + L.cnext);
     p.cdone = reinterpret_cast<unsigned int *>(w->ptr + L.cdone);
+    p.cready = reinterpret_cast<unsigned int *>(w->ptr + L.cready);
+    p.ctr = reinterpret_cast<unsigned long long *>(w->ptr + L.ctr);
     p.status = status;
     p.prev = prev;
-    for (uint64_t c = 0; c <= L.nchunks; ++c) {
-        p.count_chunk = c;
-        p.c0 = std::min<uint64_t>(c * kChunkTiles, ntiles);
-        p.c1 = std::min<uint64_t>((c + 1) * kChunkTiles, ntiles);
-        p.d0 = c > 0 ? (c - 1) * kChunkTiles : 0;
-        p.d1 = c > 0 ? std::min<uint64_t>(c * kChunkTiles, ntiles) : 0;
-        const uint64_t blocks = (p.c1 - p.c0) + (p.d1 - p.d0);
-        const cudaError_t e = delta ? launch_interval<true>(p, blocks, s) : launch_interval<false>(p, blocks, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return VBYTE_ECUDA;
-        }
-    }
-    return VBYTE_OK;
+    p.lead = std::min<uint64_t>(kChunkTiles + kLeadSlack, ntiles);
+    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
+    if (delta)
+        decode_kernel<true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+    else
+        decode_kernel<false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
 }  // namespace vbk
