@@ -50,6 +50,7 @@ extern "C" {
 #define VBYTE_EINVAL 1 /* null pointer with a nonzero size, misaligned output */
 #define VBYTE_ECUDA 2  /* a CUDA runtime call or kernel launch failed */
 #define VBYTE_ENOMEM 3 /* workspace could not be grown */
+#define VBYTE_ETOOBIG 4 /* input above VBYTE_NOALLOC_MAX_BYTES (vbyte_decode_noalloc) */
 
 /* ---- data-error bits of the per-stream status word --------------------- */
 /* A run of five or more consecutive bytes with the high bit set: Algorithm 1
@@ -114,6 +115,43 @@ int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
  * is still read with vbyte_get_status(). */
 int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out,
                       size_t n, int delta, uint32_t prev, void *stream);
+
+/* ---- decoding without allocation ---------------------------------------- */
+
+/* Largest input vbyte_decode_noalloc accepts: 128 MiB (about 2^27 one-byte
+ * integers).  Its scratch is a fixed device array of about 576 KiB. */
+#define VBYTE_NOALLOC_MAX_BYTES ((size_t)128 << 20)
+
+/* The paper has no counterpart to this entry point: it is a deployment form
+ * of vbyte_decode / vbyte_decode_delta for callers that cannot allocate
+ * device memory -- a process whose device memory is all owned by another
+ * allocator (a framework's caching allocator, an arena set aside at
+ * start-up), or a latency-bound serving loop that cannot take the implicit
+ * device synchronisation of cudaMalloc/cudaFree or an out-of-memory failure
+ * in the middle of a request.  It decodes exactly as vbyte_decode (delta = 0)
+ * or vbyte_decode_delta (delta != 0, from prev) and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Scratch: the look-back descriptors live in one file-scope __device__ array
+ * in the library, shared by every call on a device.  The first call on each
+ * device (with that device current) looks up that array's address with
+ * cudaGetSymbolAddress and the device's SM count; make that first call
+ * before any stream capture.  Each call clears the part of the array that
+ * must start at zero (cudaMemsetAsync on `stream`) before its kernel.
+ * Calls whose work overlaps on the GPU -- on two streams, or from two host
+ * threads without ordering -- race on the shared array and give unspecified
+ * output: order them (one stream, or events).
+ *
+ * d_status: a caller-owned, 4-byte-aligned device word into which data
+ * errors are OR-ed (VBYTE_ERR_* bits; never cleared by the library), or NULL
+ * to discard them.  vbyte_get_status() does not see these errors.
+ *
+ * Returns VBYTE_ETOOBIG if nbytes > VBYTE_NOALLOC_MAX_BYTES (nothing is
+ * queued), VBYTE_EINVAL as vbyte_decode does (and for a misaligned
+ * d_status), VBYTE_ECUDA if the set-up or a launch fails. */
+int vbyte_decode_noalloc(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
+                         size_t n, int delta, uint32_t prev, uint32_t *d_status,
+                         void *stream);
 
 /* ---- status ---------------------------------------------------------- */
 

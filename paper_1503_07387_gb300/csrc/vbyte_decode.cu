@@ -1043,6 +1043,106 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
+// ---- scratch for vbyte_decode_noalloc -----------------------------------
+// A file-scope device array replaces the per-stream workspace for callers
+// that cannot allocate device memory.  It holds the layout() of an input of
+// up to VBYTE_NOALLOC_MAX_BYTES bytes (about 545 KiB); every call on a device
+// shares it.
+constexpr size_t kStaticScratchBytes = size_t(576) << 10;
+static __device__ __align__(256) uint8_t g_scratch[kStaticScratchBytes];
+
+constexpr int kMaxStaticDevices = 64;
+struct StaticDevice {
+    bool ready = false;
+    uint8_t *scratch = nullptr;
+    int sms = 0;
+    int occ[2] = {0, 0};
+};
+std::mutex g_static_mu;
+StaticDevice g_static[kMaxStaticDevices];
+
+// Set-up, once per device, with that device current: the address of
+// g_scratch on it, its SM count and the kernels' occupancy.  No allocation.
+int static_device(StaticDevice *out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VBYTE_ECUDA;
+    if (dev < 0 || dev >= kMaxStaticDevices) return VBYTE_EINVAL;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    StaticDevice &d = g_static[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || ptr == nullptr) {
+            cudaGetLastError();
+            return VBYTE_ECUDA;
+        }
+        int sms = 0, occ0 = 0, occ1 = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, decode_kernel<false>, kThreads, 0) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, decode_kernel<true>, kThreads, 0) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return VBYTE_ECUDA;
+        }
+        d.scratch = static_cast<uint8_t *>(ptr);
+        d.sms = sms;
+        d.occ[0] = std::max(occ0, 1);
+        d.occ[1] = std::max(occ1, 1);
+        d.ready = true;
+    }
+    *out = d;
+    return VBYTE_OK;
+}
+
+int launch_decode_noalloc(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta,
+                          uint32_t prev, uint32_t *status, cudaStream_t s)
+{
+    if (nbytes > VBYTE_NOALLOC_MAX_BYTES) return VBYTE_ETOOBIG;
+    if ((nbytes && !in) || (n && !out)) return VBYTE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(out) & 3u) return VBYTE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(status) & 3u) return VBYTE_EINVAL;
+    StaticDevice d;
+    int rc = static_device(&d);
+    if (rc != VBYTE_OK) return rc;
+    if (nbytes == 0 && n == 0) return VBYTE_OK;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
+    const uint64_t ntiles = nbytes ? ((a & 15u) + nbytes + kTile - 1) / kTile : 0;
+    const Layout L = layout(ntiles);
+    if (L.total > kStaticScratchBytes) return VBYTE_ETOOBIG;
+    // without a caller status word, data errors go to the array's own head
+    if (status == nullptr) status = reinterpret_cast<uint32_t *>(d.scratch);
+    if (nbytes == 0) {   // n > 0 values expected from an empty stream
+        set_status_kernel<<<1, 1, 0, s>>>(status, VBYTE_ERR_COUNT_MISMATCH);
+        return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+    }
+    // the ticket counter, the chunk words and the group accumulators start at 0
+    if (cudaMemsetAsync(d.scratch + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
+    Params p;
+    p.in = in;
+    p.nbytes = nbytes;
+    p.out = out;
+    p.n = n;
+    p.ntiles = ntiles;
+    p.base = a & ~static_cast<uintptr_t>(15);
+    p.tdesc = reinterpret_cast<uint64_t *>(d.scratch + L.tdesc);
+    p.gagg = reinterpret_cast<unsigned long long *>(d.scratch + L.gagg);
+    p.gpre = reinterpret_cast<uint64_t *>(d.scratch + L.gpre);
+    p.cnext = reinterpret_cast<uint64_t *>(d.scratch + L.cnext);
+    p.cdone = reinterpret_cast<unsigned int *>(d.scratch + L.cdone);
+    p.cready = reinterpret_cast<unsigned int *>(d.scratch + L.cready);
+    p.ctr = reinterpret_cast<unsigned long long *>(d.scratch + L.ctr);
+    p.status = status;
+    p.prev = prev;
+    p.lead = std::min<uint64_t>(kChunkTiles + kLeadSlack, ntiles);
+    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(d.sms) * d.occ[delta]);
+    if (delta)
+        decode_kernel<true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+    else
+        decode_kernel<false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
 }  // namespace vbk
 
 extern "C" {
@@ -1097,6 +1197,13 @@ int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out, size_
     return cudaStreamSynchronize(s) == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
+int vbyte_decode_noalloc(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size_t n, int delta,
+                         uint32_t prev, uint32_t *d_status, void *stream)
+{
+    return vbk::launch_decode_noalloc(d_in, nbytes, d_out, n, delta != 0, prev, d_status,
+                                      static_cast<cudaStream_t>(stream));
+}
+
 int vbyte_get_status(void *stream, uint32_t *status_out)
 {
     if (!status_out) return VBYTE_EINVAL;
@@ -1119,6 +1226,7 @@ const char *vbyte_strerror(int code)
     case VBYTE_EINVAL: return "invalid argument (null pointer with nonzero size or misaligned output)";
     case VBYTE_ECUDA: return "CUDA runtime error or kernel launch failure";
     case VBYTE_ENOMEM: return "workspace allocation failed (or needed during stream capture)";
+    case VBYTE_ETOOBIG: return "input larger than VBYTE_NOALLOC_MAX_BYTES (vbyte_decode_noalloc)";
     default: return "unknown vbyte error code";
     }
 }

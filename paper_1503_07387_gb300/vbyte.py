@@ -10,6 +10,7 @@ Names mirror the C ABI in ``include/vbyte.h``:
     decode(d_bytes, n)                          Algorithm 1 on the GPU (Sec. 2)
     decode_delta(d_bytes, n, prev)              ... plus the prefix sum of Sec. 1/4
     decode_host(h_bytes, n, delta, prev)        host buffers in and out
+    decode_noalloc(d_bytes, n, delta, prev)     fixed library scratch, no allocation
     get_status()                                data-error bits of a stream
 """
 from __future__ import annotations
@@ -22,7 +23,8 @@ import numpy as np
 
 from . import _build
 
-OK, EINVAL, ECUDA, ENOMEM = 0, 1, 2, 3
+OK, EINVAL, ECUDA, ENOMEM, ETOOBIG = 0, 1, 2, 3, 4
+NOALLOC_MAX_BYTES = 128 << 20
 ERR_MALFORMED_LONG = 1
 ERR_TRUNCATED = 2
 ERR_COUNT_MISMATCH = 4
@@ -47,6 +49,7 @@ def _signatures(lib):
         "vbyte_decode": ([P, S, P, S, P], I),
         "vbyte_decode_delta": ([P, S, P, S, U32, P], I),
         "vbyte_decode_host": ([P, S, P, S, I, U32, P], I),
+        "vbyte_decode_noalloc": ([P, S, P, S, I, U32, P, P], I),
         "vbyte_get_status": ([P, P], I),
         "vbyte_strerror": ([I], ctypes.c_char_p),
         "vbyte_workspace_size": ([S], S),
@@ -168,6 +171,26 @@ def decode_host(data: np.ndarray, n: int, delta: bool = False, prev: int = 0, ou
     rc = load().vbyte_decode_host(_np_ptr(b), b.size, _np_ptr(out), n, int(delta),
                                   ctypes.c_uint32(prev & 0xFFFFFFFF), _stream_handle(stream))
     _check(rc, "vbyte_decode_host")
+    return out
+
+
+def decode_noalloc(data, n: int, delta: bool = False, prev: int = 0, out=None, status=None,
+                   stream=None):
+    """vbyte_decode_noalloc: decode with the library's fixed scratch array.
+
+    `status` is an optional CUDA int32/uint32 tensor of one element into which
+    the data-error bits are OR-ed."""
+    import torch
+    out = _device_args(data, n, out)
+    sp = None
+    if status is not None:
+        if not status.is_cuda or status.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("status must be a 32-bit CUDA tensor")
+        sp = ctypes.c_void_p(status.data_ptr())
+    rc = load().vbyte_decode_noalloc(ctypes.c_void_p(data.data_ptr()), data.numel(),
+                                     ctypes.c_void_p(out.data_ptr()), n, int(delta),
+                                     ctypes.c_uint32(prev & 0xFFFFFFFF), sp, _stream_handle(stream))
+    _check(rc, "vbyte_decode_noalloc")
     return out
 
 
