@@ -65,6 +65,9 @@ extern "C" {
 /* A cross-tile look-back wait gave up after its time limit (about two
  * seconds); the outputs of that call are unspecified. */
 #define VBYTE_ERR_TIMEOUT 8u
+/* Batched calls: the offset arrays break their contract (not non-decreasing,
+ * or not running from 0 to nbytes and from 0 to n). */
+#define VBYTE_ERR_BAD_OFFSETS 16u
 
 /* ---- host-side encoding (input generation) ----------------------------- */
 
@@ -108,7 +111,38 @@ int vbyte_decode(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size_t n,
 int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
                        size_t n, uint32_t prev, void *stream);
 
-/* End-to-end form of the two calls above for data in host memory: copies
+/* ---- batched GPU decoding ------------------------------------------------ */
+
+/* Decode num_lists lists laid end to end in one launch (Sec. 5 decodes
+ * posting lists one after another; here they are decoded together).  List j
+ * is the bytes d_in[d_byte_off[j] .. d_byte_off[j+1]) and decodes to
+ * d_out[d_val_off[j] .. d_val_off[j+1]).  The offset arrays hold
+ * num_lists + 1 uint64 each, in device memory (8-byte aligned), and must be
+ * non-decreasing with d_byte_off[0] = 0, d_byte_off[num_lists] = nbytes,
+ * d_val_off[0] = 0, d_val_off[num_lists] = n (nbytes and n are passed from
+ * the host so the call needs no device-to-host read); a violation sets
+ * VBYTE_ERR_BAD_OFFSETS.  Each list must hold exactly its value count
+ * (VBYTE_ERR_COUNT_MISMATCH otherwise) and end on a terminator byte
+ * (VBYTE_ERR_TRUNCATED otherwise).  Empty lists are allowed.  Since a
+ * well-formed list ends on a terminator, the values equal those of
+ * vbyte_decode on the concatenation.  num_lists = 0 requires nbytes = n = 0.
+ * Returns VBYTE_EINVAL for null or misaligned pointers. */
+int vbyte_decode_batched(const uint8_t *d_in, size_t nbytes,
+                         const uint64_t *d_byte_off, uint32_t *d_out, size_t n,
+                         const uint64_t *d_val_off, size_t num_lists,
+                         void *stream);
+
+/* As vbyte_decode_batched, each list differentially coded on its own (Sec. 1
+ * "Differential coding"): d_out[d_val_off[j] + i] = d_prev[j] + g_0 + ... +
+ * g_i modulo 2^32 over list j's gaps g.  d_prev (num_lists uint32, device)
+ * may be NULL for x_0 = 0 in every list. */
+int vbyte_decode_delta_batched(const uint8_t *d_in, size_t nbytes,
+                               const uint64_t *d_byte_off, uint32_t *d_out,
+                               size_t n, const uint64_t *d_val_off,
+                               size_t num_lists, const uint32_t *d_prev,
+                               void *stream);
+
+/* End-to-end form of vbyte_decode / vbyte_decode_delta for data in host memory: copies
  * h_in to the device, decodes (differentially when delta != 0) and copies the
  * n values back to h_out, through library-owned device buffers kept per
  * stream.  Synchronises the stream before returning.  The data-error status

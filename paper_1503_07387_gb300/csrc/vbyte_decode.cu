@@ -41,6 +41,7 @@
 // tickets (counting never waits, except a chunk's last CTA on the chunk
 // before), so every wait ends; each is bounded by the global timer.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -86,7 +87,19 @@ struct Params {
     uint32_t *status;          // data-error bits
     uint32_t prev;             // x_0 for differential decoding
     uint64_t lead;             // tickets [0, lead) only count; ticket k >= lead also decodes k - lead
+    // segmented (batched) decoding only
+    const uint64_t *bo;        // list byte offsets [L + 1], relative to in
+    const uint64_t *vo;        // list value offsets [L + 1]
+    const uint32_t *prevs;     // per-list x_0 (nullptr: 0)
+    uint64_t L;                // number of lists
+    const uint64_t *hr;        // per tile: [first, end) of the lists whose head may own a terminator in it
+    uint64_t *tpre;            // per tile: values before it, running x before it
 };
+
+// Heads of lists are looked up in a window that starts this many bytes
+// before a tile or slice: an integer ends at most four bytes after it starts.
+constexpr int kHeadBack = 8;
+constexpr int kHeadWords = (kHalo + kTile) / 32 + 2;   // head bitmap of a staged tile
 
 // ---------------------------------------------------------------- helpers --
 
@@ -400,6 +413,154 @@ __device__ __forceinline__ void slice_count_sum(const SliceMasks &m, const uint3
     }
 }
 
+// ---- segmented sums (batched differential decoding) ----------------------
+// A list head restarts the running value at that list's x_0.  A slice of
+// integers acts on the running value x as: f ? s : x + s, where f says that a
+// head was crossed and s is the sum since the last head (including its x_0).
+struct Seg {
+    uint32_t f, s;
+};
+
+__device__ __forceinline__ Seg seg_op(Seg a, Seg b)
+{
+    Seg r;
+    r.f = a.f | b.f;
+    r.s = b.f ? b.s : a.s + b.s;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t seg_apply(uint32_t x, Seg a) { return a.f ? a.s : x + a.s; }
+
+__device__ __forceinline__ Seg warp_seg_incl(Seg x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ys = __shfl_up_sync(~0u, x.s, o);
+        const uint32_t yf = __shfl_up_sync(~0u, x.f, o);
+        if (lane >= o) {
+            if (!x.f) x.s += ys;
+            x.f |= yf;
+        }
+    }
+    return x;
+}
+
+// Bitmap of the list heads (byte offsets bo[j], j in [ha, he)) that fall in
+// the staged window of the tile starting at stream offset trel: bit i is
+// staging byte i (the 16 halo bytes first).  All threads take part.
+__device__ __forceinline__ void build_head_bits(const Params &p, long long trel, uint64_t ha, uint64_t he,
+                                                uint32_t *bits)
+{
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kHeadWords; i += kThreads) bits[i] = 0u;
+    __syncthreads();
+    const long long w0 = trel - kHalo;
+    for (uint64_t j = ha + tid; j < he; j += kThreads) {
+        const long long pos = static_cast<long long>(p.bo[j]) - w0;
+        if (pos >= 0 && pos < kHalo + kTile) atomicOr(bits + (pos >> 5), 1u << (pos & 31));
+    }
+    __syncthreads();
+}
+
+// The 24 staged bytes ending with tid's slice: terminator bits (t24) and head
+// bits (h24); bit i is staging byte kHalo + 16*tid - kHeadBack + i.
+struct HeadWin {
+    uint32_t t24, h24;
+};
+
+__device__ __forceinline__ HeadWin head_window(const uint32_t *sw, const uint32_t *bits, int tid, uint32_t tl)
+{
+    HeadWin h;
+    const int q = (kHalo + tid * kBPT) / 4;
+    h.t24 = term4(sw[q - 2]) | (term4(sw[q - 1]) << 4) | (tl << 8);
+    const int b0 = kHalo + tid * kBPT - kHeadBack;   // a multiple of 8
+    h.h24 = __funnelshift_r(bits[b0 >> 5], bits[(b0 >> 5) + 1], b0 & 31) & 0xFFFFFFu;
+    return h;
+}
+
+// Terminators (slice bits) that end the first integer of a list: the integer
+// starting at a head bit h ends at the first terminator at or after h.  Adding
+// h to the non-terminator mask carries from h through the continuation bytes
+// into exactly that terminator.
+__device__ __forceinline__ uint32_t head_terms(const HeadWin &h, uint32_t tc)
+{
+    const uint32_t r = ~h.t24 & 0xFFFFFFu;
+    return (((r + h.h24) & h.t24) >> kHeadBack) & tc;
+}
+
+// Index of the last list in [ha, he) whose byte offset is pos (a head bit was
+// set from one of them); ha - 1 if none.
+__device__ __forceinline__ long long last_list_at(const Params &p, uint64_t ha, uint64_t he, long long pos)
+{
+    uint64_t lo = ha, hi = he;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (static_cast<long long>(p.bo[mid]) <= pos)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return static_cast<long long>(lo) - 1;
+}
+
+// x_0 of the list whose first integer ends at slice bit o (a head_terms bit):
+// that integer starts after the previous terminator; the head bit in between
+// names the list.  srel: stream offset of the slice's first byte.
+__device__ __forceinline__ uint32_t head_prev(const Params &p, const HeadWin &h, int o, long long srel, uint64_t ha,
+                                              uint64_t he)
+{
+    const int P = o + kHeadBack;
+    const uint32_t below = h.t24 & ((1u << P) - 1u);
+    const int q = below ? 31 - __clz(below) : -1;          // previous terminator
+    const uint32_t above_q = q >= 0 ? ~((2u << q) - 1u) : ~0u;
+    const uint32_t hb = h.h24 & ((2u << P) - 1u) & above_q;   // heads in (q, P]
+    if (!hb) return 0u;
+    const int k = 31 - __clz(hb);
+    const long long j = last_list_at(p, ha, he, srel - kHeadBack + k);
+    if (j < static_cast<long long>(ha) || p.prevs == nullptr) return 0u;
+    return p.prevs[j];
+}
+
+// Per-terminator assembly as assemble_all, also passing each terminator's
+// slice bit to emit(o, value).
+template <typename F>
+__device__ __forceinline__ void assemble_all_o(const uint32_t *sw, int tid, uint32_t tl, uint32_t t20, uint32_t tc,
+                                               F emit)
+{
+    uint32_t m = tl;
+    int prevo = 27 - __clz(t20 & 0xFu);
+    while (m) {
+        const int o = __ffs(m) - 1;
+        m &= m - 1u;
+        const int L = min(o - prevo, 5);
+        prevo = o;
+        if ((tc >> o) & 1u) {
+            const int q = kHalo + tid * kBPT + o;
+            const uint32_t A = sw[(q >> 2) - 1];
+            const uint32_t B = sw[q >> 2];
+            const uint32_t lo4 = __funnelshift_r(A, B, 8 * q);
+            const uint32_t x = (B >> (8 * (q & 3))) & 0xFFu;
+            emit(o, assemble(lo4, x, L));
+        }
+    }
+}
+
+// Segmented sum of a slice that holds list heads (ht != 0): the sum since the
+// last head, starting from that list's x_0.
+__device__ __forceinline__ uint32_t slice_seg_sum(const Params &p, const uint32_t *sw, int tid, uint32_t tl,
+                                                  uint32_t t20, uint32_t tc, const HeadWin &h, uint32_t ht,
+                                                  long long srel, uint64_t ha, uint64_t he)
+{
+    uint32_t s = 0;
+    assemble_all_o(sw, tid, tl, t20, tc, [&](int o, uint32_t v) {
+        if ((ht >> o) & 1u)
+            s = head_prev(p, h, o, srel, ha, he) + v;
+        else
+            s += v;
+    });
+    return s;
+}
+
 struct Shared {
     uint8_t cbytes[2][kByteBuf];     // staged tiles to count (double-buffered)
     uint8_t dbytes[2][kByteBuf];     // staged tiles to decode (double-buffered)
@@ -416,12 +577,25 @@ struct Shared {
     unsigned long long pR0[2];       // prefetched tile prefixes (per buffer)
     uint32_t pS0[2];
     uint32_t pok[2];                 // prefetch valid
+    // segmented decoding
+    alignas(16) unsigned long long hrc[2][2];   // head ranges of the staged count tiles (cp.async targets)
+    alignas(16) unsigned long long hrd[2][2];   // head ranges of the staged decode tiles
+    uint32_t hbits[kHeadWords];      // head bitmap of the tile being worked on
+    uint32_t wsf[kWarps];            // count: per-warp "crossed a list head" flags
+    uint32_t dsf[kWarps];            // decode: the same
+    unsigned long long csc[kWarps];  // segmented chunk scan: per-warp count totals
+    uint32_t css[kWarps], csf[kWarps];
 };
+// 16-byte cp.async and vector accesses need 16-byte aligned shared addresses
+static_assert(offsetof(Shared, cbytes) % 16 == 0 && kByteBuf % 16 == 0, "cbytes alignment");
+static_assert(offsetof(Shared, dbytes) % 16 == 0, "dbytes alignment");
+static_assert(offsetof(Shared, vals) % 16 == 0, "vals alignment");
+static_assert(offsetof(Shared, hrc) % 16 == 0 && offsetof(Shared, hrd) % 16 == 0, "head range alignment");
 
 // --------------------------------------------------------------- counting --
 
-template <bool kDelta>
-__device__ void count_tile(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes)
+template <bool kDelta, bool kSeg>
+__device__ void count_tile(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes, int b)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -456,6 +630,51 @@ __device__ void count_tile(const Params &p, uint64_t t, Shared &S, const uint8_t
                              [&](uint32_t v) { vsum += v; });
             }
         }
+    }
+
+    if constexpr (kSeg) {
+        // batched: the tile's sum restarts at every list head it holds
+        uint32_t segf = 0;
+        if constexpr (kDelta) {
+            const uint64_t ha = S.hrc[b][0], he = S.hrc[b][1];
+            if (ha < he) {   // CTA-uniform
+                const long long trel = static_cast<long long>(tstart) - static_cast<long long>(lo);
+                build_head_bits(p, trel, ha, he, S.hbits);
+                const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+                const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
+                const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
+                const HeadWin h = head_window(sw, S.hbits, tid, m.tl);
+                const uint32_t ht = head_terms(h, m.tc);
+                if (ht) {
+                    segf = 1u;
+                    vsum = slice_seg_sum(p, sw, tid, m.tl, m.t20, m.tc, h, ht, trel + tid * kBPT, ha, he);
+                }
+            }
+        }
+        Seg sg;
+        sg.f = segf;
+        sg.s = vsum;
+        sg = warp_seg_incl(sg, lane);
+        const uint32_t wc = __reduce_add_sync(~0u, cnt);
+        if (lane == 31) {
+            S.wcnt[warp] = wc;
+            S.wsum[warp] = sg.s;
+            S.wsf[warp] = sg.f;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Seg ws;
+            ws.f = lane < kWarps ? S.wsf[lane] : 0u;
+            ws.s = lane < kWarps ? S.wsum[lane] : 0u;
+            ws = warp_seg_incl(ws, lane);
+            const uint32_t tcnt = __reduce_add_sync(~0u, lane < kWarps ? S.wcnt[lane] : 0u);
+            if (lane == 31) {
+                p.tdesc[2 * t] = tcnt;
+                p.tdesc[2 * t + 1] = (static_cast<uint64_t>(ws.f) << 32) | ws.s;
+                red_release_add(p.cdone + t / kChunkTiles, 1u);
+            }
+        }
+        return;
     }
 
     const uint32_t wc = __reduce_add_sync(~0u, cnt);
@@ -557,6 +776,111 @@ __device__ void chunk_scan(const Params &p, uint64_t c, Shared &S)
     __syncthreads();
 }
 
+// Batched form: the per-tile prefixes of chunk c, computed from the tile
+// descriptors by the CTA that decodes the chunk's first tile (same waits as
+// chunk_scan).  Each thread scans eight consecutive tiles; the running value
+// restarts at list heads (segmented sums).
+template <bool kDelta>
+__device__ void chunk_scan_seg(const Params &p, uint64_t c, Shared &S)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    constexpr int kPer = static_cast<int>(kChunkTiles / kThreads);   // 8
+    const uint64_t c0 = c * kChunkTiles;
+    const uint64_t c1 = (c0 + kChunkTiles < p.ntiles) ? c0 + kChunkTiles : p.ntiles;
+    if (tid == 0) {
+        uint64_t t0 = 0;
+        for (int spin = 0;; ++spin) {
+            if (ld_acquire_u32(p.cdone + c) >= static_cast<unsigned int>(c1 - c0)) break;
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            if (now - t0 > kWaitLimitNs) {
+                atomicOr(p.status, VBYTE_ERR_TIMEOUT);
+                break;
+            }
+            if (spin > 4) __nanosleep(200);
+        }
+    }
+    uint64_t pc = 0;
+    uint32_t ps = 0;
+    if (c > 0) {
+        wait_flag(p.cready + (c - 1), p.status);
+        pc = __ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1)));
+        ps = static_cast<uint32_t>(__ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1) + 1)));
+    } else {
+        __syncthreads();
+    }
+    const uint64_t tb = c0 + static_cast<uint64_t>(kPer) * tid;
+    uint64_t cn[kPer];
+    Seg sg[kPer];
+    uint64_t tcn = 0;
+    Seg ts;
+    ts.f = 0u;
+    ts.s = 0u;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        cn[i] = 0;
+        sg[i].f = 0u;
+        sg[i].s = 0u;
+        if (tb + i < c1) {
+            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + 2 * (tb + i)));
+            cn[i] = d.x;
+            sg[i].f = static_cast<uint32_t>(d.y >> 32);
+            sg[i].s = static_cast<uint32_t>(d.y);
+        }
+        tcn += cn[i];
+        ts = seg_op(ts, sg[i]);
+    }
+    const uint64_t icn = warp_incl_scan64(tcn, lane);
+    const Seg is = warp_seg_incl(ts, lane);
+    if (lane == 31) {
+        S.csc[warp] = icn;
+        S.css[warp] = is.s;
+        S.csf[warp] = is.f;
+    }
+    __syncthreads();
+    uint64_t wc0 = 0, call = 0;
+    Seg w0, wall;
+    w0.f = w0.s = wall.f = wall.s = 0u;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+        Seg e;
+        e.f = S.csf[q];
+        e.s = S.css[q];
+        if (q < warp) {
+            wc0 += S.csc[q];
+            w0 = seg_op(w0, e);
+        }
+        call += S.csc[q];
+        wall = seg_op(wall, e);
+    }
+    // state before my first tile: chunk start, earlier warps, earlier lanes
+    Seg ex;
+    ex.f = __shfl_up_sync(~0u, is.f, 1);
+    ex.s = __shfl_up_sync(~0u, is.s, 1);
+    if (lane == 0) ex.f = ex.s = 0u;
+    uint64_t rc = pc + wc0 + icn - tcn;
+    uint32_t x = seg_apply(ps, seg_op(w0, ex));
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        if (tb + i < c1) {
+            *reinterpret_cast<ulonglong2 *>(p.tpre + 2 * (tb + i)) = make_ulonglong2(rc, x);
+        }
+        rc += cn[i];
+        x = seg_apply(x, sg[i]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        p.cnext[2 * c] = pc + call;
+        p.cnext[2 * c + 1] = seg_apply(ps, wall);
+        if (c1 == p.ntiles && pc + call != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        __threadfence();
+        *reinterpret_cast<volatile unsigned int *>(p.cready + c) = 1u;
+    }
+    __syncthreads();
+}
+
 // --------------------------------------------------------------- decoding --
 
 // Warp 0's loads of a tile's prefix: the group prefix (lane 0) and the
@@ -566,11 +890,20 @@ struct PrefixLoads {
     bool ok;   // loaded after the tile's chunk was seen ready (warp-uniform)
 };
 
+template <bool kSeg>
 __device__ __forceinline__ PrefixLoads load_prefix(const Params &p, uint64_t t, int lane)
 {
     PrefixLoads r;
     r.pa = r.pb = r.ga = r.gb = 0;
     r.ok = true;
+    if constexpr (kSeg) {   // the chunk scan wrote the tile's own prefix
+        if (lane == 0) {
+            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tpre + 2 * t));
+            r.ga = d.x;
+            r.gb = d.y;
+        }
+        return r;
+    }
     const uint64_t g = t / kGroup;
     const uint64_t j = g * kGroup + lane;
     if (j < t) {
@@ -587,6 +920,7 @@ __device__ __forceinline__ PrefixLoads load_prefix(const Params &p, uint64_t t, 
 // Warp 0: if tile t's chunk is already published (and t is not the chunk's
 // first tile, whose CTA scans the chunk), issue its prefix loads now, to be
 // consumed an iteration later.
+template <bool kSeg>
 __device__ __forceinline__ PrefixLoads try_prefetch_prefix(const Params &p, uint64_t t, int lane)
 {
     PrefixLoads r;
@@ -597,10 +931,10 @@ __device__ __forceinline__ PrefixLoads try_prefetch_prefix(const Params &p, uint
     if (lane == 0) ready = ld_acquire_u32(p.cready + t / kChunkTiles);
     ready = __shfl_sync(~0u, ready, 0);   // the warp sync orders lane 0's acquire before the loads
     if (!ready) return r;
-    return load_prefix(p, t, lane);
+    return load_prefix<kSeg>(p, t, lane);
 }
 
-template <bool kDelta>
+template <bool kDelta, bool kSeg>
 __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes, int b)
 {
     const int tid = threadIdx.x;
@@ -618,12 +952,15 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
     pre.pa = pre.pb = pre.ga = pre.gb = 0;
     const bool prefetched = S.pok[b] != 0u && t % kChunkTiles != 0;
     if (t % kChunkTiles == 0) {
-        chunk_scan<kDelta>(p, t / kChunkTiles, S);
-        if (warp == 0) pre = load_prefix(p, t, lane);
+        if constexpr (kSeg)
+            chunk_scan_seg<kDelta>(p, t / kChunkTiles, S);
+        else
+            chunk_scan<kDelta>(p, t / kChunkTiles, S);
+        if (warp == 0) pre = load_prefix<kSeg>(p, t, lane);
     } else if (warp == 0 && !prefetched) {
         if (lane == 0) spin_flag(p.cready + t / kChunkTiles, p.status);
         __syncwarp();
-        pre = load_prefix(p, t, lane);
+        pre = load_prefix<kSeg>(p, t, lane);
     }
     auto fold_prefix = [&]() {
         if (warp == 0) {
@@ -647,7 +984,13 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
     const bool interior = tstart >= lo && tstart + kTile <= hi;
     const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
     const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
-    const bool mineA = interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u);
+    bool mineA = interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u);
+    uint64_t ha = 0, he = 0;
+    if constexpr (kSeg) {
+        ha = S.hrd[b][0];
+        he = S.hrd[b][1];
+        if (ha < he) mineA = false;   // tiles with list heads take the general path
+    }
 
     if (!__syncthreads_or(!mineA)) {
         // ---- class A: every byte is a one-byte integer; tile rank 16*tid + i is
@@ -750,29 +1093,105 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
     uint32_t cnt, vsum;
     bool notB;
     slice_count_sum<kDelta>(m, sw, tid, interior, cnt, vsum, notB);
+    const long long trel = static_cast<long long>(tstart) - static_cast<long long>(lo);
+    const long long srel = trel + tid * kBPT;
+    HeadWin hw;
+    hw.t24 = hw.h24 = 0u;
+    uint32_t ht = 0;
+    if constexpr (kSeg) {
+        if (ha < he) {   // CTA-uniform
+            build_head_bits(p, trel, ha, he, S.hbits);
+            hw = head_window(sw, S.hbits, tid, m.tl);
+            if constexpr (kDelta) {
+                ht = head_terms(hw, m.tc);
+                if (ht) {
+                    vsum = slice_seg_sum(p, sw, tid, m.tl, m.t20, m.tc, hw, ht, srel, ha, he);
+                    notB = true;   // values with restarts take the per-terminator path
+                }
+            }
+        }
+    }
     const uint32_t inc = warp_incl_scan(cnt, lane);
-    const uint32_t incs = kDelta ? warp_incl_scan(vsum, lane) : 0u;
+    Seg isg;
+    isg.f = ht ? 1u : 0u;
+    isg.s = vsum;
+    if constexpr (kSeg && kDelta) {
+        isg = warp_seg_incl(isg, lane);
+    } else if constexpr (kDelta) {
+        isg.s = warp_incl_scan(vsum, lane);
+    }
     if (lane == 31) {
         S.dcnt[warp] = inc;
-        S.dsum[warp] = incs;
+        S.dsum[warp] = isg.s;
+        if constexpr (kSeg) S.dsf[warp] = isg.f;
     }
     fold_prefix();
     __syncthreads();
     uint32_t wbase = 0, wsbase = 0, tcnt = 0;
+    Seg wseg;
+    wseg.f = wseg.s = 0u;
 #pragma unroll
     for (int q = 0; q < kWarps; ++q) {
         const uint32_t c = S.dcnt[q];
         wbase += (q < warp) ? c : 0u;
-        if (kDelta) wsbase += (q < warp) ? S.dsum[q] : 0u;
+        if constexpr (kSeg && kDelta) {
+            if (q < warp) {
+                Seg e;
+                e.f = S.dsf[q];
+                e.s = S.dsum[q];
+                wseg = seg_op(wseg, e);
+            }
+        } else if constexpr (kDelta) {
+            wsbase += (q < warp) ? S.dsum[q] : 0u;
+        }
         tcnt += c;
     }
     const unsigned long long R0 = S.R0;
     const uint32_t sh = (out_word + static_cast<uint32_t>(R0)) & 3u;
 
+    if constexpr (kSeg) {
+        // each list head in my slice: its first integer's rank must be vo[j],
+        // and the byte before it must end the previous list's last integer
+        const uint32_t hs = (hw.h24 >> kHeadBack) & 0xFFFFu;
+        if (hs) {
+            uint32_t mm = hs;
+            while (mm) {
+                const int k = __ffs(mm) - 1;
+                mm &= mm - 1u;
+                const long long pos = srel + k;
+                if (pos < 0 || pos >= static_cast<long long>(p.nbytes)) continue;
+                if (pos > 0 && !((hw.t24 >> (kHeadBack + k - 1)) & 1u)) atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+                const uint64_t rank = R0 + wbase + inc - cnt + __popc(m.tc & ((1u << k) - 1u));
+                for (long long j = last_list_at(p, ha, he, pos); j >= static_cast<long long>(ha); --j) {
+                    if (static_cast<long long>(p.bo[j]) != pos) break;
+                    if (p.vo[j] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+                }
+            }
+        }
+    }
+
     // assemble my values into vals[sh + rank], prefix-summed in delta mode
     uint32_t *dst = S.vals + sh + wbase + inc - cnt;
-    uint32_t run = kDelta ? S.S0 + wsbase + incs - vsum : 0u;
-    if (!__any_sync(~0u, notB)) {
+    uint32_t run = 0u;
+    if constexpr (kSeg && kDelta) {
+        Seg ex;
+        ex.f = __shfl_up_sync(~0u, isg.f, 1);
+        ex.s = __shfl_up_sync(~0u, isg.s, 1);
+        if (lane == 0) ex.f = ex.s = 0u;
+        run = seg_apply(S.S0, seg_op(wseg, ex));
+    } else if constexpr (kDelta) {
+        run = S.S0 + wsbase + isg.s - vsum;
+    }
+    const bool warp_le2 = !__any_sync(~0u, notB);
+    if (ht) {
+        assemble_all_o(sw, tid, m.tl, m.t20, m.tc, [&](int o, uint32_t v) {
+            if ((ht >> o) & 1u)
+                run = head_prev(p, hw, o, srel, ha, he) + v;
+            else
+                run += v;
+            *dst++ = run;
+        });
+    } else if (warp_le2) {
         const uint32_t c4[4] = {m.w.x, m.w.y, m.w.z, m.w.w};
         uint32_t wp = m.wprev;
         int q = 0;
@@ -835,7 +1254,7 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
 // from HBM by its count and again, about 12 MiB of input later, from L2 by
 // its decode.
 
-template <bool kDelta>
+template <bool kDelta, bool kSeg>
 __global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
 {
     __shared__ __align__(16) Shared S;
@@ -853,6 +1272,10 @@ __global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
     auto stage = [&](uint64_t tk, int b) {
         if (tk < p.ntiles) issue_stage(p, tk, tid, S.cbytes[b]);
         if (tk >= p.lead && tk < total) issue_stage(p, tk - p.lead, tid, S.dbytes[b]);
+        if constexpr (kSeg) {   // the tiles' list-head ranges travel with them
+            if (kDelta && tid == 32 && tk < p.ntiles) cp_async16(S.hrc[b], p.hr + 2 * tk);
+            if (tid == 64 && tk >= p.lead && tk < total) cp_async16(S.hrd[b], p.hr + 2 * (tk - p.lead));
+        }
         cp_async_commit();
     };
     stage(k, 0);
@@ -867,11 +1290,11 @@ __global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
         PrefixLoads pn;
         pn.pa = pn.pb = pn.ga = pn.gb = 0;
         pn.ok = false;
-        if (warp == 0 && kn >= p.lead && kn < total) pn = try_prefetch_prefix(p, kn - p.lead, lane);
+        if (warp == 0 && kn >= p.lead && kn < total) pn = try_prefetch_prefix<kSeg>(p, kn - p.lead, lane);
         cp_async_wait_prior();
         __syncthreads();   // ticket k's tiles are staged
-        if (k < p.ntiles) count_tile<kDelta>(p, k, S, S.cbytes[b]);
-        if (k >= p.lead) decode_tile<kDelta>(p, k - p.lead, S, S.dbytes[b], b);
+        if (k < p.ntiles) count_tile<kDelta, kSeg>(p, k, S, S.cbytes[b], b);
+        if (k >= p.lead) decode_tile<kDelta, kSeg>(p, k - p.lead, S, S.dbytes[b], b);
         if (warp == 0) {
             const uint64_t ec = warp_sum64(pn.pa);
             const uint64_t es = warp_sum64(pn.pb & 0xFFFFFFFFull);
@@ -890,6 +1313,49 @@ __global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
 }
 
 __global__ void set_status_kernel(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
+
+// Batched form, before the decode: for every tile, the range [first, end) of
+// list indices whose byte offset lies in [tile start - kHeadBack, tile end)
+// (binary searches over bo), and the offset arrays' contract: bo and vo
+// non-decreasing from 0 to nbytes and n; a list that starts at the end of the
+// bytes holds no values.
+__device__ __forceinline__ uint64_t lower_bound_bo(const uint64_t *bo, uint64_t L, long long x)
+{
+    if (x <= 0) return 0;
+    uint64_t lo = 0, hi = L + 1;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (static_cast<long long>(bo[mid]) < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) head_range_kernel(const Params p)
+{
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const long long in0 = static_cast<long long>(reinterpret_cast<uintptr_t>(p.in));
+    uint64_t *hr = const_cast<uint64_t *>(p.hr);
+    for (uint64_t t = i0; t < p.ntiles; t += stride) {
+        const long long trel = static_cast<long long>(p.base + t * kTile) - in0;
+        uint64_t a = lower_bound_bo(p.bo, p.L, trel - kHeadBack);
+        uint64_t e = lower_bound_bo(p.bo, p.L, trel + kTile);
+        if (e > p.L) e = p.L;
+        if (a > e) a = e;
+        *reinterpret_cast<ulonglong2 *>(hr + 2 * t) = make_ulonglong2(a, e);
+    }
+    uint32_t bad = 0;
+    for (uint64_t j = i0; j < p.L; j += stride) {
+        if (p.bo[j] > p.bo[j + 1] || p.vo[j] > p.vo[j + 1]) bad |= VBYTE_ERR_BAD_OFFSETS;
+        if (p.bo[j] == p.nbytes && p.vo[j] != p.n) bad |= VBYTE_ERR_COUNT_MISMATCH;
+    }
+    if (i0 == 0 && (p.bo[0] != 0 || p.vo[0] != 0 || p.bo[p.L] != p.nbytes || p.vo[p.L] != p.n))
+        bad |= VBYTE_ERR_BAD_OFFSETS;
+    if (bad) atomicOr(p.status, bad);
+}
 
 // ------------------------------------------------------------- workspace --
 
@@ -974,9 +1440,34 @@ int get_workspace(cudaStream_t s, size_t need, Workspace **out)
     return VBYTE_OK;
 }
 
+// Batched workspace: after the single-stream head, ticket counter and chunk
+// words, per tile two words of tdesc, two of tpre and two of hr.
+struct LayoutSeg {
+    uint64_t ntiles, nchunks;
+    size_t ctr, cnext, cdone, cready, tdesc, tpre, hr, total, clear;
+};
+
+LayoutSeg layout_seg(uint64_t ntiles)
+{
+    LayoutSeg L;
+    L.ntiles = ntiles;
+    L.nchunks = (ntiles + kChunkTiles - 1) / kChunkTiles;
+    L.ctr = kWsHead;
+    L.cnext = L.ctr + 16;
+    L.cdone = L.cnext + 16 * L.nchunks;
+    L.cready = L.cdone + 4 * L.nchunks;
+    L.tdesc = (L.cready + 4 * L.nchunks + 15) / 16 * 16;
+    L.tpre = L.tdesc + 16 * ntiles;
+    L.hr = L.tpre + 16 * ntiles;
+    L.total = L.hr + 16 * ntiles;
+    L.clear = L.tdesc - L.ctr;   // ticket counter and chunk words
+    return L;
+}
+
 struct DeviceInfo {
     int sms = 0;
     int occ[2] = {0, 0};
+    int occ_seg[2] = {0, 0};
 };
 std::map<int, DeviceInfo> g_dev;
 
@@ -989,9 +1480,12 @@ int device_info(DeviceInfo *di)
     if (d.sms == 0) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return VBYTE_ECUDA;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], decode_kernel<false>, kThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], decode_kernel<true>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], decode_kernel<false, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], decode_kernel<true, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_seg[0], decode_kernel<false, true>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_seg[1], decode_kernel<true, true>, kThreads, 0);
         for (int &o : d.occ) o = std::max(o, 1);
+        for (int &o : d.occ_seg) o = std::max(o, 1);
     }
     *di = d;
     return VBYTE_OK;
@@ -1018,7 +1512,7 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     rc = device_info(&di);
     if (rc != VBYTE_OK) return rc;
     if (cudaMemsetAsync(w->ptr + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
-    Params p;
+    Params p = {};
     p.in = in;
     p.nbytes = nbytes;
     p.out = out;
@@ -1037,9 +1531,71 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     p.lead = std::min<uint64_t>(kChunkTiles + kLeadSlack, ntiles);
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
     if (delta)
-        decode_kernel<true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+        decode_kernel<true, false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
     else
-        decode_kernel<false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+        decode_kernel<false, false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
+// Batched decoding: lists j in [0, L) are bytes [bo[j], bo[j+1]) of in and
+// values [vo[j], vo[j+1]) of out; the concatenation is decoded as one stream
+// whose running value (delta) restarts at prevs[j] at each list head.
+int launch_decode_batched(const uint8_t *in, size_t nbytes, const uint64_t *bo, uint32_t *out, size_t n,
+                          const uint64_t *vo, size_t L, const uint32_t *prevs, bool delta, cudaStream_t s)
+{
+    if ((nbytes && !in) || (n && !out) || !bo || !vo) return VBYTE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(out) & 3u) return VBYTE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(bo) | reinterpret_cast<uintptr_t>(vo)) & 7u) return VBYTE_EINVAL;
+    if (prevs && (reinterpret_cast<uintptr_t>(prevs) & 3u)) return VBYTE_EINVAL;
+    if (L == 0 && (nbytes || n)) return VBYTE_EINVAL;
+    if (L == 0) return VBYTE_OK;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
+    const uint64_t ntiles = nbytes ? ((a & 15u) + nbytes + kTile - 1) / kTile : 0;
+    const LayoutSeg Y = layout_seg(ntiles);
+    Workspace *w = nullptr;
+    int rc = get_workspace(s, Y.total, &w);
+    if (rc != VBYTE_OK) return rc;
+    DeviceInfo di;
+    rc = device_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    Params p = {};
+    p.in = in;
+    p.nbytes = nbytes;
+    p.out = out;
+    p.n = n;
+    p.ntiles = ntiles;
+    p.base = a & ~static_cast<uintptr_t>(15);
+    p.tdesc = reinterpret_cast<uint64_t *>(w->ptr + Y.tdesc);
+    p.gagg = nullptr;
+    p.gpre = nullptr;
+    p.cnext = reinterpret_cast<uint64_t *>(w->ptr + Y.cnext);
+    p.cdone = reinterpret_cast<unsigned int *>(w->ptr + Y.cdone);
+    p.cready = reinterpret_cast<unsigned int *>(w->ptr + Y.cready);
+    p.ctr = reinterpret_cast<unsigned long long *>(w->ptr + Y.ctr);
+    p.status = reinterpret_cast<uint32_t *>(w->ptr);
+    p.prev = 0u;
+    p.lead = std::min<uint64_t>(kChunkTiles + kLeadSlack, ntiles);
+    p.bo = bo;
+    p.vo = vo;
+    p.prevs = prevs;
+    p.L = L;
+    p.hr = reinterpret_cast<const uint64_t *>(w->ptr + Y.hr);
+    p.tpre = reinterpret_cast<uint64_t *>(w->ptr + Y.tpre);
+    const uint64_t work = std::max<uint64_t>(ntiles, L);
+    const unsigned pre_grid = static_cast<unsigned>(
+        std::min<uint64_t>((work + 255) / 256, static_cast<uint64_t>(di.sms) * 8));
+    head_range_kernel<<<std::max(pre_grid, 1u), 256, 0, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return VBYTE_ECUDA;
+    if (nbytes == 0) {
+        if (n > 0) set_status_kernel<<<1, 1, 0, s>>>(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+    }
+    if (cudaMemsetAsync(w->ptr + Y.ctr, 0, Y.clear, s) != cudaSuccess) return VBYTE_ECUDA;
+    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ_seg[delta]);
+    if (delta)
+        decode_kernel<true, true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+    else
+        decode_kernel<false, true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
@@ -1078,9 +1634,9 @@ int static_device(StaticDevice *out)
         }
         int sms = 0, occ0 = 0, occ1 = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, decode_kernel<false>, kThreads, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, decode_kernel<false, false>, kThreads, 0) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, decode_kernel<true>, kThreads, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, decode_kernel<true, false>, kThreads, 0) !=
                 cudaSuccess) {
             cudaGetLastError();
             return VBYTE_ECUDA;
@@ -1118,7 +1674,7 @@ int launch_decode_noalloc(const uint8_t *in, size_t nbytes, uint32_t *out, size_
     }
     // the ticket counter, the chunk words and the group accumulators start at 0
     if (cudaMemsetAsync(d.scratch + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
-    Params p;
+    Params p = {};
     p.in = in;
     p.nbytes = nbytes;
     p.out = out;
@@ -1137,9 +1693,9 @@ int launch_decode_noalloc(const uint8_t *in, size_t nbytes, uint32_t *out, size_
     p.lead = std::min<uint64_t>(kChunkTiles + kLeadSlack, ntiles);
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(d.sms) * d.occ[delta]);
     if (delta)
-        decode_kernel<true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+        decode_kernel<true, false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
     else
-        decode_kernel<false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+        decode_kernel<false, false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
@@ -1156,6 +1712,21 @@ int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size
                        void *stream)
 {
     return vbk::launch_decode(d_in, nbytes, d_out, n, true, prev, static_cast<cudaStream_t>(stream));
+}
+
+int vbyte_decode_batched(const uint8_t *d_in, size_t nbytes, const uint64_t *d_byte_off, uint32_t *d_out,
+                         size_t n, const uint64_t *d_val_off, size_t num_lists, void *stream)
+{
+    return vbk::launch_decode_batched(d_in, nbytes, d_byte_off, d_out, n, d_val_off, num_lists, nullptr, false,
+                                      static_cast<cudaStream_t>(stream));
+}
+
+int vbyte_decode_delta_batched(const uint8_t *d_in, size_t nbytes, const uint64_t *d_byte_off, uint32_t *d_out,
+                               size_t n, const uint64_t *d_val_off, size_t num_lists, const uint32_t *d_prev,
+                               void *stream)
+{
+    return vbk::launch_decode_batched(d_in, nbytes, d_byte_off, d_out, n, d_val_off, num_lists, d_prev, true,
+                                      static_cast<cudaStream_t>(stream));
 }
 
 int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out, size_t n, int delta,

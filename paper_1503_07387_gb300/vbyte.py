@@ -11,6 +11,8 @@ Names mirror the C ABI in ``include/vbyte.h``:
     decode_delta(d_bytes, n, prev)              ... plus the prefix sum of Sec. 1/4
     decode_host(h_bytes, n, delta, prev)        host buffers in and out
     decode_noalloc(d_bytes, n, delta, prev)     fixed library scratch, no allocation
+    decode_batched(d_bytes, d_bo, d_vo)         lists laid end to end, one launch
+    decode_delta_batched(d_bytes, d_bo, d_vo, d_prev)   ... each list differential
     get_status()                                data-error bits of a stream
 """
 from __future__ import annotations
@@ -29,6 +31,7 @@ ERR_MALFORMED_LONG = 1
 ERR_TRUNCATED = 2
 ERR_COUNT_MISMATCH = 4
 ERR_TIMEOUT = 8
+ERR_BAD_OFFSETS = 16
 
 HEADER = os.path.join(_build.INCLUDE, "vbyte.h")
 
@@ -49,6 +52,8 @@ def _signatures(lib):
         "vbyte_decode": ([P, S, P, S, P], I),
         "vbyte_decode_delta": ([P, S, P, S, U32, P], I),
         "vbyte_decode_host": ([P, S, P, S, I, U32, P], I),
+        "vbyte_decode_batched": ([P, S, P, P, S, P, S, P], I),
+        "vbyte_decode_delta_batched": ([P, S, P, P, S, P, S, P, P], I),
         "vbyte_decode_noalloc": ([P, S, P, S, I, U32, P, P], I),
         "vbyte_get_status": ([P, P], I),
         "vbyte_strerror": ([I], ctypes.c_char_p),
@@ -160,6 +165,56 @@ def decode_delta(data, n: int, prev: int = 0, out=None, stream=None):
                                    ctypes.c_void_p(out.data_ptr()), n,
                                    ctypes.c_uint32(prev & 0xFFFFFFFF), _stream_handle(stream))
     _check(rc, "vbyte_decode_delta")
+    return out
+
+
+def _offsets(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype not in (torch.int64, torch.uint64) \
+            or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA int64/uint64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _batched_args(data, byte_off, val_off, n, out):
+    import torch
+    if not isinstance(data, torch.Tensor) or data.dtype != torch.uint8 or not data.is_cuda \
+            or not data.is_contiguous():
+        raise TypeError("data must be a contiguous CUDA uint8 tensor")
+    if byte_off.numel() != val_off.numel() or byte_off.numel() < 1:
+        raise ValueError("byte_off and val_off must both hold num_lists + 1 entries")
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint32, device=data.device)
+    elif out.dtype not in (torch.uint32, torch.int32) or not out.is_contiguous() or out.numel() < n:
+        raise ValueError("out must be a contiguous 32-bit CUDA tensor with at least n elements")
+    return out, _offsets(byte_off, "byte_off"), _offsets(val_off, "val_off")
+
+
+def decode_batched(data, byte_off, val_off, n: int, out=None, stream=None):
+    """Decode the lists laid end to end in `data` (list j: bytes
+    byte_off[j]..byte_off[j+1], values val_off[j]..val_off[j+1]); n = val_off[-1]."""
+    out, bo, vo = _batched_args(data, byte_off, val_off, n, out)
+    rc = load().vbyte_decode_batched(ctypes.c_void_p(data.data_ptr()), data.numel(), bo,
+                                     ctypes.c_void_p(out.data_ptr()), n, vo, byte_off.numel() - 1,
+                                     _stream_handle(stream))
+    _check(rc, "vbyte_decode_batched")
+    return out
+
+
+def decode_delta_batched(data, byte_off, val_off, n: int, prev=None, out=None, stream=None):
+    """As decode_batched, each list differentially coded from prev[j] (0 if prev is None)."""
+    import torch
+    out, bo, vo = _batched_args(data, byte_off, val_off, n, out)
+    pp = None
+    if prev is not None:
+        if not prev.is_cuda or prev.dtype not in (torch.int32, torch.uint32) or not prev.is_contiguous() \
+                or prev.numel() != byte_off.numel() - 1:
+            raise TypeError("prev must be a contiguous 32-bit CUDA tensor with num_lists entries")
+        pp = ctypes.c_void_p(prev.data_ptr())
+    rc = load().vbyte_decode_delta_batched(ctypes.c_void_p(data.data_ptr()), data.numel(), bo,
+                                           ctypes.c_void_p(out.data_ptr()), n, vo, byte_off.numel() - 1,
+                                           pp, _stream_handle(stream))
+    _check(rc, "vbyte_decode_delta_batched")
     return out
 
 
