@@ -142,6 +142,49 @@ int vbyte_decode_delta_batched(const uint8_t *d_in, size_t nbytes,
                                size_t num_lists, const uint32_t *d_prev,
                                void *stream);
 
+/* ---- batched plans: tuned once, replayed from a CUDA graph -------------- */
+
+/* An opaque, reusable batched decode of one fixed batch (the arguments of
+ * vbyte_decode_batched / vbyte_decode_delta_batched; d_prev is ignored when
+ * delta = 0).  Creation synchronises `stream` (the inputs must be ready),
+ * allocates the plan's own workspace (cudaMalloc), and, when autotune != 0,
+ * picks the batched kernel's launch parameters -- CTAs per SM and how far
+ * counting runs ahead of decoding -- by timing every candidate on this
+ * batch, or reuses the choice made earlier for the same length class
+ * (device, delta, log2 of mean bytes per list, log2 of total bytes).  It then
+ * captures the launch sequence into a CUDA graph.  Creation overwrites
+ * d_out (with the decoded values) while tuning.  A plan may be launched any
+ * number of times; launches of one plan must not overlap on the GPU (they
+ * share its workspace).  Data errors go to the plan's own status word.
+ * Returns VBYTE_EINVAL as vbyte_decode_batched does (and for num_lists = 0),
+ * VBYTE_ENOMEM if the workspace cannot be allocated. */
+typedef struct vbyte_plan vbyte_plan;
+int vbyte_plan_create(vbyte_plan **plan, const uint8_t *d_in, size_t nbytes,
+                      const uint64_t *d_byte_off, uint32_t *d_out, size_t n,
+                      const uint64_t *d_val_off, size_t num_lists,
+                      const uint32_t *d_prev, int delta, int autotune,
+                      void *stream);
+/* Queue the plan's graph on `stream` (cudaGraphLaunch); does not wait. */
+int vbyte_plan_launch(vbyte_plan *plan, void *stream);
+/* Synchronise `stream`, return and clear the plan's VBYTE_ERR_* bits. */
+int vbyte_plan_get_status(vbyte_plan *plan, void *stream, uint32_t *status_out);
+/* The chosen launch parameters (ctas_per_sm 0 = occupancy limit), the tuned
+ * time in ms, and tuned = 0 (defaults), 1 (timed now), 2 (from the cache). */
+int vbyte_plan_describe(const vbyte_plan *plan, int *ctas_per_sm,
+                        uint64_t *lead_slack, float *tuned_ms, int *tuned);
+/* Free the plan's graph and workspace (synchronises the device). */
+void vbyte_plan_destroy(vbyte_plan *plan);
+
+/* The form batched decoding replaces, kept for comparison: one
+ * vbyte_decode / vbyte_decode_delta call per list, queued back to back on
+ * `stream` with no synchronisation in between.  The offsets (and h_prev,
+ * nullable) are in HOST memory here.  Data errors go to the stream's status
+ * word. */
+int vbyte_decode_each(const uint8_t *d_in, const uint64_t *h_byte_off,
+                      uint32_t *d_out, const uint64_t *h_val_off,
+                      size_t num_lists, int delta, const uint32_t *h_prev,
+                      void *stream);
+
 /* End-to-end form of vbyte_decode / vbyte_decode_delta for data in host memory: copies
  * h_in to the device, decodes (differentially when delta != 0) and copies the
  * n values back to h_out, through library-owned device buffers kept per

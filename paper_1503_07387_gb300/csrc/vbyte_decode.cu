@@ -50,6 +50,7 @@
 #include <utility>
 
 #include "vbyte.h"
+#include "vbyte_internal.h"
 
 namespace vbk {
 
@@ -64,7 +65,7 @@ constexpr uint64_t kChunkTiles = 2048;        // tiles per chunk (8 MiB)
 constexpr int kGroupsPerChunk = static_cast<int>(kChunkTiles / kGroup);   // 64
 constexpr int kByteBuf = kHalo + kTile + 16;
 constexpr int kValBuf = kTile + 16;
-constexpr uint64_t kLeadSlack = 1024;         // extra tickets between a chunk's last count and first decode
+constexpr uint64_t kLeadSlack = kDefaultLeadSlack;   // extra tickets between a chunk's last count and first decode
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 static_assert(kGroupsPerChunk <= kThreads && kGroupsPerChunk % 32 == 0, "chunk scan: one thread per group");
 
@@ -1464,11 +1465,6 @@ LayoutSeg layout_seg(uint64_t ntiles)
     return L;
 }
 
-struct DeviceInfo {
-    int sms = 0;
-    int occ[2] = {0, 0};
-    int occ_seg[2] = {0, 0};
-};
 std::map<int, DeviceInfo> g_dev;
 
 int device_info(DeviceInfo *di)
@@ -1540,63 +1536,82 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
 // Batched decoding: lists j in [0, L) are bytes [bo[j], bo[j+1]) of in and
 // values [vo[j], vo[j+1]) of out; the concatenation is decoded as one stream
 // whose running value (delta) restarts at prevs[j] at each list head.
-int launch_decode_batched(const uint8_t *in, size_t nbytes, const uint64_t *bo, uint32_t *out, size_t n,
-                          const uint64_t *vo, size_t L, const uint32_t *prevs, bool delta, cudaStream_t s)
+int check_batch(const BatchArgs &a)
 {
-    if ((nbytes && !in) || (n && !out) || !bo || !vo) return VBYTE_EINVAL;
-    if (reinterpret_cast<uintptr_t>(out) & 3u) return VBYTE_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(bo) | reinterpret_cast<uintptr_t>(vo)) & 7u) return VBYTE_EINVAL;
-    if (prevs && (reinterpret_cast<uintptr_t>(prevs) & 3u)) return VBYTE_EINVAL;
-    if (L == 0 && (nbytes || n)) return VBYTE_EINVAL;
-    if (L == 0) return VBYTE_OK;
-    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
-    const uint64_t ntiles = nbytes ? ((a & 15u) + nbytes + kTile - 1) / kTile : 0;
+    if ((a.nbytes && !a.in) || (a.n && !a.out) || !a.bo || !a.vo) return VBYTE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(a.out) & 3u) return VBYTE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a.bo) | reinterpret_cast<uintptr_t>(a.vo)) & 7u) return VBYTE_EINVAL;
+    if (a.prevs && (reinterpret_cast<uintptr_t>(a.prevs) & 3u)) return VBYTE_EINVAL;
+    if (a.L == 0 && (a.nbytes || a.n)) return VBYTE_EINVAL;
+    return VBYTE_OK;
+}
+
+uint64_t batch_tiles(const BatchArgs &a)
+{
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(a.in);
+    return a.nbytes ? ((addr & 15u) + a.nbytes + kTile - 1) / kTile : 0;
+}
+
+size_t batch_workspace_bytes(const BatchArgs &a) { return layout_seg(batch_tiles(a)).total; }
+
+// Queue the batched decode of a (already checked, L > 0) on s, with its
+// scratch in ws (layout_seg of the batch's tile count).
+int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const DeviceInfo &di, cudaStream_t s)
+{
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(a.in);
+    const uint64_t ntiles = batch_tiles(a);
     const LayoutSeg Y = layout_seg(ntiles);
-    Workspace *w = nullptr;
-    int rc = get_workspace(s, Y.total, &w);
-    if (rc != VBYTE_OK) return rc;
-    DeviceInfo di;
-    rc = device_info(&di);
-    if (rc != VBYTE_OK) return rc;
     Params p = {};
-    p.in = in;
-    p.nbytes = nbytes;
-    p.out = out;
-    p.n = n;
+    p.in = a.in;
+    p.nbytes = a.nbytes;
+    p.out = a.out;
+    p.n = a.n;
     p.ntiles = ntiles;
-    p.base = a & ~static_cast<uintptr_t>(15);
-    p.tdesc = reinterpret_cast<uint64_t *>(w->ptr + Y.tdesc);
-    p.gagg = nullptr;
-    p.gpre = nullptr;
-    p.cnext = reinterpret_cast<uint64_t *>(w->ptr + Y.cnext);
-    p.cdone = reinterpret_cast<unsigned int *>(w->ptr + Y.cdone);
-    p.cready = reinterpret_cast<unsigned int *>(w->ptr + Y.cready);
-    p.ctr = reinterpret_cast<unsigned long long *>(w->ptr + Y.ctr);
-    p.status = reinterpret_cast<uint32_t *>(w->ptr);
-    p.prev = 0u;
-    p.lead = std::min<uint64_t>(kChunkTiles + kLeadSlack, ntiles);
-    p.bo = bo;
-    p.vo = vo;
-    p.prevs = prevs;
-    p.L = L;
-    p.hr = reinterpret_cast<const uint64_t *>(w->ptr + Y.hr);
-    p.tpre = reinterpret_cast<uint64_t *>(w->ptr + Y.tpre);
-    const uint64_t work = std::max<uint64_t>(ntiles, L);
+    p.base = addr & ~static_cast<uintptr_t>(15);
+    p.tdesc = reinterpret_cast<uint64_t *>(ws + Y.tdesc);
+    p.cnext = reinterpret_cast<uint64_t *>(ws + Y.cnext);
+    p.cdone = reinterpret_cast<unsigned int *>(ws + Y.cdone);
+    p.cready = reinterpret_cast<unsigned int *>(ws + Y.cready);
+    p.ctr = reinterpret_cast<unsigned long long *>(ws + Y.ctr);
+    p.status = reinterpret_cast<uint32_t *>(ws);
+    p.lead = std::min<uint64_t>(kChunkTiles + cfg.lead_slack, ntiles);
+    p.bo = a.bo;
+    p.vo = a.vo;
+    p.prevs = a.prevs;
+    p.L = a.L;
+    p.hr = reinterpret_cast<const uint64_t *>(ws + Y.hr);
+    p.tpre = reinterpret_cast<uint64_t *>(ws + Y.tpre);
+    const uint64_t work = std::max<uint64_t>(ntiles, a.L);
     const unsigned pre_grid = static_cast<unsigned>(
         std::min<uint64_t>((work + 255) / 256, static_cast<uint64_t>(di.sms) * 8));
     head_range_kernel<<<std::max(pre_grid, 1u), 256, 0, s>>>(p);
     if (cudaGetLastError() != cudaSuccess) return VBYTE_ECUDA;
-    if (nbytes == 0) {
-        if (n > 0) set_status_kernel<<<1, 1, 0, s>>>(p.status, VBYTE_ERR_COUNT_MISMATCH);
+    if (a.nbytes == 0) {
+        if (a.n > 0) set_status_kernel<<<1, 1, 0, s>>>(p.status, VBYTE_ERR_COUNT_MISMATCH);
         return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
     }
-    if (cudaMemsetAsync(w->ptr + Y.ctr, 0, Y.clear, s) != cudaSuccess) return VBYTE_ECUDA;
-    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ_seg[delta]);
-    if (delta)
+    if (cudaMemsetAsync(ws + Y.ctr, 0, Y.clear, s) != cudaSuccess) return VBYTE_ECUDA;
+    const int occ = di.occ_seg[a.delta];
+    const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
+    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * per_sm);
+    if (a.delta)
         decode_kernel<true, true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
     else
         decode_kernel<false, true><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
+int launch_decode_batched(const BatchArgs &a, cudaStream_t s)
+{
+    int rc = check_batch(a);
+    if (rc != VBYTE_OK || a.L == 0) return rc;
+    Workspace *w = nullptr;
+    rc = get_workspace(s, layout_seg(batch_tiles(a)).total, &w);
+    if (rc != VBYTE_OK) return rc;
+    DeviceInfo di;
+    rc = device_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    return enqueue_batched(a, w->ptr, LaunchCfg(), di, s);
 }
 
 // ---- scratch for vbyte_decode_noalloc -----------------------------------
@@ -1717,16 +1732,16 @@ int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size
 int vbyte_decode_batched(const uint8_t *d_in, size_t nbytes, const uint64_t *d_byte_off, uint32_t *d_out,
                          size_t n, const uint64_t *d_val_off, size_t num_lists, void *stream)
 {
-    return vbk::launch_decode_batched(d_in, nbytes, d_byte_off, d_out, n, d_val_off, num_lists, nullptr, false,
-                                      static_cast<cudaStream_t>(stream));
+    const vbk::BatchArgs a{d_in, nbytes, d_byte_off, d_out, n, d_val_off, num_lists, nullptr, false};
+    return vbk::launch_decode_batched(a, static_cast<cudaStream_t>(stream));
 }
 
 int vbyte_decode_delta_batched(const uint8_t *d_in, size_t nbytes, const uint64_t *d_byte_off, uint32_t *d_out,
                                size_t n, const uint64_t *d_val_off, size_t num_lists, const uint32_t *d_prev,
                                void *stream)
 {
-    return vbk::launch_decode_batched(d_in, nbytes, d_byte_off, d_out, n, d_val_off, num_lists, d_prev, true,
-                                      static_cast<cudaStream_t>(stream));
+    const vbk::BatchArgs a{d_in, nbytes, d_byte_off, d_out, n, d_val_off, num_lists, d_prev, true};
+    return vbk::launch_decode_batched(a, static_cast<cudaStream_t>(stream));
 }
 
 int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out, size_t n, int delta,

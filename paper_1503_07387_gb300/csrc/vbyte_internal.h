@@ -1,0 +1,54 @@
+// Internal interface between the decode kernels (vbyte_decode.cu) and the
+// host runtime built on them (vbyte_runtime.cpp: batched plans, the
+// one-call-per-list form, the serving loop).  Not installed; not part of the
+// C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace vbk {
+
+constexpr uint64_t kDefaultLeadSlack = 1024;
+
+// Per device: SM count and the decode kernels' occupancy (CTAs per SM) for
+// plain / delta, single-stream (occ) and batched (occ_seg).
+struct DeviceInfo {
+    int sms = 0;
+    int occ[2] = {0, 0};
+    int occ_seg[2] = {0, 0};
+};
+
+// One batched decode: list j is bytes [bo[j], bo[j+1]) of in and values
+// [vo[j], vo[j+1]) of out (bo, vo, prevs in device memory).
+struct BatchArgs {
+    const uint8_t *in;
+    size_t nbytes;
+    const uint64_t *bo;
+    uint32_t *out;
+    size_t n;
+    const uint64_t *vo;
+    size_t L;
+    const uint32_t *prevs;
+    bool delta;
+};
+
+// Launch parameters of the batched kernel (the plan autotuner's choices).
+struct LaunchCfg {
+    int ctas_per_sm = 0;                        // 0: the occupancy limit
+    uint64_t lead_slack = kDefaultLeadSlack;    // tickets between a chunk's last count and first decode
+};
+
+int device_info(DeviceInfo *di);
+int check_batch(const BatchArgs &a);
+uint64_t batch_tiles(const BatchArgs &a);
+size_t batch_workspace_bytes(const BatchArgs &a);
+// Queue a checked batch (L > 0) on s with its scratch in ws (at least
+// batch_workspace_bytes(a) bytes; ws[0..4) is the status word).
+int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const DeviceInfo &di, cudaStream_t s);
+// The single-stream call with the per-stream workspace.
+int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
+                  cudaStream_t s);
+
+}  // namespace vbk

@@ -55,6 +55,12 @@ def _signatures(lib):
         "vbyte_decode_batched": ([P, S, P, P, S, P, S, P], I),
         "vbyte_decode_delta_batched": ([P, S, P, P, S, P, S, P, P], I),
         "vbyte_decode_noalloc": ([P, S, P, S, I, U32, P, P], I),
+        "vbyte_plan_create": ([P, P, S, P, P, S, P, S, P, I, I, P], I),
+        "vbyte_plan_launch": ([P, P], I),
+        "vbyte_plan_get_status": ([P, P, P], I),
+        "vbyte_plan_describe": ([P, P, P, P, P], I),
+        "vbyte_plan_destroy": ([P], None),
+        "vbyte_decode_each": ([P, P, P, P, S, I, P, P], I),
         "vbyte_get_status": ([P, P], I),
         "vbyte_strerror": ([I], ctypes.c_char_p),
         "vbyte_workspace_size": ([S], S),
@@ -215,6 +221,74 @@ def decode_delta_batched(data, byte_off, val_off, n: int, prev=None, out=None, s
                                            ctypes.c_void_p(out.data_ptr()), n, vo, byte_off.numel() - 1,
                                            pp, _stream_handle(stream))
     _check(rc, "vbyte_decode_delta_batched")
+    return out
+
+
+class Plan:
+    """A batched decode tuned once and replayed from a CUDA graph
+    (vbyte_plan_*).  Keeps references to every tensor it points at."""
+
+    def __init__(self, data, byte_off, val_off, n: int, delta: bool, prev=None, out=None,
+                 autotune: bool = True, stream=None):
+        import torch
+        out, bo, vo = _batched_args(data, byte_off, val_off, n, out)
+        pp = None
+        if delta and prev is not None:
+            if not prev.is_cuda or prev.dtype not in (torch.int32, torch.uint32) or \
+                    prev.numel() != byte_off.numel() - 1:
+                raise TypeError("prev must be a 32-bit CUDA tensor with num_lists entries")
+            pp = ctypes.c_void_p(prev.data_ptr())
+        self._keep = (data, byte_off, val_off, prev, out)
+        self.out = out
+        h = ctypes.c_void_p()
+        rc = load().vbyte_plan_create(ctypes.byref(h), ctypes.c_void_p(data.data_ptr()), data.numel(), bo,
+                                      ctypes.c_void_p(out.data_ptr()), n, vo, byte_off.numel() - 1, pp,
+                                      int(delta), int(autotune), _stream_handle(stream))
+        _check(rc, "vbyte_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load().vbyte_plan_launch(self._h, _stream_handle(stream)), "vbyte_plan_launch")
+        return self.out
+
+    def get_status(self, stream=None) -> int:
+        v = ctypes.c_uint32(0)
+        _check(load().vbyte_plan_get_status(self._h, _stream_handle(stream), ctypes.byref(v)),
+               "vbyte_plan_get_status")
+        return int(v.value)
+
+    def describe(self) -> dict:
+        c, sl, ms, tu = ctypes.c_int(0), ctypes.c_uint64(0), ctypes.c_float(0), ctypes.c_int(0)
+        _check(load().vbyte_plan_describe(self._h, ctypes.byref(c), ctypes.byref(sl), ctypes.byref(ms),
+                                          ctypes.byref(tu)), "vbyte_plan_describe")
+        return {"ctas_per_sm": c.value, "lead_slack_tiles": int(sl.value), "tuned_ms": round(ms.value, 5),
+                "tuned": {0: "defaults", 1: "timed", 2: "cached for the length class"}[tu.value]}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vbyte_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decode_each(data, h_byte_off: np.ndarray, h_val_off: np.ndarray, n: int, delta: bool, h_prev=None,
+                out=None, stream=None):
+    """One single-stream call per list (host offsets): the form batching replaces."""
+    import torch
+    bo = np.ascontiguousarray(h_byte_off, dtype=np.uint64)
+    vo = np.ascontiguousarray(h_val_off, dtype=np.uint64)
+    pv = None if h_prev is None else np.ascontiguousarray(h_prev, dtype=np.uint32)
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint32, device=data.device)
+    rc = load().vbyte_decode_each(ctypes.c_void_p(data.data_ptr()), _np_ptr(bo), ctypes.c_void_p(out.data_ptr()),
+                                  _np_ptr(vo), bo.size - 1, int(delta), None if pv is None else _np_ptr(pv),
+                                  _stream_handle(stream))
+    _check(rc, "vbyte_decode_each")
     return out
 
 

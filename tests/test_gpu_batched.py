@@ -201,3 +201,55 @@ def test_full_size_posting_lists():
         got, status = _gpu(b, bo, vo, delta, prev if delta else None)
         assert status == 0
         assert np.array_equal(got, want)
+
+
+def test_plan_autotuned_graph_replay_and_cache():
+    import torch
+    ids, vo = inputs.posting_lists(2000, universe=1 << 22, cap=50000, seed=18)
+    prev = inputs.full_range(2000, seed=19)
+    b, bo = oracle.encode_batched(ids, vo, True, prev)
+    want, _ = oracle.decode_batched(b, bo, vo, True, prev)
+    d, dbo, dvo = _dev_bytes(b), _dev_u64(bo), _dev_u64(vo)
+    dp = torch.from_numpy(prev.view(np.int32)).cuda()
+    n = int(vo[-1])
+    plan = vbyte.Plan(d, dbo, dvo, n, True, prev=dp)
+    info = plan.describe()
+    assert info["tuned"] in ("timed", "cached for the length class")
+    for _ in range(2):
+        plan.out.fill_(0)
+        plan.launch()
+        torch.cuda.synchronize()
+        assert np.array_equal(plan.out.cpu().numpy().view(np.uint32), want)
+    assert plan.get_status() == 0
+    # a second plan of the same length class reuses the tuned parameters
+    plan2 = vbyte.Plan(d, dbo, dvo, n, True, prev=dp)
+    assert plan2.describe()["tuned"] == "cached for the length class"
+    assert plan2.describe()["ctas_per_sm"] == info["ctas_per_sm"]
+    plan2.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(plan2.out.cpu().numpy().view(np.uint32), want)
+    plan.close()
+    plan2.close()
+
+
+def test_plan_status_is_its_own():
+    ids, vo, b, bo = _valid_batch()
+    vo = vo.copy()
+    j = int(np.flatnonzero(np.diff(vo) > 1)[20])
+    vo[j + 1] -= 1
+    plan = vbyte.Plan(_dev_bytes(b), _dev_u64(bo), _dev_u64(vo), int(vo[-1]), False, autotune=False)
+    plan.launch()
+    assert plan.get_status() == vbyte.ERR_COUNT_MISMATCH
+    assert vbyte.get_status() == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("delta", [False, True])
+def test_decode_each_matches_oracle(delta):
+    ids, vo = inputs.posting_lists(500, universe=1 << 20, cap=5000, seed=20)
+    prev = inputs.full_range(500, seed=21) if delta else None
+    b, bo = oracle.encode_batched(ids, vo, delta, prev)
+    want, _ = oracle.decode_batched(b, bo, vo, delta, prev)
+    got = vbyte.decode_each(_dev_bytes(b), bo, vo, int(vo[-1]), delta, prev)
+    assert vbyte.get_status() == 0
+    assert np.array_equal(got.cpu().numpy().view(np.uint32), want)
