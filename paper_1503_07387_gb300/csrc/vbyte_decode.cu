@@ -446,21 +446,52 @@ __device__ __forceinline__ Seg warp_seg_incl(Seg x, int lane)
     return x;
 }
 
-// Bitmap of the list heads (byte offsets bo[j], j in [ha, he)) that fall in
-// the staged window of the tile starting at stream offset trel: bit i is
-// staging byte i (the 16 halo bytes first).  All threads take part.
-__device__ __forceinline__ void build_head_bits(const Params &p, long long trel, uint64_t ha, uint64_t he,
-                                                uint32_t *bits)
+// The list heads of a tile in shared memory: a bitmap of their first bytes
+// over the staged window (bit i: staging byte i, the 16 halo bytes first)
+// and, for the first kMaxHeadList lists of the tile's range [ha, he), each
+// list's staging index, x_0 and value offset, so that lookups stay on chip.
+constexpr int kMaxHeadList = 512;
+struct HeadTab {
+    int pos[kMaxHeadList];
+    uint32_t prv[kMaxHeadList];
+    unsigned long long vo[kMaxHeadList];
+    uint32_t bits[kHeadWords];
+};
+
+// Fill T for the tile starting at stream offset trel.  All threads take part.
+__device__ __forceinline__ void build_heads(const Params &p, long long trel, uint64_t ha, uint64_t he, HeadTab &T,
+                                            bool want_prev, bool want_vo)
 {
     const int tid = threadIdx.x;
-    for (int i = tid; i < kHeadWords; i += kThreads) bits[i] = 0u;
+    for (int i = tid; i < kHeadWords; i += kThreads) T.bits[i] = 0u;
     __syncthreads();
     const long long w0 = trel - kHalo;
-    for (uint64_t j = ha + tid; j < he; j += kThreads) {
-        const long long pos = static_cast<long long>(p.bo[j]) - w0;
-        if (pos >= 0 && pos < kHalo + kTile) atomicOr(bits + (pos >> 5), 1u << (pos & 31));
+    const uint64_t nh = he - ha;
+    for (uint64_t i = tid; i < nh; i += kThreads) {
+        const uint64_t j = ha + i;
+        const long long d = static_cast<long long>(p.bo[j]) - w0;
+        if (d >= 0 && d < kHalo + kTile) atomicOr(T.bits + (d >> 5), 1u << (d & 31));
+        if (i < static_cast<uint64_t>(kMaxHeadList)) {
+            T.pos[i] = d < 0 ? -1 : (d > (1 << 30) ? (1 << 30) : static_cast<int>(d));
+            if (want_prev) T.prv[i] = p.prevs ? p.prevs[j] : 0u;
+            if (want_vo) T.vo[i] = p.vo[j];
+        }
     }
     __syncthreads();
+}
+
+// Index of the last table entry whose staging index is <= q (-1 if none).
+__device__ __forceinline__ int tab_last_le(const HeadTab &T, int n, int q)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (T.pos[mid] <= q)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo - 1;
 }
 
 // The 24 staged bytes ending with tid's slice: terminator bits (t24) and head
@@ -507,8 +538,8 @@ __device__ __forceinline__ long long last_list_at(const Params &p, uint64_t ha, 
 // x_0 of the list whose first integer ends at slice bit o (a head_terms bit):
 // that integer starts after the previous terminator; the head bit in between
 // names the list.  srel: stream offset of the slice's first byte.
-__device__ __forceinline__ uint32_t head_prev(const Params &p, const HeadWin &h, int o, long long srel, uint64_t ha,
-                                              uint64_t he)
+__device__ __forceinline__ uint32_t head_prev(const Params &p, const HeadTab &T, const HeadWin &h, int o, int tid,
+                                              long long srel, uint64_t ha, uint64_t he)
 {
     const int P = o + kHeadBack;
     const uint32_t below = h.t24 & ((1u << P) - 1u);
@@ -517,6 +548,11 @@ __device__ __forceinline__ uint32_t head_prev(const Params &p, const HeadWin &h,
     const uint32_t hb = h.h24 & ((2u << P) - 1u) & above_q;   // heads in (q, P]
     if (!hb) return 0u;
     const int k = 31 - __clz(hb);
+    if (he - ha <= static_cast<uint64_t>(kMaxHeadList)) {
+        const int qs = kHalo + tid * kBPT - kHeadBack + k;   // staging index of the head
+        const int i = tab_last_le(T, static_cast<int>(he - ha), qs);
+        return (i >= 0 && T.pos[i] == qs) ? T.prv[i] : 0u;
+    }
     const long long j = last_list_at(p, ha, he, srel - kHeadBack + k);
     if (j < static_cast<long long>(ha) || p.prevs == nullptr) return 0u;
     return p.prevs[j];
@@ -548,14 +584,14 @@ __device__ __forceinline__ void assemble_all_o(const uint32_t *sw, int tid, uint
 
 // Segmented sum of a slice that holds list heads (ht != 0): the sum since the
 // last head, starting from that list's x_0.
-__device__ __forceinline__ uint32_t slice_seg_sum(const Params &p, const uint32_t *sw, int tid, uint32_t tl,
-                                                  uint32_t t20, uint32_t tc, const HeadWin &h, uint32_t ht,
-                                                  long long srel, uint64_t ha, uint64_t he)
+__device__ __forceinline__ uint32_t slice_seg_sum(const Params &p, const HeadTab &T, const uint32_t *sw, int tid,
+                                                  uint32_t tl, uint32_t t20, uint32_t tc, const HeadWin &h,
+                                                  uint32_t ht, long long srel, uint64_t ha, uint64_t he)
 {
     uint32_t s = 0;
     assemble_all_o(sw, tid, tl, t20, tc, [&](int o, uint32_t v) {
         if ((ht >> o) & 1u)
-            s = head_prev(p, h, o, srel, ha, he) + v;
+            s = head_prev(p, T, h, o, tid, srel, ha, he) + v;
         else
             s += v;
     });
@@ -581,7 +617,7 @@ struct Shared {
     // segmented decoding
     alignas(16) unsigned long long hrc[2][2];   // head ranges of the staged count tiles (cp.async targets)
     alignas(16) unsigned long long hrd[2][2];   // head ranges of the staged decode tiles
-    uint32_t hbits[kHeadWords];      // head bitmap of the tile being worked on
+    HeadTab heads;                   // list heads of the tile being worked on
     uint32_t wsf[kWarps];            // count: per-warp "crossed a list head" flags
     uint32_t dsf[kWarps];            // decode: the same
     unsigned long long csc[kWarps];  // segmented chunk scan: per-warp count totals
@@ -640,15 +676,16 @@ __device__ void count_tile(const Params &p, uint64_t t, Shared &S, const uint8_t
             const uint64_t ha = S.hrc[b][0], he = S.hrc[b][1];
             if (ha < he) {   // CTA-uniform
                 const long long trel = static_cast<long long>(tstart) - static_cast<long long>(lo);
-                build_head_bits(p, trel, ha, he, S.hbits);
+                build_heads(p, trel, ha, he, S.heads, true, false);
                 const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
                 const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
                 const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
-                const HeadWin h = head_window(sw, S.hbits, tid, m.tl);
+                const HeadWin h = head_window(sw, S.heads.bits, tid, m.tl);
                 const uint32_t ht = head_terms(h, m.tc);
                 if (ht) {
                     segf = 1u;
-                    vsum = slice_seg_sum(p, sw, tid, m.tl, m.t20, m.tc, h, ht, trel + tid * kBPT, ha, he);
+                    vsum = slice_seg_sum(p, S.heads, sw, tid, m.tl, m.t20, m.tc, h, ht, trel + tid * kBPT, ha,
+                                         he);
                 }
             }
         }
@@ -1101,12 +1138,12 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
     uint32_t ht = 0;
     if constexpr (kSeg) {
         if (ha < he) {   // CTA-uniform
-            build_head_bits(p, trel, ha, he, S.hbits);
-            hw = head_window(sw, S.hbits, tid, m.tl);
+            build_heads(p, trel, ha, he, S.heads, kDelta, true);
+            hw = head_window(sw, S.heads.bits, tid, m.tl);
             if constexpr (kDelta) {
                 ht = head_terms(hw, m.tc);
                 if (ht) {
-                    vsum = slice_seg_sum(p, sw, tid, m.tl, m.t20, m.tc, hw, ht, srel, ha, he);
+                    vsum = slice_seg_sum(p, S.heads, sw, tid, m.tl, m.t20, m.tc, hw, ht, srel, ha, he);
                     notB = true;   // values with restarts take the per-terminator path
                 }
             }
@@ -1163,9 +1200,17 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
                 if (pos < 0 || pos >= static_cast<long long>(p.nbytes)) continue;
                 if (pos > 0 && !((hw.t24 >> (kHeadBack + k - 1)) & 1u)) atomicOr(p.status, VBYTE_ERR_TRUNCATED);
                 const uint64_t rank = R0 + wbase + inc - cnt + __popc(m.tc & ((1u << k) - 1u));
-                for (long long j = last_list_at(p, ha, he, pos); j >= static_cast<long long>(ha); --j) {
-                    if (static_cast<long long>(p.bo[j]) != pos) break;
-                    if (p.vo[j] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+                if (he - ha <= static_cast<uint64_t>(kMaxHeadList)) {
+                    const int qs = kHalo + tid * kBPT + k;
+                    for (int i = tab_last_le(S.heads, static_cast<int>(he - ha), qs); i >= 0; --i) {
+                        if (S.heads.pos[i] != qs) break;
+                        if (S.heads.vo[i] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+                    }
+                } else {
+                    for (long long j = last_list_at(p, ha, he, pos); j >= static_cast<long long>(ha); --j) {
+                        if (static_cast<long long>(p.bo[j]) != pos) break;
+                        if (p.vo[j] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+                    }
                 }
             }
         }
@@ -1187,7 +1232,7 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
     if (ht) {
         assemble_all_o(sw, tid, m.tl, m.t20, m.tc, [&](int o, uint32_t v) {
             if ((ht >> o) & 1u)
-                run = head_prev(p, hw, o, srel, ha, he) + v;
+                run = head_prev(p, S.heads, hw, o, tid, srel, ha, he) + v;
             else
                 run += v;
             *dst++ = run;
@@ -1256,7 +1301,7 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
 // its decode.
 
 template <bool kDelta, bool kSeg>
-__global__ void __launch_bounds__(kThreads) decode_kernel(const Params p)
+__global__ void __launch_bounds__(kThreads, 4) decode_kernel(const Params p)
 {
     __shared__ __align__(16) Shared S;
     const int tid = threadIdx.x;
