@@ -75,6 +75,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device: str) -> float:
+    """The slowest rank's time: every rank's timed region ends at a barrier,
+    and the job took as long as its slowest replica."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
+    """Whole-job throughput in 10^9 units/s: every rank decodes its own replica
+    (weak scaling), so the job processed ws times one rank's units."""
+    return ws * units_per_rank / seconds / 1e9
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1503_07387_gb300", "csrc")
@@ -240,10 +258,7 @@ def run_gpu(args):
     launch_ms = [[ev[0].elapsed_time(ev[1]) for ev in row] for row in per_launch]
     status = vbyte.get_status()
 
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, ws, "cuda")
 
     # ---- end to end through the public host-buffer call (copies inside)
     pinned_in = [torch.from_numpy(s["host"]).pin_memory() for s in streams]
@@ -260,16 +275,16 @@ def run_gpu(args):
         for i, s in enumerate(streams):
             vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
     e2e_s = time.perf_counter() - te
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, ws, "cuda")
     status |= vbyte.get_status()
 
     # ---- batched lists: one tuned, graph-replayed launch vs one call per list
-    batched = None
+    batched = serving = None
     if ws == 1 and not args.no_batched:
-        batched = run_batched(args, measured_peaks())
+        batched, pool = run_batched(args, measured_peaks())
+        if not args.no_serving:
+            serving = run_serving(args, pool)
+        del pool
 
     # ---- CPU baseline (rank 0, N = 1 only): the oracle as it stands
     cpu = None
@@ -287,7 +302,7 @@ def run_gpu(args):
     achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
     src_hash = kernel_source_hash()
     traffic = profiled_traffic(src_hash)
-    value = ws * total_vals * args.steps / (elapsed_ms * 1e-3) / 1e9
+    value = whole_job_rate(total_vals * args.steps, ws, elapsed_ms * 1e-3)
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -323,7 +338,7 @@ def run_gpu(args):
             "kernel_source_hash": src_hash,
         },
         "e2e": {
-            "value": round(ws * total_vals * e2e_steps / e2e_s / 1e9, 3),
+            "value": round(whole_job_rate(total_vals * e2e_steps, ws, e2e_s), 3),
             "unit": UNIT,
             "h2d_bytes_per_step": int(sum(s["host"].size for s in streams)),
             "d2h_bytes_per_step": int(4 * total_vals),
@@ -331,6 +346,7 @@ def run_gpu(args):
         },
         "gpu_launches": len(streams) * args.steps,
         "batched": batched,
+        "serving": serving,
         "status": status,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -409,7 +425,49 @@ def run_batched(args, peaks):
         "status": st_b | st_e,
     }
     plan.close()
-    return res
+    pool = dict(d=d, bo=hbo, vo=vo, prev=prev, lens=np.diff(vo).astype(np.int64))
+    return res, pool
+
+
+def run_serving(args, pool):
+    """Open-loop Poisson query streams against the resident 100,000-list pool:
+    each query names 2..8 lists drawn proportionally to length; continuous
+    batching (gather + one batched launch per batch) against the same loop
+    decoding every list with its own call.  Latency runs from a query's
+    scheduled arrival to the scheduler seeing its batch complete."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(min(free * 0.25, 32 << 30)) // 4096 * 4096
+    cfg = dict(arena_bytes=arena, staging_bytes=512 << 20, max_inflight=4, max_batch_queries=64,
+               max_batch_lists=512)
+    rows = []
+    for rate in args.serve_rates:
+        nq = int(min(max(rate * args.serve_seconds, 200), 40000))
+        arr, qoff, ql = inputs.query_stream(pool["lens"], nq, float(rate), seed=40)
+        vals = int(sum(int(pool["lens"][ql[qoff[i]:qoff[i + 1]]].sum()) for i in range(nq)))
+        row = {"rate_qps": rate, "queries": nq, "values": vals}
+        for form, per_list in (("batched", False), ("per_list", True)):
+            srv = vbyte.Server(pool["d"], pool["bo"], pool["vo"], True, pool["prev"], per_list=per_list, **cfg)
+            w = min(nq, 100)   # untimed warm-up at the same rate
+            srv.replay(arr[:w], qoff[:w + 1], ql[:int(qoff[w])])
+            s0 = srv.stats()
+            t0 = time.perf_counter()
+            lat, st = srv.replay(arr, qoff, ql)
+            span = time.perf_counter() - t0
+            s = srv.stats()
+            s["batches"] -= s0["batches"]
+            srv.close()
+            lat_ms = np.sort(lat) * 1e3
+            row[form] = {"p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                         "qps": round(nq / span, 1), "gints_per_s": round(vals / span / 1e9, 3),
+                         "batches": s["batches"], "status": int(np.bitwise_or.reduce(st)) if st.size else 0}
+        rows.append(row)
+    return {"pool": "the 100,000-list batch above, resident in HBM", "arena_bytes": arena,
+            "config": {k: v for k, v in cfg.items() if k != "arena_bytes"},
+            "latency": "scheduled arrival -> batch completion seen by the scheduler thread",
+            "rates": rows}
 
 
 def cpu_baseline(streams, budget_s=10.0):
@@ -523,6 +581,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000, 50000])
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

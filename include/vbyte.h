@@ -185,6 +185,69 @@ int vbyte_decode_each(const uint8_t *d_in, const uint64_t *h_byte_off,
                       size_t num_lists, int delta, const uint32_t *h_prev,
                       void *stream);
 
+/* ---- serving: a resident pool and a continuous-batching request loop ---- */
+
+/* A server keeps a pool of compressed lists (laid end to end in d_pool, list
+ * j = bytes [h_byte_off[j], h_byte_off[j+1]) holding h_val_off[j+1] -
+ * h_val_off[j] values; offsets in host memory, copied) resident on the
+ * current device and decodes queries, each naming up to max_batch_lists of
+ * its lists, as they arrive.  A scheduler thread admits waiting queries in
+ * arrival order into a batch as long as the batch's decoded output fits in
+ * the free part of a device arena (arena_bytes), its compressed lists fit
+ * the staging buffer (staging_bytes) and the batch limits hold; up to
+ * max_inflight batches run at once, each on its own stream, so queries that
+ * arrive while others are on the GPU start as soon as a slot and arena
+ * space free up.  A batch's lists are gathered end to end on the device and
+ * decoded with one batched launch (per_list = 0), or each list is decoded
+ * with its own vbyte_decode / vbyte_decode_delta call (per_list = 1, the
+ * comparison form).  A query's values (the concatenation of its lists'
+ * values, in the order named) stay in the arena until it is released.  All
+ * device memory is allocated at creation.  The pool and its offsets must
+ * not change while the server lives. */
+typedef struct vbyte_server vbyte_server;
+typedef struct vbyte_server_config {
+    size_t arena_bytes;      /* device memory for decoded outputs */
+    size_t staging_bytes;    /* per in-flight batch: gathered compressed bytes */
+    int max_inflight;        /* batches on the GPU at once */
+    int max_batch_queries;   /* queries per batch */
+    int max_batch_lists;     /* lists per batch (and per query) */
+    int per_list;            /* 1: one single-stream call per list */
+} vbyte_server_config;
+int vbyte_server_create(vbyte_server **srv, const uint8_t *d_pool,
+                        size_t pool_bytes, const uint64_t *h_byte_off,
+                        const uint64_t *h_val_off, size_t num_lists, int delta,
+                        const uint32_t *h_prev, const vbyte_server_config *cfg);
+/* Queue a query (k list indices, host memory); returns at once with its id.
+ * VBYTE_EINVAL if a list index is out of range or the query can never fit
+ * (more lists than max_batch_lists, more bytes than staging_bytes, more
+ * output than arena_bytes). */
+int vbyte_server_submit(vbyte_server *srv, const uint32_t *h_lists, size_t k,
+                        uint64_t *query_id);
+/* Block until the query is decoded; its latency (arrival to completion seen
+ * by the scheduler, seconds) and data-error bits. */
+int vbyte_server_wait(vbyte_server *srv, uint64_t query_id, double *latency_s,
+                      uint32_t *status);
+/* Device pointer to a decoded, unreleased query's n values, and how many
+ * queries shared its batch. */
+int vbyte_server_result(vbyte_server *srv, uint64_t query_id,
+                        uint32_t **d_values, size_t *n,
+                        uint32_t *batch_queries);
+/* Return a decoded query's arena space. */
+int vbyte_server_release(vbyte_server *srv, uint64_t query_id);
+/* Open-loop replay: query i (lists h_query_lists[h_query_off[i] ..
+ * h_query_off[i+1])) arrives h_arrival_s[i] seconds after the call starts;
+ * blocks until all are decoded, writes each latency (from its scheduled
+ * arrival) and status; queries are released as they complete. */
+int vbyte_server_replay(vbyte_server *srv, const uint64_t *h_query_off,
+                        const uint32_t *h_query_lists, size_t num_queries,
+                        const double *h_arrival_s, double *h_latency_s,
+                        uint32_t *h_status);
+/* Batches launched, queries admitted, values and lists decoded so far. */
+int vbyte_server_stats(vbyte_server *srv, uint64_t *batches, uint64_t *queries,
+                       uint64_t *values, uint64_t *lists);
+/* Stop the scheduler, wait for the GPU, free everything. */
+void vbyte_server_destroy(vbyte_server *srv);
+
 /* End-to-end form of vbyte_decode / vbyte_decode_delta for data in host memory: copies
  * h_in to the device, decodes (differentially when delta != 0) and copies the
  * n values back to h_out, through library-owned device buffers kept per

@@ -1646,6 +1646,40 @@ int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
+int reserve_workspace(cudaStream_t s, size_t nbytes)
+{
+    const uint64_t ntiles = (15 + nbytes + kTile - 1) / kTile;
+    const size_t need = std::max(layout(ntiles).total, layout_seg(ntiles).total);
+    Workspace *w = nullptr;
+    return get_workspace(s, need, &w);
+}
+
+int status_word(cudaStream_t s, uint32_t **word)
+{
+    Workspace *w = nullptr;
+    const int rc = get_workspace(s, kWsHead, &w);
+    if (rc == VBYTE_OK) *word = reinterpret_cast<uint32_t *>(w->ptr);
+    return rc;
+}
+
+void release_workspace(cudaStream_t s)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find({dev, reinterpret_cast<uintptr_t>(s)});
+    if (it != g_ws.end()) {
+        if (it->second.ptr) cudaFreeAsync(it->second.ptr, s);
+        g_ws.erase(it);
+    }
+    auto ih = g_hb.find({dev, reinterpret_cast<uintptr_t>(s)});
+    if (ih != g_hb.end()) {
+        if (ih->second.d_in) cudaFreeAsync(ih->second.d_in, s);
+        if (ih->second.d_out) cudaFreeAsync(ih->second.d_out, s);
+        g_hb.erase(ih);
+    }
+}
+
 int launch_decode_batched(const BatchArgs &a, cudaStream_t s)
 {
     int rc = check_batch(a);

@@ -50,5 +50,26 @@ int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const
 // The single-stream call with the per-stream workspace.
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
                   cudaStream_t s);
+// The batched call with the per-stream workspace.
+int launch_decode_batched(const BatchArgs &a, cudaStream_t s);
+// Grow the per-stream workspace of s (current device) for single-stream and
+// batched inputs of up to nbytes, so that later calls need no allocation.
+int reserve_workspace(cudaStream_t s, size_t nbytes);
+// The device status word of s's workspace (allocating a minimal one if none).
+int status_word(cudaStream_t s, uint32_t **word);
+// Free s's workspace (queued on s; call before destroying s).
+void release_workspace(cudaStream_t s);
+
+// A piece of a gather: len bytes from src + src_off to dst + dst_off.
+struct GatherPiece {
+    uint64_t src;
+    uint64_t dst;
+    uint32_t len;
+    uint32_t pad;
+};
+// Load the gather kernel's code now rather than at its first launch.
+int load_gather_kernel();
+// Queue the copy of every piece (device array) from src to dst on s.
+int enqueue_gather(const uint8_t *src, uint8_t *dst, const GatherPiece *d_pieces, size_t num_pieces, cudaStream_t s);
 
 }  // namespace vbk

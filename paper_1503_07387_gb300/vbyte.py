@@ -61,6 +61,14 @@ def _signatures(lib):
         "vbyte_plan_describe": ([P, P, P, P, P], I),
         "vbyte_plan_destroy": ([P], None),
         "vbyte_decode_each": ([P, P, P, P, S, I, P, P], I),
+        "vbyte_server_create": ([P, P, S, P, P, S, I, P, P], I),
+        "vbyte_server_submit": ([P, P, S, P], I),
+        "vbyte_server_wait": ([P, ctypes.c_uint64, P, P], I),
+        "vbyte_server_result": ([P, ctypes.c_uint64, P, P, P], I),
+        "vbyte_server_release": ([P, ctypes.c_uint64], I),
+        "vbyte_server_replay": ([P, P, P, S, P, P, P], I),
+        "vbyte_server_stats": ([P, P, P, P, P], I),
+        "vbyte_server_destroy": ([P], None),
         "vbyte_get_status": ([P, P], I),
         "vbyte_strerror": ([I], ctypes.c_char_p),
         "vbyte_workspace_size": ([S], S),
@@ -267,6 +275,95 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             load().vbyte_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("staging_bytes", ctypes.c_size_t),
+                ("max_inflight", ctypes.c_int), ("max_batch_queries", ctypes.c_int),
+                ("max_batch_lists", ctypes.c_int), ("per_list", ctypes.c_int)]
+
+
+class _DeviceView:
+    """A borrowed device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, False),
+                                         "version": 2}
+
+
+class Server:
+    """vbyte_server_*: a resident pool of compressed lists and a continuous-
+    batching request loop (the scheduler runs in a native thread)."""
+
+    def __init__(self, pool, h_byte_off, h_val_off, delta: bool, h_prev=None, arena_bytes: int = 1 << 30,
+                 staging_bytes: int = 256 << 20, max_inflight: int = 4, max_batch_queries: int = 64,
+                 max_batch_lists: int = 512, per_list: bool = False):
+        import torch
+        if not isinstance(pool, torch.Tensor) or pool.dtype != torch.uint8 or not pool.is_cuda:
+            raise TypeError("pool must be a CUDA uint8 tensor")
+        self._bo = np.ascontiguousarray(h_byte_off, dtype=np.uint64)
+        self._vo = np.ascontiguousarray(h_val_off, dtype=np.uint64)
+        self._pv = None if h_prev is None else np.ascontiguousarray(h_prev, dtype=np.uint32)
+        self._pool = pool
+        cfg = _ServerConfig(arena_bytes, staging_bytes, max_inflight, max_batch_queries, max_batch_lists,
+                            int(per_list))
+        h = ctypes.c_void_p()
+        rc = load().vbyte_server_create(ctypes.byref(h), ctypes.c_void_p(pool.data_ptr()), pool.numel(),
+                                        _np_ptr(self._bo), _np_ptr(self._vo), self._bo.size - 1, int(delta),
+                                        None if self._pv is None else _np_ptr(self._pv), ctypes.byref(cfg))
+        _check(rc, "vbyte_server_create")
+        self._h = h
+
+    def submit(self, lists) -> int:
+        a = np.ascontiguousarray(lists, dtype=np.uint32)
+        q = ctypes.c_uint64(0)
+        _check(load().vbyte_server_submit(self._h, _np_ptr(a), a.size, ctypes.byref(q)), "vbyte_server_submit")
+        return int(q.value)
+
+    def wait(self, qid: int):
+        lat, st = ctypes.c_double(0), ctypes.c_uint32(0)
+        _check(load().vbyte_server_wait(self._h, qid, ctypes.byref(lat), ctypes.byref(st)), "vbyte_server_wait")
+        return float(lat.value), int(st.value)
+
+    def result(self, qid: int):
+        """(values as a borrowed CUDA int32 tensor, queries in its batch); valid until release."""
+        import torch
+        p, n, bq = ctypes.c_void_p(), ctypes.c_size_t(0), ctypes.c_uint32(0)
+        _check(load().vbyte_server_result(self._h, qid, ctypes.byref(p), ctypes.byref(n), ctypes.byref(bq)),
+               "vbyte_server_result")
+        if n.value == 0:
+            return torch.zeros(0, dtype=torch.int32, device=self._pool.device), int(bq.value)
+        return torch.as_tensor(_DeviceView(p.value, n.value), device=self._pool.device), int(bq.value)
+
+    def release(self, qid: int):
+        _check(load().vbyte_server_release(self._h, qid), "vbyte_server_release")
+
+    def replay(self, arrival_s, query_off, query_lists):
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        qo = np.ascontiguousarray(query_off, dtype=np.uint64)
+        ql = np.ascontiguousarray(query_lists, dtype=np.uint32)
+        lat = np.zeros(arr.size, dtype=np.float64)
+        st = np.zeros(arr.size, dtype=np.uint32)
+        _check(load().vbyte_server_replay(self._h, _np_ptr(qo), _np_ptr(ql), arr.size, _np_ptr(arr),
+                                          _np_ptr(lat), _np_ptr(st)), "vbyte_server_replay")
+        return lat, st
+
+    def stats(self) -> dict:
+        b, q, v, l_ = (ctypes.c_uint64(0) for _ in range(4))
+        _check(load().vbyte_server_stats(self._h, ctypes.byref(b), ctypes.byref(q), ctypes.byref(v),
+                                         ctypes.byref(l_)), "vbyte_server_stats")
+        return {"batches": b.value, "queries": q.value, "values": v.value, "lists": l_.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vbyte_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
