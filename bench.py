@@ -332,7 +332,7 @@ def run_gpu(args):
             "frac": round(achieved / peak_gbs, 4),
             "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
             "traffic": traffic,
-            "kernel": "decode_kernel<delta>" if all(s["delta"] for s in streams) else "decode_kernel",
+            "kernel": "sdecode_kernel<delta>" if all(s["delta"] for s in streams) else "sdecode_kernel",
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": round(avg_launch_ms, 5),
             "kernel_source_hash": src_hash,

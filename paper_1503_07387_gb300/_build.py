@@ -81,12 +81,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
 
 def ptxas_report(src: str | None = None) -> str:
-    """Register / spill / shared-memory usage from ptxas (-Xptxas -v)."""
+    """Register / spill / shared-memory usage from ptxas (-Xptxas -v), for one
+    source or every .cu file."""
     nvcc = _nvcc()
-    src = src or os.path.join(CSRC, "vbyte_decode.cu")
-    cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-Xptxas", "-v", "-c", src, "-o", os.devnull]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    return r.stdout + r.stderr
+    srcs = [src] if src else sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    out = []
+    for f in srcs:
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-Xptxas", "-v", "-c", f, "-o", os.devnull]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        out.append(r.stdout + r.stderr)
+    return "".join(out)
 
 
 if __name__ == "__main__":  # pragma: no cover

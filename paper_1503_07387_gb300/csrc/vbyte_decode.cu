@@ -51,14 +51,13 @@
 
 #include "vbyte.h"
 #include "vbyte_internal.h"
+#include "vbyte_device.cuh"
 
 namespace vbk {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kBPT = 16;                      // input bytes per thread
 constexpr int kTile = kThreads * kBPT;        // input bytes per tile (4 KiB)
-constexpr int kHalo = 16;                     // bytes staged before the tile
 constexpr int kRoundVals = kThreads * 4;      // values per copy-out round
 constexpr int kGroup = 32;                    // tiles per group
 constexpr uint64_t kChunkTiles = 2048;        // tiles per chunk (8 MiB)
@@ -66,7 +65,6 @@ constexpr int kGroupsPerChunk = static_cast<int>(kChunkTiles / kGroup);   // 64
 constexpr int kByteBuf = kHalo + kTile + 16;
 constexpr int kValBuf = kTile + 16;
 constexpr uint64_t kLeadSlack = kDefaultLeadSlack;   // extra tickets between a chunk's last count and first decode
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
 static_assert(kGroupsPerChunk <= kThreads && kGroupsPerChunk % 32 == 0, "chunk scan: one thread per group");
 
 enum : uint32_t { kClassA = 0, kClassB = 1, kClassC = 2 };
@@ -102,71 +100,6 @@ struct Params {
 constexpr int kHeadBack = 8;
 constexpr int kHeadWords = (kHalo + kTile) / 32 + 2;   // head bitmap of a staged tile
 
-// ---------------------------------------------------------------- helpers --
-
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
-{
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
-__device__ __forceinline__ void st_quad(uint32_t *p, uint4 v)
-{
-    asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Wait until at most one committed group of this thread is still in flight.
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Fire-and-forget increment with release semantics: every global write this
-// thread made before is visible to whoever observes the new value.
-__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// One thread waits (acquire) until *flag != 0, bounded by the global timer;
-// on expiry the status word gets VBYTE_ERR_TIMEOUT and the caller carries on.
-__device__ __forceinline__ void spin_flag(const unsigned int *flag, uint32_t *status)
-{
-    uint64_t t0 = 0;
-    for (int spin = 0; ld_acquire_u32(flag) == 0u; ++spin) {
-        const uint64_t now = global_ns();
-        if (t0 == 0) t0 = now;
-        if (now - t0 > kWaitLimitNs) {
-            atomicOr(status, VBYTE_ERR_TIMEOUT);
-            break;
-        }
-        if (spin > 4) __nanosleep(200);
-    }
-}
-
 // Thread 0 waits until *flag != 0 (bounded by the global timer; on expiry the
 // status word gets VBYTE_ERR_TIMEOUT and the caller carries on), then the CTA
 // syncs.  The flag is set after __threadfence() by a CTA that holds a ticket
@@ -175,142 +108,6 @@ __device__ __forceinline__ void wait_flag(const unsigned int *flag, uint32_t *st
 {
     if (threadIdx.x == 0) spin_flag(flag, status);
     __syncthreads();
-}
-
-// Bit i of the result is 1 iff byte i of w has its high bit clear (a
-// terminator).  The multiply moves bits 7, 15, 23, 31 to bits 28..31; the
-// other partial products land on distinct lower bits, so nothing carries.
-__device__ __forceinline__ uint32_t term4(uint32_t w)
-{
-    return ((~w & 0x80808080u) * 0x00204081u) >> 28;
-}
-
-// Value of an integer of L bytes (1..5) whose terminator byte is x and whose
-// preceding four stream bytes are lo4 (byte q-4 in bits 0..7).  The 7-bit
-// groups of lo4 are compacted into 28 bits, x is put on top (a 35-bit
-// number), and the groups that belong to earlier integers fall off the low
-// end with one funnel shift.  For L = 5 the top of x lands above bit 31 and is
-// dropped: Algorithm 1's b * 2^28 modulo 2^32.
-__device__ __forceinline__ uint32_t assemble(uint32_t lo4, uint32_t x, int L)
-{
-    const uint32_t t = (lo4 & 0x007F007Fu) | ((lo4 >> 1) & 0x3F803F80u);
-    const uint32_t u = (t & 0x00003FFFu) | ((t >> 2) & 0x0FFFC000u);
-    return __funnelshift_r(u | (x << 28), x >> 4, 35 - 7 * L);
-}
-
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(~0u, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-__device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t x, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(~0u, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-__device__ __forceinline__ uint64_t warp_sum64(uint64_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
-    return v;
-}
-
-__device__ __forceinline__ uint32_t byte_sum4(uint4 w)
-{
-    return __dp4a(w.x, 0x01010101u, __dp4a(w.y, 0x01010101u, __dp4a(w.z, 0x01010101u,
-                                                                      __dp4a(w.w, 0x01010101u, 0u))));
-}
-
-__device__ __forceinline__ uint4 bytes_as_values(uint32_t x)
-{
-    return make_uint4(prmt(x, 0u, 0x4440u), prmt(x, 0u, 0x4441u), prmt(x, 0u, 0x4442u),
-                      prmt(x, 0u, 0x4443u));
-}
-
-// 0xFF in byte i of the result iff bit i of the nibble m is set.
-__device__ __forceinline__ uint32_t nibble_to_bytes(uint32_t m)
-{
-    return ((m * 0x00204081u) & 0x01010101u) * 0xFFu;
-}
-
-// Codes of at most two bytes (SWAR over one 4-byte word c, wp the word before
-// it): lob holds each integer's low 7-bit group and hib its high byte, at the
-// position of the integer's terminator.
-struct Pairs {
-    uint32_t lob, hib;
-};
-
-__device__ __forceinline__ Pairs pairs_le2(uint32_t wp, uint32_t c)
-{
-    const uint32_t s = __funnelshift_l(wp, c, 8);   // byte i: the byte before byte i
-    const uint32_t cm = prmt(s, 0u, 0xBA98u);        // 0xFF where that byte continues
-    Pairs r;
-    r.lob = (s & 0x7F7F7F7Fu & cm) | (c & ~cm);
-    r.hib = c & cm;
-    return r;
-}
-
-// Sum of the values whose terminators are marked in tc, for a thread whose
-// codes are all at most two bytes long.
-__device__ __forceinline__ uint32_t sum_le2(uint4 w, uint32_t wprev, uint32_t tc)
-{
-    const uint32_t c4[4] = {w.x, w.y, w.z, w.w};
-    uint32_t wp = wprev, s = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const Pairs pr = pairs_le2(wp, c4[j]);
-        const uint32_t tm = nibble_to_bytes((tc >> (4 * j)) & 0xFu);
-        s += __dp4a(pr.lob & tm, 0x01010101u, 0u) + (__dp4a(pr.hib & tm, 0x01010101u, 0u) << 7);
-        wp = c4[j];
-    }
-    return s;
-}
-
-// Per-terminator assembly for codes of any length.  Calls emit(value) for each
-// terminator marked in tc, in order.  t20 bits 0..3 describe the four bytes
-// before the thread's slice, bits 4..19 the slice; sw is the staged tile.
-template <typename F>
-__device__ __forceinline__ void assemble_all(const uint32_t *sw, int tid, uint32_t tl, uint32_t t20,
-                                             uint32_t tc, F emit)
-{
-    uint32_t m = tl;
-    int prevo = 27 - __clz(t20 & 0xFu);   // last terminator before my bytes (-5: none)
-    while (m) {
-        const int o = __ffs(m) - 1;
-        m &= m - 1u;
-        const int L = min(o - prevo, 5);
-        prevo = o;
-        if ((tc >> o) & 1u) {
-            const int q = kHalo + tid * kBPT + o;   // staging byte of the terminator
-            const uint32_t A = sw[(q >> 2) - 1];
-            const uint32_t B = sw[q >> 2];
-            const uint32_t lo4 = __funnelshift_r(A, B, 8 * q);
-            const uint32_t x = (B >> (8 * (q & 3))) & 0xFFu;
-            emit(assemble(lo4, x, L));
-        }
-    }
-}
-
-// Bit j set iff byte va + j lies inside [lo, hi).
-__device__ __forceinline__ uint32_t slice_valid(uintptr_t va, uintptr_t lo, uintptr_t hi)
-{
-    if (va >= lo && va + kBPT <= hi) return 0xFFFFu;
-    const long long a = static_cast<long long>(lo) - static_cast<long long>(va);
-    const long long z = static_cast<long long>(hi) - static_cast<long long>(va);
-    const int first = a > 0 ? (a > kBPT ? kBPT : static_cast<int>(a)) : 0;
-    const int last = z > 0 ? (z > kBPT ? kBPT : static_cast<int>(z)) : 0;
-    if (last <= first) return 0u;
-    return ((1u << last) - 1u) & ~((1u << first) - 1u);
 }
 
 // Stage tile t into `bytes`: bytes[16 + 16*tid ..] gets tid's 16-byte slice
@@ -347,71 +144,6 @@ __device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid
     }
     if (tid == kThreads - 1)
         *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
-}
-
-// Terminator masks of tid's 16-byte slice of a staged tile.
-struct SliceMasks {
-    uint4 w;          // the slice
-    uint32_t wprev;   // the 4 bytes before it
-    uint32_t tl;      // terminator bits of the slice
-    uint32_t t20;     // bits 0..3: the 4 bytes before, 4..19: the slice
-    uint32_t tc;      // terminators inside the stream
-};
-
-__device__ __forceinline__ SliceMasks slice_masks(const uint8_t *bt, int tid, bool interior, uintptr_t va,
-                                                  uintptr_t lo, uintptr_t hi)
-{
-    SliceMasks m;
-    m.w = *reinterpret_cast<const uint4 *>(bt + kHalo + tid * kBPT);
-    m.wprev = reinterpret_cast<const uint32_t *>(bt)[(kHalo + tid * kBPT) / 4 - 1];
-    m.tl = term4(m.w.x) | (term4(m.w.y) << 4) | (term4(m.w.z) << 8) | (term4(m.w.w) << 12);
-    m.t20 = term4(m.wprev) | (m.tl << 4);
-    m.tc = interior ? m.tl : (m.tl & slice_valid(va, lo, hi));
-    return m;
-}
-
-// Sum of the values whose terminators lie in a thread's slice, for a thread
-// whose codes are at most two bytes (every continuation byte is followed by
-// its terminator): the 7-bit payloads of the bytes of those values plus 127
-// times each two-byte value's high byte.  The byte before the slice belongs
-// to my first value when it is a continuation byte; my last byte belongs to
-// the next slice's first value when it is one.
-__device__ __forceinline__ uint32_t sum_le2_fast(uint4 w, uint32_t wprev)
-{
-    const uint32_t c4[4] = {w.x, w.y, w.z, w.w};
-    uint32_t s = 0, hi = 0, wp = wprev;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint32_t c = c4[j];
-        s = __dp4a(c & 0x7F7F7F7Fu, 0x01010101u, s);
-        const uint32_t sh = __funnelshift_l(wp, c, 8);      // byte i: the byte before byte i
-        hi = __dp4a(c & prmt(sh, 0u, 0xBA98u), 0x01010101u, hi);
-        wp = c;
-    }
-    if (wprev & 0x80000000u) s += (wprev >> 24) & 0x7Fu;   // my first value started earlier
-    if (w.w & 0x80000000u) s -= (w.w >> 24) & 0x7Fu;       // my last byte starts the next value
-    return s + 127u * hi;
-}
-
-// Per-thread count and (delta) value sum of the integers ending in its slice.
-template <bool kDelta>
-__device__ __forceinline__ void slice_count_sum(const SliceMasks &m, const uint32_t *sw, int tid, bool interior,
-                                                uint32_t &cnt, uint32_t &vsum, bool &notB)
-{
-    cnt = __popc(m.tc);
-    const uint32_t c20 = ~m.t20 & 0xFFFFFu;   // continuation bytes
-    const bool notA = !interior || (c20 & 0xFFFF8u);
-    notB = (c20 & (c20 << 1) & 0xFFFF8u) != 0;
-    vsum = 0;
-    if (kDelta) {
-        if (!notA) {
-            vsum = byte_sum4(m.w);
-        } else if (!notB) {
-            vsum = interior ? sum_le2_fast(m.w, m.wprev) : sum_le2(m.w, m.wprev, m.tc);
-        } else {
-            assemble_all(sw, tid, m.tl, m.t20, m.tc, [&](uint32_t v) { vsum += v; });
-        }
-    }
 }
 
 // ---- segmented sums (batched differential decoding) ----------------------
@@ -1532,49 +1264,17 @@ int device_info(DeviceInfo *di)
     return VBYTE_OK;
 }
 
-int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                  cudaStream_t s)
+int stream_workspace(cudaStream_t s, size_t need, uint8_t **ptr)
 {
-    if (nbytes == 0 && n == 0) return VBYTE_OK;
-    if ((nbytes && !in) || (n && !out)) return VBYTE_EINVAL;
-    if (reinterpret_cast<uintptr_t>(out) & 3u) return VBYTE_EINVAL;
-    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
-    const uint64_t ntiles = nbytes ? ((a & 15u) + nbytes + kTile - 1) / kTile : 0;
-    const Layout L = layout(ntiles);
     Workspace *w = nullptr;
-    int rc = get_workspace(s, L.total, &w);
-    if (rc != VBYTE_OK) return rc;
-    uint32_t *status = reinterpret_cast<uint32_t *>(w->ptr);
-    if (nbytes == 0) {   // n > 0 values expected from an empty stream
-        set_status_kernel<<<1, 1, 0, s>>>(status, VBYTE_ERR_COUNT_MISMATCH);
-        return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
-    }
-    DeviceInfo di;
-    rc = device_info(&di);
-    if (rc != VBYTE_OK) return rc;
-    if (cudaMemsetAsync(w->ptr + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
-    Params p = {};
-    p.in = in;
-    p.nbytes = nbytes;
-    p.out = out;
-    p.n = n;
-    p.ntiles = ntiles;
-    p.base = a & ~static_cast<uintptr_t>(15);
-    p.tdesc = reinterpret_cast<uint64_t *>(w->ptr + L.tdesc);
-    p.gagg = reinterpret_cast<unsigned long long *>(w->ptr + L.gagg);
-    p.gpre = reinterpret_cast<uint64_t *>(w->ptr + L.gpre);
-    p.cnext = reinterpret_cast<uint64_t *>(w->ptr + L.cnext);
-    p.cdone = reinterpret_cast<unsigned int *>(w->ptr + L.cdone);
-    p.cready = reinterpret_cast<unsigned int *>(w->ptr + L.cready);
-    p.ctr = reinterpret_cast<unsigned long long *>(w->ptr + L.ctr);
-    p.status = status;
-    p.prev = prev;
-    p.lead = std::min<uint64_t>(kChunkTiles + kLeadSlack, ntiles);
-    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
-    if (delta)
-        decode_kernel<true, false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
-    else
-        decode_kernel<false, false><<<static_cast<unsigned>(grid), kThreads, 0, s>>>(p);
+    const int rc = get_workspace(s, need, &w);
+    if (rc == VBYTE_OK) *ptr = w->ptr;
+    return rc;
+}
+
+int set_status_async(uint32_t *status, uint32_t bits, cudaStream_t s)
+{
+    set_status_kernel<<<1, 1, 0, s>>>(status, bits);
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
@@ -1649,7 +1349,7 @@ int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const
 int reserve_workspace(cudaStream_t s, size_t nbytes)
 {
     const uint64_t ntiles = (15 + nbytes + kTile - 1) / kTile;
-    const size_t need = std::max(layout(ntiles).total, layout_seg(ntiles).total);
+    const size_t need = std::max(wdecode_workspace_bytes(nbytes), layout_seg(ntiles).total);
     Workspace *w = nullptr;
     return get_workspace(s, need, &w);
 }
@@ -1899,7 +1599,7 @@ const char *vbyte_strerror(int code)
 size_t vbyte_workspace_size(size_t nbytes)
 {
     const uint64_t ntiles = (15 + nbytes + vbk::kTile - 1) / vbk::kTile;
-    return vbk::layout(ntiles).total;
+    return std::max(vbk::wdecode_workspace_bytes(nbytes), vbk::layout_seg(ntiles).total);
 }
 
 }  // extern "C"

@@ -47,6 +47,13 @@ size_t batch_workspace_bytes(const BatchArgs &a);
 // Queue a checked batch (L > 0) on s with its scratch in ws (at least
 // batch_workspace_bytes(a) bytes; ws[0..4) is the status word).
 int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const DeviceInfo &di, cudaStream_t s);
+// The per-stream workspace of s (current device) with at least need bytes;
+// its first 4 bytes are the stream's status word.
+int stream_workspace(cudaStream_t s, size_t need, uint8_t **ptr);
+// OR bits into a device status word, on s.
+int set_status_async(uint32_t *status, uint32_t bits, cudaStream_t s);
+// Workspace bytes of the single-stream decoder for an nbytes input.
+size_t wdecode_workspace_bytes(size_t nbytes);
 // The single-stream call with the per-stream workspace.
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
                   cudaStream_t s);

@@ -1,0 +1,690 @@
+// Single-stream decoder (vbyte_decode, vbyte_decode_delta).
+//
+// Operation (arXiv 1503.07387): Algorithm 1 (Sec. 2) on a VByte byte stream
+// (Sec. 1, Table 1), optionally followed by the prefix sum that undoes
+// differential coding (Sec. 1 "Differential coding", Sec. 4).
+//
+// Design: count, then decode, with the input read from HBM once; two CTA
+// barriers per 4 KiB tile.
+//   * The stream is cut into 4 KiB tiles aligned to 16 bytes in absolute
+//     address space; a tile owns the integers whose terminator byte lies in
+//     it; the 16 bytes before it are staged too, so an integer that starts
+//     up to four bytes earlier is assembled by the tile holding its
+//     terminator.
+//   * Persistent CTAs take tickets; ticket k counts tile k and, from ticket
+//     `lead` (one 8 MiB chunk plus slack) on, decodes tile k - lead.  The
+//     next ticket's tiles travel with cp.async while the current one is
+//     processed.
+//   * Count (a): per warp, terminator counts and (delta) value sums of its
+//     slices; after the iteration's middle barrier one warp publishes the
+//     tile's descriptor, adds it to its group's aggregates and releases the
+//     chunk's counter.  The data-error contract is checked here.
+//   * Chunk scan: the CTA whose count completes a chunk (its acquire-release
+//     increment of the chunk's counter returns the last value) scans the
+//     chunk's 64 group aggregates at the start of its next iteration, once
+//     the chunk before it is scanned -- before the chunk's first decode
+//     ticket, and before any decode of its own that could wait on it.
+//   * Decode (b, c): the tile prefix is the group prefix plus the earlier
+//     tiles of the group (staged an iteration ahead by warp 0).  Each warp
+//     stages its 512 bytes' values in its own buffer -- one-byte integers
+//     straight from the bytes, codes of at most two bytes by a SWAR byte-pair
+//     merge, longer codes by per-terminator assembly, each value assembled
+//     once, then (delta) running sums relative to the warp's first value.
+//     One barrier exchanges the per-warp totals (and the count partials and
+//     the prefix); then each warp adds its base and writes its rank range
+//     with coalesced 16-byte stores.
+// Every wait is on work of a CTA holding an earlier ticket; each is bounded
+// by the global timer (VBYTE_ERR_TIMEOUT on expiry).
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "vbyte.h"
+#include "vbyte_device.cuh"
+#include "vbyte_internal.h"
+
+namespace vbk {
+namespace sd {
+
+constexpr int kLanes = 32;
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * kLanes;
+constexpr int kTile = kThreads * kBPT;          // 4 KiB per tile
+constexpr int kWarpBytes = kLanes * kBPT;       // 512 bytes per warp
+constexpr int kGroup = 32;                      // tiles per group
+constexpr uint64_t kChunk = 2048;               // tiles per chunk (8 MiB)
+constexpr int kGroupsPerChunk = static_cast<int>(kChunk / kGroup);   // 64
+constexpr uint64_t kSlack = 2560;               // tickets between a chunk's last count ticket and its first decode
+constexpr int kByteBuf = kHalo + kTile + 16;
+constexpr int kWarpValBuf = kWarpBytes + 16;    // staged values of one warp (528)
+constexpr int kStages = 2;                      // tickets in flight per CTA (processed + staged)
+static_assert(kGroupsPerChunk <= kThreads && kGroupsPerChunk % 32 == 0, "chunk scan: one thread per group");
+
+struct Params {
+    const uint8_t *in;
+    uint64_t nbytes;
+    uint32_t *out;
+    uint64_t n;
+    uint64_t ntiles;
+    uintptr_t base;            // 16-byte aligned address of tile 0
+    uint64_t *tdesc;           // per tile: count, value sum
+    unsigned long long *gagg;  // per group: count, value sum (atomic accumulators)
+    uint64_t *gpre;            // per group: values before it, running x before it
+    uint64_t *cnext;           // per chunk: values and running x after it
+    unsigned int *cdone;       // per chunk: tiles counted
+    unsigned int *cready;      // per chunk: group prefixes published
+    unsigned long long *ctr;   // tickets
+    uint32_t *status;
+    uint32_t prev;             // x_0
+    uint64_t lead;             // tickets [0, lead) only count
+};
+
+struct Shared {
+    alignas(16) uint8_t cbytes[kStages][kByteBuf];   // staged tiles to count
+    alignas(16) uint8_t dbytes[kStages][kByteBuf];   // staged tiles to decode
+    alignas(16) uint32_t vals[kWarps][kWarpValBuf];  // general warps: values at rank + sh
+    uint32_t ccnt[kWarps], csum[kWarps];           // count: per-warp totals
+    uint32_t dcnt[kWarps], dsum[kWarps];           // decode: per-warp totals
+    unsigned long long R0;                         // decode: values before the tile
+    uint32_t S0;                                   // decode: running x before the tile
+    alignas(16) ulonglong2 pdesc[kStages][kGroup];   // prefetched: earlier tiles of the decode tile's group
+    alignas(16) ulonglong2 pgpre[kStages];         // prefetched: the group's prefix
+    uint32_t pf[kStages];                          // prefetch issued for this buffer
+    unsigned long long tnext;                      // the ticket to stage next
+    unsigned long long tinit[2];                   // the first two tickets
+    unsigned long long gsc[kWarps];                // chunk scan
+    uint32_t gss[kWarps];
+    long long scan_c;                              // chunk this CTA completed (scans it), or -1
+};
+static_assert(offsetof(Shared, cbytes) % 16 == 0 && kByteBuf % 16 == 0, "cbytes alignment");
+static_assert(offsetof(Shared, dbytes) % 16 == 0 && offsetof(Shared, vals) % 16 == 0, "dbytes/vals alignment");
+static_assert((kWarpValBuf * 4) % 16 == 0, "per-warp value buffers keep 16-byte alignment");
+static_assert(offsetof(Shared, pdesc) % 16 == 0 && offsetof(Shared, pgpre) % 16 == 0, "prefix buffers alignment");
+
+// Stage tile t (its 16-byte slices, the 16 bytes before it, zeros outside
+// the stream) into `bytes`; the caller commits, waits and syncs.
+__device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid, uint8_t *bytes)
+{
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+    uint8_t *dst = bytes + kHalo + tid * kBPT;
+    if (va >= lo && va + kBPT <= hi) {
+        cp_async16(dst, reinterpret_cast<const void *>(va));
+    } else {
+        uint32_t wb[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const uintptr_t ad = va + j;
+            if (ad >= lo && ad < hi)
+                wb[j >> 2] |= static_cast<uint32_t>(*reinterpret_cast<const uint8_t *>(ad)) << (8 * (j & 3));
+        }
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+    }
+    if (tid == 0) {
+        if (t > 0)
+            cp_async16(bytes, reinterpret_cast<const void *>(tstart - 16));
+        else
+            *reinterpret_cast<uint4 *>(bytes) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == kThreads - 1) *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// ---- counting
+
+template <bool kDelta>
+__device__ __forceinline__ void count_partials(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
+    const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
+    uint32_t cnt, vsum = 0;
+    if (interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u)) {
+        cnt = kBPT;   // one-byte integers only
+        if (kDelta) vsum = byte_sum4(w0);
+    } else {
+        const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+        const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
+        cnt = __popc(m.tc);
+        const uint32_t c20 = ~m.t20 & 0xFFFFFu;
+        if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
+            atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
+        if (t == p.ntiles - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((m.tl >> (hi - 1 - va)) & 1u))
+            atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+        if (kDelta) {
+            if (interior && !(c20 & (c20 << 1) & 0xFFFF8u))
+                vsum = sum_le2_fast(m.w, m.wprev);
+            else
+                assemble_all(reinterpret_cast<const uint32_t *>(bytes), tid, m.tl, m.t20, m.tc,
+                             [&](uint32_t v) { vsum += v; });
+        }
+    }
+    const uint32_t wc = __reduce_add_sync(~0u, cnt);
+    const uint32_t ws = kDelta ? __reduce_add_sync(~0u, vsum) : 0u;
+    if (lane == 0) {
+        S.ccnt[warp] = wc;
+        S.csum[warp] = ws;
+    }
+}
+
+// One warp, after the middle barrier: publish tile t's totals.  Lane 0
+// returns the chunk counter's old value (read an iteration later).
+template <bool kDelta>
+__device__ __forceinline__ unsigned int count_publish(const Params &p, uint64_t t, const Shared &S, int lane)
+{
+    const uint32_t tc = __reduce_add_sync(~0u, lane < kWarps ? S.ccnt[lane] : 0u);
+    const uint32_t ts = kDelta ? __reduce_add_sync(~0u, lane < kWarps ? S.csum[lane] : 0u) : 0u;
+    unsigned int old = 0;
+    if (lane == 0) {
+        const uint64_t g = t / kGroup;
+        *reinterpret_cast<ulonglong2 *>(p.tdesc + 2 * t) = make_ulonglong2(tc, ts);
+        atomicAdd(p.gagg + 2 * g, static_cast<unsigned long long>(tc));
+        if (kDelta) atomicAdd(p.gagg + 2 * g + 1, static_cast<unsigned long long>(ts));
+        old = atom_add_acq_rel(p.cdone + t / kChunk, 1u);
+    }
+    return old;
+}
+
+// ---- chunk scan (whole CTA)
+
+__device__ __forceinline__ uint64_t chunk_tiles(const Params &p, long long c)
+{
+    const uint64_t c0 = static_cast<uint64_t>(c) * kChunk;
+    return ((c0 + kChunk < p.ntiles) ? c0 + kChunk : p.ntiles) - c0;
+}
+
+__device__ __forceinline__ void cta_wait_flag(const unsigned int *flag, unsigned int target, uint32_t *status)
+{
+    if (threadIdx.x == 0) {
+        uint64_t t0 = 0;
+        for (int spin = 0; ld_acquire_u32(flag) < target; ++spin) {
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            if (now - t0 > kWaitLimitNs) {
+                atomicOr(status, VBYTE_ERR_TIMEOUT);
+                break;
+            }
+            if (spin > 4) __nanosleep(200);
+        }
+    }
+    __syncthreads();
+}
+
+template <bool kDelta>
+__device__ void chunk_scan(const Params &p, uint64_t c, Shared &S)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t c0 = c * kChunk;
+    const uint64_t c1 = (c0 + kChunk < p.ntiles) ? c0 + kChunk : p.ntiles;
+    uint64_t pc = 0;
+    uint32_t ps = p.prev;
+    if (c > 0) {
+        cta_wait_flag(p.cready + (c - 1), 1u, p.status);
+        pc = __ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1)));
+        ps = static_cast<uint32_t>(__ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1) + 1)));
+    }
+    const uint64_t ng = (p.ntiles + kGroup - 1) / kGroup;
+    const uint64_t g = c * kGroupsPerChunk + tid;
+    uint64_t ac = 0;
+    uint32_t as = 0;
+    if (tid < kGroupsPerChunk && g < ng) {
+        const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2 *>(p.gagg + 2 * g));
+        ac = a.x;
+        as = static_cast<uint32_t>(a.y);
+    }
+    const uint64_t ic = warp_incl_scan64(ac, lane);
+    const uint32_t is = warp_incl_scan(as, lane);
+    if (lane == 31) {
+        S.gsc[warp] = ic;
+        S.gss[warp] = is;
+    }
+    __syncthreads();
+    uint64_t wc0 = 0, tc_all = 0;
+    uint32_t ws0 = 0, ts_all = 0;
+#pragma unroll
+    for (int q = 0; q < kGroupsPerChunk / 32; ++q) {
+        wc0 += (q < warp) ? S.gsc[q] : 0ull;
+        ws0 += (q < warp) ? S.gss[q] : 0u;
+        tc_all += S.gsc[q];
+        ts_all += S.gss[q];
+    }
+    if (tid < kGroupsPerChunk && g < ng)
+        *reinterpret_cast<ulonglong2 *>(p.gpre + 2 * g) =
+            make_ulonglong2(pc + wc0 + ic - ac, static_cast<uint32_t>(ps + ws0 + is - as));
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        p.cnext[2 * c] = pc + tc_all;
+        p.cnext[2 * c + 1] = static_cast<uint32_t>(ps + ts_all);
+        if (c1 == p.ntiles && pc + tc_all != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        __threadfence();
+        *reinterpret_cast<volatile unsigned int *>(p.cready + c) = 1u;
+    }
+    __syncthreads();
+}
+
+// ---- tile prefixes (warp 0)
+
+struct PrefixLoads {
+    uint64_t pa, pb, ga, gb;
+    bool ok;
+};
+
+__device__ __forceinline__ PrefixLoads load_prefix(const Params &p, uint64_t t, int lane)
+{
+    PrefixLoads r;
+    r.pa = r.pb = r.ga = r.gb = 0;
+    r.ok = true;
+    const uint64_t g = t / kGroup;
+    const uint64_t j = g * kGroup + lane;
+    if (j < t) {
+        const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + 2 * j));
+        r.pa = d.x;
+        r.pb = d.y;
+    }
+    if (lane == 0) {
+        const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.gpre + 2 * g));
+        r.ga = d.x;
+        r.gb = d.y;
+    }
+    return r;
+}
+
+// Warp 0: stage tile t's prefix descriptors (its group's prefix and the
+// earlier tiles of its group) with cp.async, once its chunk is known scanned.
+__device__ __forceinline__ void stage_prefix(const Params &p, uint64_t t, int lane, Shared &S, int b)
+{
+    const uint64_t g = t / kGroup;
+    const uint64_t j = g * kGroup + lane;
+    if (j < t) cp_async16(&S.pdesc[b][lane], p.tdesc + 2 * j);
+    if (lane == 0) cp_async16(&S.pgpre[b], p.gpre + 2 * g);
+}
+
+__device__ __forceinline__ void fold_staged(uint64_t t, int lane, const Shared &S, int b, unsigned long long &R0,
+                                            uint32_t &S0)
+{
+    const uint64_t j = (t / kGroup) * kGroup + lane;
+    uint32_t c = 0, x = 0;
+    if (j < t) {
+        const ulonglong2 d = S.pdesc[b][lane];
+        c = static_cast<uint32_t>(d.x);
+        x = static_cast<uint32_t>(d.y);
+    }
+    c = __reduce_add_sync(~0u, c);
+    x = __reduce_add_sync(~0u, x);
+    R0 = S.pgpre[b].x + c;
+    S0 = static_cast<uint32_t>(S.pgpre[b].y) + x;
+}
+
+__device__ __forceinline__ void fold(const PrefixLoads &r, int lane, unsigned long long &R0, uint32_t &S0)
+{
+    const uint32_t c = __reduce_add_sync(~0u, static_cast<uint32_t>(r.pa));
+    const uint32_t x = __reduce_add_sync(~0u, static_cast<uint32_t>(r.pb));
+    R0 = __shfl_sync(~0u, r.ga, 0) + c;
+    S0 = static_cast<uint32_t>(__shfl_sync(~0u, r.gb, 0)) + x;
+    (void)lane;
+}
+
+// ---- decoding
+//
+// Before the middle barrier each warp stages its values in its own buffer:
+// warp rank r at vals[4 + r], running sums (delta) relative to the warp's
+// first value.  After it, one coalesced copy-out adds the warp's base and
+// realigns to 16-byte output quads.
+
+template <bool kDelta>
+__device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
+    const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
+    const bool mineA = interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u);
+    uint32_t *vals = S.vals[warp];
+    uint32_t wc, ws = 0;
+    if (__all_sync(~0u, mineA)) {
+        // one-byte integers only: lane l holds warp ranks 16l .. 16l+15
+        uint4 q[4] = {bytes_as_values(w0.x), bytes_as_values(w0.y), bytes_as_values(w0.z),
+                      bytes_as_values(w0.w)};
+        if (kDelta) {
+            const uint32_t mine = byte_sum4(w0);
+            const uint32_t incs = warp_incl_scan(mine, lane);
+            ws = __shfl_sync(~0u, incs, 31);
+            uint32_t run = incs - mine;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                run += q[j].x; q[j].x = run;
+                run += q[j].y; q[j].y = run;
+                run += q[j].z; q[j].z = run;
+                run += q[j].w; q[j].w = run;
+            }
+        }
+        uint4 *d4 = reinterpret_cast<uint4 *>(vals + 4 + 16 * lane);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d4[j] = q[j];
+        wc = kWarpBytes;
+    } else {
+        const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+        const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
+        const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
+        const uint32_t cnt = __popc(m.tc);
+        const uint32_t c20 = ~m.t20 & 0xFFFFFu;
+        const bool notB = (c20 & (c20 << 1) & 0xFFFF8u) != 0;
+        const uint32_t inc = warp_incl_scan(cnt, lane);
+        wc = __shfl_sync(~0u, inc, 31);
+        uint32_t *dst = vals + 4 + inc - cnt;
+        uint32_t vsum = 0;
+        if (!__any_sync(~0u, notB)) {
+            // codes of at most two bytes: the lane's sum by the byte-weight
+            // formula, then the values (with running sums) in one SWAR pass
+            uint32_t run = 0;
+            if (kDelta) {
+                vsum = interior ? sum_le2_fast(m.w, m.wprev) : sum_le2(m.w, m.wprev, m.tc);
+                const uint32_t incs = warp_incl_scan(vsum, lane);
+                ws = __shfl_sync(~0u, incs, 31);
+                run = incs - vsum;
+            }
+            const uint32_t c4[4] = {m.w.x, m.w.y, m.w.z, m.w.w};
+            uint32_t wp = m.wprev;
+            int qi = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const Pairs pr = pairs_le2(wp, c4[j]);
+                uint32_t q01 = prmt(pr.lob, pr.hib, 0x5140u);
+                uint32_t q23 = prmt(pr.lob, pr.hib, 0x7362u);
+                q01 -= (q01 & 0xFF00FF00u) >> 1;
+                q23 -= (q23 & 0xFF00FF00u) >> 1;
+                const uint32_t v4[4] = {q01 & 0xFFFFu, q01 >> 16, q23 & 0xFFFFu, q23 >> 16};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if ((m.tc >> (4 * j + i)) & 1u) {
+                        if (kDelta) {
+                            run += v4[i];
+                            dst[qi++] = run;
+                        } else {
+                            dst[qi++] = v4[i];
+                        }
+                    }
+                }
+                wp = c4[j];
+            }
+        } else {
+            // longer codes: each value assembled once (pass 1), then running
+            // sums from this lane's offset within the warp (pass 2)
+            assemble_all(sw, tid, m.tl, m.t20, m.tc, [&](uint32_t v) {
+                *dst++ = v;
+                vsum += v;
+            });
+            dst -= cnt;
+            if (kDelta) {
+                const uint32_t incs = warp_incl_scan(vsum, lane);
+                ws = __shfl_sync(~0u, incs, 31);
+                uint32_t run = incs - vsum;
+                for (uint32_t i = 0; i < cnt; ++i) {
+                    run += dst[i];
+                    dst[i] = run;
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        S.dcnt[warp] = wc;
+        S.dsum[warp] = ws;
+    }
+}
+
+// After the middle barrier: this warp's values to the output, coalesced.
+template <bool kDelta>
+__device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
+    const long long n = static_cast<long long>(p.n);
+    uint32_t wbase = 0, wsb = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+        wbase += (q < warp) ? S.dcnt[q] : 0u;
+        if (kDelta) wsb += (q < warp) ? S.dsum[q] : 0u;
+    }
+    const uint32_t wc = S.dcnt[warp];
+    const long long G0 = static_cast<long long>(S.R0 + wbase);   // global rank of warp rank 0
+    const uint32_t add = kDelta ? S.S0 + wsb : 0u;
+    const int sh = static_cast<int>((out_word + static_cast<uint32_t>(G0)) & 3u);
+    const uint32_t *vals = S.vals[warp];
+    // output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
+    // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of V = vals[4q+4..]
+    for (int q = lane; 4 * q < static_cast<int>(wc) + sh; q += kLanes) {
+        const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
+        const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
+        uint4 e;
+        switch (sh) {
+        case 0: e = V; break;
+        case 1: e = make_uint4(U.w, V.x, V.y, V.z); break;
+        case 2: e = make_uint4(U.z, U.w, V.x, V.y); break;
+        default: e = make_uint4(U.y, U.z, U.w, V.x); break;
+        }
+        e.x += add;
+        e.y += add;
+        e.z += add;
+        e.w += add;
+        const int r0 = 4 * q - sh;
+        const long long g0 = G0 + r0;
+        if (r0 >= 0 && r0 + 4 <= static_cast<int>(wc) && g0 + 4 <= n) {
+            st_quad(p.out + g0, e);
+        } else {
+            const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (r0 + j >= 0 && r0 + j < static_cast<int>(wc) && g0 + j < n) p.out[g0 + j] = e4[j];
+        }
+    }
+}
+
+// ---- kernel
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kThreads, 5) sdecode_kernel(const Params p)
+{
+    __shared__ Shared S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t total = p.ntiles + p.lead;
+    const uint64_t nchunks = (p.ntiles + kChunk - 1) / kChunk;
+    if (tid == 0) {
+        S.tinit[0] = atomicAdd(p.ctr, 1ull);
+        S.tnext = atomicAdd(p.ctr, 1ull);
+        S.scan_c = -1;
+    }
+    __syncthreads();
+    uint64_t k = S.tinit[0];
+    // warp 0 knows chunks [0, ready] are scanned (they are scanned in order);
+    // it reads the next chunk's flag one iteration before using it
+    long long ready = -1, probe = -1;
+    unsigned int rflag = 0;
+    auto stage = [&](uint64_t tk, int b) {
+        if (tk < p.ntiles) issue_stage(p, tk, tid, S.cbytes[b]);
+        uint32_t pf = 0;
+        if (tk >= p.lead && tk < total) {
+            const uint64_t t = tk - p.lead;
+            issue_stage(p, t, tid, S.dbytes[b]);
+            if (t % kChunk != 0 && static_cast<long long>(t / kChunk) <= ready) {
+                if (warp == 0) stage_prefix(p, t, lane, S, b);
+                pf = 1;
+            }
+        }
+        if (tid == 0) S.pf[b] = pf;
+        cp_async_commit();
+    };
+    stage(k, 0);
+    for (int b = 0; k < total; b ^= 1) {
+        cp_async_wait_all();   // ticket k's group is complete
+        __syncthreads();       // ... for every thread; the previous iteration is over
+        const uint64_t kn = S.tnext;   // staged now, processed next iteration
+        unsigned long long knn = 0;
+        if (tid == 0) knn = atomicAdd(p.ctr, 1ull);
+        if (warp == 0) {
+            if (probe >= 0 && __shfl_sync(~0u, rflag, 0)) ready = std::max(ready, probe);
+            probe = -1;
+            // probe the chunk after `ready` while the tickets near it
+            if (kn >= p.lead && kn < total && static_cast<long long>((kn - p.lead) / kChunk) >= ready &&
+                static_cast<uint64_t>(ready + 1) < nchunks) {
+                probe = ready + 1;
+                if (lane == 0) rflag = ld_acquire_u32(p.cready + probe);
+            }
+        }
+        if (kn < total) stage(kn, b ^ 1);
+        // the count this CTA published last iteration completed its chunk
+        if (S.scan_c >= 0) chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);   // CTA-uniform
+
+        const bool dec = k >= p.lead;
+        const uint64_t t = k - p.lead;
+        if (k < p.ntiles) count_partials<kDelta>(p, k, S, S.cbytes[b]);
+        if (dec) {
+            if (warp == 0) {
+                unsigned long long R0;
+                uint32_t S0;
+                if (S.pf[b]) {
+                    fold_staged(t, lane, S, b, R0, S0);
+                } else {
+                    if (lane == 0) spin_flag(p.cready + t / kChunk, p.status);
+                    __syncwarp();
+                    fold(load_prefix(p, t, lane), lane, R0, S0);
+                    ready = std::max<long long>(ready, static_cast<long long>(t / kChunk));
+                }
+                if (lane == 0) {
+                    S.R0 = R0;
+                    S.S0 = S0;
+                }
+            }
+            decode_stage<kDelta>(p, t, S, S.dbytes[b]);
+        }
+        __syncthreads();   // count partials, decode partials and the prefix are in place
+        long long pend_c = -1;
+        unsigned int pend_old = 0;
+        if (k < p.ntiles && warp == kWarps - 1) {
+            pend_old = count_publish<kDelta>(p, k, S, lane);
+            pend_c = static_cast<long long>(k / kChunk);
+        }
+        if (dec) decode_emit<kDelta>(p, S);
+        // did this count complete its chunk?  (read after the emission, so the
+        // atomic has had time to return); the scan runs after the next barrier,
+        // before any decode of this CTA waits
+        if (warp == kWarps - 1 && lane == 0)
+            S.scan_c = (pend_c >= 0 && static_cast<uint64_t>(pend_old) + 1 == chunk_tiles(p, pend_c)) ? pend_c : -1;
+        if (tid == 0) S.tnext = knn;
+        k = kn;
+    }
+    __syncthreads();
+    if (S.scan_c >= 0) chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);
+    cp_async_wait_all();
+}
+
+// ---- host
+
+struct Layout {
+    uint64_t ntiles, ngroups, nchunks;
+    size_t ctr, cnext, cdone, cready, gagg, gpre, tdesc, total, clear;
+};
+
+Layout layout(uint64_t ntiles)
+{
+    Layout L;
+    L.ntiles = ntiles;
+    L.ngroups = (ntiles + kGroup - 1) / kGroup;
+    L.nchunks = (ntiles + kChunk - 1) / kChunk;
+    L.ctr = 256;   // after the status head
+    L.cnext = L.ctr + 16;
+    L.cdone = L.cnext + 16 * L.nchunks;
+    L.cready = L.cdone + 4 * L.nchunks;
+    L.gagg = (L.cready + 4 * L.nchunks + 15) / 16 * 16;
+    L.gpre = L.gagg + 16 * L.ngroups;
+    L.tdesc = L.gpre + 16 * L.ngroups;
+    L.total = L.tdesc + 16 * ntiles;
+    L.clear = L.gpre - L.ctr;   // ticket counter, chunk words, group accumulators
+    return L;
+}
+
+uint64_t tiles_for(uintptr_t addr, size_t nbytes) { return nbytes ? ((addr & 15u) + nbytes + kTile - 1) / kTile : 0; }
+
+struct Dev {
+    int sms = 0;
+    int occ[2] = {0, 0};
+};
+std::mutex g_mu;
+std::map<int, Dev> g_dev;
+
+int dev_info(Dev *out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VBYTE_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Dev &d = g_dev[dev];
+    if (d.sms == 0) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return VBYTE_ECUDA;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], sdecode_kernel<false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], sdecode_kernel<true>, kThreads, 0);
+        for (int &o : d.occ) o = std::max(o, 1);
+    }
+    *out = d;
+    return VBYTE_OK;
+}
+
+}  // namespace sd
+
+size_t wdecode_workspace_bytes(size_t nbytes) { return sd::layout(sd::tiles_for(15, nbytes)).total; }
+
+int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
+                  cudaStream_t s)
+{
+    if (nbytes == 0 && n == 0) return VBYTE_OK;
+    if ((nbytes && !in) || (n && !out)) return VBYTE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(out) & 3u) return VBYTE_EINVAL;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
+    const uint64_t ntiles = sd::tiles_for(a, nbytes);
+    const sd::Layout L = sd::layout(ntiles);
+    uint8_t *ws = nullptr;
+    int rc = stream_workspace(s, L.total, &ws);
+    if (rc != VBYTE_OK) return rc;
+    uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+    if (nbytes == 0) return set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s);   // n > 0 from no bytes
+    sd::Dev di;
+    rc = sd::dev_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    if (cudaMemsetAsync(ws + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
+    sd::Params p = {};
+    p.in = in;
+    p.nbytes = nbytes;
+    p.out = out;
+    p.n = n;
+    p.ntiles = ntiles;
+    p.base = a & ~static_cast<uintptr_t>(15);
+    p.tdesc = reinterpret_cast<uint64_t *>(ws + L.tdesc);
+    p.gagg = reinterpret_cast<unsigned long long *>(ws + L.gagg);
+    p.gpre = reinterpret_cast<uint64_t *>(ws + L.gpre);
+    p.cnext = reinterpret_cast<uint64_t *>(ws + L.cnext);
+    p.cdone = reinterpret_cast<unsigned int *>(ws + L.cdone);
+    p.cready = reinterpret_cast<unsigned int *>(ws + L.cready);
+    p.ctr = reinterpret_cast<unsigned long long *>(ws + L.ctr);
+    p.status = status;
+    p.prev = prev;
+    p.lead = std::min<uint64_t>(sd::kChunk + sd::kSlack, ntiles);
+    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
+    if (delta)
+        sd::sdecode_kernel<true><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    else
+        sd::sdecode_kernel<false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
+}  // namespace vbk
