@@ -114,6 +114,12 @@ __device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
     const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
     uint8_t *dst = bytes + kHalo + tid * kBPT;
+    if (t > 0 && tstart + kTile <= hi && tstart >= lo + 16) {   // interior tile: no checks
+        cp_async16(dst, reinterpret_cast<const void *>(va));
+        if (tid == 0) cp_async16(bytes, reinterpret_cast<const void *>(tstart - 16));
+        if (tid == kThreads - 1) *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
     if (va >= lo && va + kBPT <= hi) {
         cp_async16(dst, reinterpret_cast<const void *>(va));
     } else {
@@ -463,9 +469,17 @@ __device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
     const uint32_t add = kDelta ? S.S0 + wsb : 0u;
     const int sh = static_cast<int>((out_word + static_cast<uint32_t>(G0)) & 3u);
     const uint32_t *vals = S.vals[warp];
-    // output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
-    // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of V = vals[4q+4..]
-    for (int q = lane; 4 * q < static_cast<int>(wc) + sh; q += kLanes) {
+    // Output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
+    // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of
+    // V = vals[4q+4..].  Quads [qa, qb) are whole (inside this warp's ranks
+    // and below n); the others are written element by element.
+    const int nq = (static_cast<int>(wc) + sh + 3) >> 2;
+    const long long lim = n - G0 + sh;   // quads with 4q + 4 <= lim end below n
+    int qb = (static_cast<int>(wc) + sh) >> 2;
+    if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
+    const int qa = sh ? 1 : 0;
+    uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
+    auto quad = [&](int q) -> uint4 {
         const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
         const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
         uint4 e;
@@ -479,16 +493,17 @@ __device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
         e.y += add;
         e.z += add;
         e.w += add;
+        return e;
+    };
+    for (int q = qa + lane; q < qb; q += kLanes) st_quad(oq + 4 * q, quad(q));
+    // edge quads: the first (partly before this warp's ranks) and those from qb on
+    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
+        const uint4 e = quad(q);
+        const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
         const int r0 = 4 * q - sh;
-        const long long g0 = G0 + r0;
-        if (r0 >= 0 && r0 + 4 <= static_cast<int>(wc) && g0 + 4 <= n) {
-            st_quad(p.out + g0, e);
-        } else {
-            const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (r0 + j >= 0 && r0 + j < static_cast<int>(wc) && g0 + j < n) p.out[g0 + j] = e4[j];
-        }
+        for (int j = 0; j < 4; ++j)
+            if (r0 + j >= 0 && r0 + j < static_cast<int>(wc) && G0 + r0 + j < n) oq[4 * q + j] = e4[j];
     }
 }
 
