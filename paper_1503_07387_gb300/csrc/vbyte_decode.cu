@@ -95,10 +95,7 @@ struct Params {
     uint64_t *tpre;            // per tile: values before it, running x before it
 };
 
-// Heads of lists are looked up in a window that starts this many bytes
-// before a tile or slice: an integer ends at most four bytes after it starts.
-constexpr int kHeadBack = 8;
-constexpr int kHeadWords = (kHalo + kTile) / 32 + 2;   // head bitmap of a staged tile
+static_assert(kHeadTile == kTile, "head helpers assume 4 KiB tiles");
 
 // Thread 0 waits until *flag != 0 (bounded by the global timer; on expiry the
 // status word gets VBYTE_ERR_TIMEOUT and the caller carries on), then the CTA
@@ -144,190 +141,6 @@ __device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid
     }
     if (tid == kThreads - 1)
         *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
-}
-
-// ---- segmented sums (batched differential decoding) ----------------------
-// A list head restarts the running value at that list's x_0.  A slice of
-// integers acts on the running value x as: f ? s : x + s, where f says that a
-// head was crossed and s is the sum since the last head (including its x_0).
-struct Seg {
-    uint32_t f, s;
-};
-
-__device__ __forceinline__ Seg seg_op(Seg a, Seg b)
-{
-    Seg r;
-    r.f = a.f | b.f;
-    r.s = b.f ? b.s : a.s + b.s;
-    return r;
-}
-
-__device__ __forceinline__ uint32_t seg_apply(uint32_t x, Seg a) { return a.f ? a.s : x + a.s; }
-
-__device__ __forceinline__ Seg warp_seg_incl(Seg x, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t ys = __shfl_up_sync(~0u, x.s, o);
-        const uint32_t yf = __shfl_up_sync(~0u, x.f, o);
-        if (lane >= o) {
-            if (!x.f) x.s += ys;
-            x.f |= yf;
-        }
-    }
-    return x;
-}
-
-// The list heads of a tile in shared memory: a bitmap of their first bytes
-// over the staged window (bit i: staging byte i, the 16 halo bytes first)
-// and, for the first kMaxHeadList lists of the tile's range [ha, he), each
-// list's staging index, x_0 and value offset, so that lookups stay on chip.
-constexpr int kMaxHeadList = 512;
-struct HeadTab {
-    int pos[kMaxHeadList];
-    uint32_t prv[kMaxHeadList];
-    unsigned long long vo[kMaxHeadList];
-    uint32_t bits[kHeadWords];
-};
-
-// Fill T for the tile starting at stream offset trel.  All threads take part.
-__device__ __forceinline__ void build_heads(const Params &p, long long trel, uint64_t ha, uint64_t he, HeadTab &T,
-                                            bool want_prev, bool want_vo)
-{
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kHeadWords; i += kThreads) T.bits[i] = 0u;
-    __syncthreads();
-    const long long w0 = trel - kHalo;
-    const uint64_t nh = he - ha;
-    for (uint64_t i = tid; i < nh; i += kThreads) {
-        const uint64_t j = ha + i;
-        const long long d = static_cast<long long>(p.bo[j]) - w0;
-        if (d >= 0 && d < kHalo + kTile) atomicOr(T.bits + (d >> 5), 1u << (d & 31));
-        if (i < static_cast<uint64_t>(kMaxHeadList)) {
-            T.pos[i] = d < 0 ? -1 : (d > (1 << 30) ? (1 << 30) : static_cast<int>(d));
-            if (want_prev) T.prv[i] = p.prevs ? p.prevs[j] : 0u;
-            if (want_vo) T.vo[i] = p.vo[j];
-        }
-    }
-    __syncthreads();
-}
-
-// Index of the last table entry whose staging index is <= q (-1 if none).
-__device__ __forceinline__ int tab_last_le(const HeadTab &T, int n, int q)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (T.pos[mid] <= q)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo - 1;
-}
-
-// The 24 staged bytes ending with tid's slice: terminator bits (t24) and head
-// bits (h24); bit i is staging byte kHalo + 16*tid - kHeadBack + i.
-struct HeadWin {
-    uint32_t t24, h24;
-};
-
-__device__ __forceinline__ HeadWin head_window(const uint32_t *sw, const uint32_t *bits, int tid, uint32_t tl)
-{
-    HeadWin h;
-    const int q = (kHalo + tid * kBPT) / 4;
-    h.t24 = term4(sw[q - 2]) | (term4(sw[q - 1]) << 4) | (tl << 8);
-    const int b0 = kHalo + tid * kBPT - kHeadBack;   // a multiple of 8
-    h.h24 = __funnelshift_r(bits[b0 >> 5], bits[(b0 >> 5) + 1], b0 & 31) & 0xFFFFFFu;
-    return h;
-}
-
-// Terminators (slice bits) that end the first integer of a list: the integer
-// starting at a head bit h ends at the first terminator at or after h.  Adding
-// h to the non-terminator mask carries from h through the continuation bytes
-// into exactly that terminator.
-__device__ __forceinline__ uint32_t head_terms(const HeadWin &h, uint32_t tc)
-{
-    const uint32_t r = ~h.t24 & 0xFFFFFFu;
-    return (((r + h.h24) & h.t24) >> kHeadBack) & tc;
-}
-
-// Index of the last list in [ha, he) whose byte offset is pos (a head bit was
-// set from one of them); ha - 1 if none.
-__device__ __forceinline__ long long last_list_at(const Params &p, uint64_t ha, uint64_t he, long long pos)
-{
-    uint64_t lo = ha, hi = he;
-    while (lo < hi) {
-        const uint64_t mid = lo + (hi - lo) / 2;
-        if (static_cast<long long>(p.bo[mid]) <= pos)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return static_cast<long long>(lo) - 1;
-}
-
-// x_0 of the list whose first integer ends at slice bit o (a head_terms bit):
-// that integer starts after the previous terminator; the head bit in between
-// names the list.  srel: stream offset of the slice's first byte.
-__device__ __forceinline__ uint32_t head_prev(const Params &p, const HeadTab &T, const HeadWin &h, int o, int tid,
-                                              long long srel, uint64_t ha, uint64_t he)
-{
-    const int P = o + kHeadBack;
-    const uint32_t below = h.t24 & ((1u << P) - 1u);
-    const int q = below ? 31 - __clz(below) : -1;          // previous terminator
-    const uint32_t above_q = q >= 0 ? ~((2u << q) - 1u) : ~0u;
-    const uint32_t hb = h.h24 & ((2u << P) - 1u) & above_q;   // heads in (q, P]
-    if (!hb) return 0u;
-    const int k = 31 - __clz(hb);
-    if (he - ha <= static_cast<uint64_t>(kMaxHeadList)) {
-        const int qs = kHalo + tid * kBPT - kHeadBack + k;   // staging index of the head
-        const int i = tab_last_le(T, static_cast<int>(he - ha), qs);
-        return (i >= 0 && T.pos[i] == qs) ? T.prv[i] : 0u;
-    }
-    const long long j = last_list_at(p, ha, he, srel - kHeadBack + k);
-    if (j < static_cast<long long>(ha) || p.prevs == nullptr) return 0u;
-    return p.prevs[j];
-}
-
-// Per-terminator assembly as assemble_all, also passing each terminator's
-// slice bit to emit(o, value).
-template <typename F>
-__device__ __forceinline__ void assemble_all_o(const uint32_t *sw, int tid, uint32_t tl, uint32_t t20, uint32_t tc,
-                                               F emit)
-{
-    uint32_t m = tl;
-    int prevo = 27 - __clz(t20 & 0xFu);
-    while (m) {
-        const int o = __ffs(m) - 1;
-        m &= m - 1u;
-        const int L = min(o - prevo, 5);
-        prevo = o;
-        if ((tc >> o) & 1u) {
-            const int q = kHalo + tid * kBPT + o;
-            const uint32_t A = sw[(q >> 2) - 1];
-            const uint32_t B = sw[q >> 2];
-            const uint32_t lo4 = __funnelshift_r(A, B, 8 * q);
-            const uint32_t x = (B >> (8 * (q & 3))) & 0xFFu;
-            emit(o, assemble(lo4, x, L));
-        }
-    }
-}
-
-// Segmented sum of a slice that holds list heads (ht != 0): the sum since the
-// last head, starting from that list's x_0.
-__device__ __forceinline__ uint32_t slice_seg_sum(const Params &p, const HeadTab &T, const uint32_t *sw, int tid,
-                                                  uint32_t tl, uint32_t t20, uint32_t tc, const HeadWin &h,
-                                                  uint32_t ht, long long srel, uint64_t ha, uint64_t he)
-{
-    uint32_t s = 0;
-    assemble_all_o(sw, tid, tl, t20, tc, [&](int o, uint32_t v) {
-        if ((ht >> o) & 1u)
-            s = head_prev(p, T, h, o, tid, srel, ha, he) + v;
-        else
-            s += v;
-    });
-    return s;
 }
 
 struct Shared {
@@ -408,7 +221,7 @@ __device__ void count_tile(const Params &p, uint64_t t, Shared &S, const uint8_t
             const uint64_t ha = S.hrc[b][0], he = S.hrc[b][1];
             if (ha < he) {   // CTA-uniform
                 const long long trel = static_cast<long long>(tstart) - static_cast<long long>(lo);
-                build_heads(p, trel, ha, he, S.heads, true, false);
+                build_heads(HeadSrc{p.bo, p.vo, p.prevs}, trel, ha, he, S.heads, true, false);
                 const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
                 const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
                 const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
@@ -416,7 +229,7 @@ __device__ void count_tile(const Params &p, uint64_t t, Shared &S, const uint8_t
                 const uint32_t ht = head_terms(h, m.tc);
                 if (ht) {
                     segf = 1u;
-                    vsum = slice_seg_sum(p, S.heads, sw, tid, m.tl, m.t20, m.tc, h, ht, trel + tid * kBPT, ha,
+                    vsum = slice_seg_sum(HeadSrc{p.bo, p.vo, p.prevs}, S.heads, sw, tid, m.tl, m.t20, m.tc, h, ht, trel + tid * kBPT, ha,
                                          he);
                 }
             }
@@ -870,12 +683,12 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
     uint32_t ht = 0;
     if constexpr (kSeg) {
         if (ha < he) {   // CTA-uniform
-            build_heads(p, trel, ha, he, S.heads, kDelta, true);
+            build_heads(HeadSrc{p.bo, p.vo, p.prevs}, trel, ha, he, S.heads, kDelta, true);
             hw = head_window(sw, S.heads.bits, tid, m.tl);
             if constexpr (kDelta) {
                 ht = head_terms(hw, m.tc);
                 if (ht) {
-                    vsum = slice_seg_sum(p, S.heads, sw, tid, m.tl, m.t20, m.tc, hw, ht, srel, ha, he);
+                    vsum = slice_seg_sum(HeadSrc{p.bo, p.vo, p.prevs}, S.heads, sw, tid, m.tl, m.t20, m.tc, hw, ht, srel, ha, he);
                     notB = true;   // values with restarts take the per-terminator path
                 }
             }
@@ -939,7 +752,7 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
                         if (S.heads.vo[i] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
                     }
                 } else {
-                    for (long long j = last_list_at(p, ha, he, pos); j >= static_cast<long long>(ha); --j) {
+                    for (long long j = last_list_at(HeadSrc{p.bo, p.vo, p.prevs}, ha, he, pos); j >= static_cast<long long>(ha); --j) {
                         if (static_cast<long long>(p.bo[j]) != pos) break;
                         if (p.vo[j] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
                     }
@@ -964,7 +777,7 @@ __device__ void decode_tile(const Params &p, uint64_t t, Shared &S, const uint8_
     if (ht) {
         assemble_all_o(sw, tid, m.tl, m.t20, m.tc, [&](int o, uint32_t v) {
             if ((ht >> o) & 1u)
-                run = head_prev(p, S.heads, hw, o, tid, srel, ha, he) + v;
+                run = head_prev(HeadSrc{p.bo, p.vo, p.prevs}, S.heads, hw, o, tid, srel, ha, he) + v;
             else
                 run += v;
             *dst++ = run;
@@ -1133,6 +946,29 @@ __global__ void __launch_bounds__(256) head_range_kernel(const Params p)
     if (i0 == 0 && (p.bo[0] != 0 || p.vo[0] != 0 || p.bo[p.L] != p.nbytes || p.vo[p.L] != p.n))
         bad |= VBYTE_ERR_BAD_OFFSETS;
     if (bad) atomicOr(p.status, bad);
+}
+
+// Launch head_range_kernel for a batch decoded by another kernel with the
+// same 4 KiB tiling (tile 0 at `in` rounded down to 16 bytes).
+int enqueue_head_ranges(const uint8_t *in, size_t nbytes, const uint64_t *bo, const uint64_t *vo, size_t L,
+                        size_t n, uint64_t *hr, uint32_t *status, int sms, cudaStream_t s)
+{
+    Params p = {};
+    p.in = in;
+    p.nbytes = nbytes;
+    p.n = n;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
+    p.ntiles = nbytes ? ((a & 15u) + nbytes + kTile - 1) / kTile : 0;
+    p.base = a & ~static_cast<uintptr_t>(15);
+    p.bo = bo;
+    p.vo = vo;
+    p.L = L;
+    p.hr = hr;
+    p.status = status;
+    const uint64_t work = std::max<uint64_t>(p.ntiles, L);
+    const unsigned grid = static_cast<unsigned>(std::min<uint64_t>((work + 255) / 256, static_cast<uint64_t>(sms) * 8));
+    head_range_kernel<<<std::max(grid, 1u), 256, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
 // ------------------------------------------------------------- workspace --
@@ -1349,7 +1185,7 @@ int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const
 int reserve_workspace(cudaStream_t s, size_t nbytes)
 {
     const uint64_t ntiles = (15 + nbytes + kTile - 1) / kTile;
-    const size_t need = std::max(wdecode_workspace_bytes(nbytes), layout_seg(ntiles).total);
+    const size_t need = std::max(wdecode_workspace_bytes(nbytes), layout_seg(ntiles).total + 16 * ntiles);
     Workspace *w = nullptr;
     return get_workspace(s, need, &w);
 }
@@ -1385,12 +1221,9 @@ int launch_decode_batched(const BatchArgs &a, cudaStream_t s)
     int rc = check_batch(a);
     if (rc != VBYTE_OK || a.L == 0) return rc;
     Workspace *w = nullptr;
-    rc = get_workspace(s, layout_seg(batch_tiles(a)).total, &w);
+    rc = get_workspace(s, sbatched_workspace_bytes(a), &w);
     if (rc != VBYTE_OK) return rc;
-    DeviceInfo di;
-    rc = device_info(&di);
-    if (rc != VBYTE_OK) return rc;
-    return enqueue_batched(a, w->ptr, LaunchCfg(), di, s);
+    return enqueue_sbatched(a, w->ptr, LaunchCfg(), s);
 }
 
 // ---- scratch for vbyte_decode_noalloc -----------------------------------

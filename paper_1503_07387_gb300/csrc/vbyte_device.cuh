@@ -290,4 +290,221 @@ __device__ __forceinline__ void slice_count_sum(const SliceMasks &m, const uint3
     }
 }
 
+
+// ---- list heads (batched decoding) ---------------------------------------
+constexpr int kHeadTile = 4096;                          // tile bytes of the decoders using these
+constexpr int kHeadBack = 8;                             // window start before a tile or slice
+constexpr int kHeadWords = (kHalo + kHeadTile) / 32 + 2; // head bitmap of a staged tile
+// ---- segmented sums (batched differential decoding) ----------------------
+// A list head restarts the running value at that list's x_0.  A slice of
+// integers acts on the running value x as: f ? s : x + s, where f says that a
+// head was crossed and s is the sum since the last head (including its x_0).
+struct Seg {
+    uint32_t f, s;
+};
+
+__device__ __forceinline__ Seg seg_op(Seg a, Seg b)
+{
+    Seg r;
+    r.f = a.f | b.f;
+    r.s = b.f ? b.s : a.s + b.s;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t seg_apply(uint32_t x, Seg a) { return a.f ? a.s : x + a.s; }
+
+__device__ __forceinline__ Seg warp_seg_incl(Seg x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ys = __shfl_up_sync(~0u, x.s, o);
+        const uint32_t yf = __shfl_up_sync(~0u, x.f, o);
+        if (lane >= o) {
+            if (!x.f) x.s += ys;
+            x.f |= yf;
+        }
+    }
+    return x;
+}
+
+// The list heads of a tile in shared memory: a bitmap of their first bytes
+// over the staged window (bit i: staging byte i, the 16 halo bytes first)
+// and, for the first kMaxHeadList lists of the tile's range [ha, he), each
+// list's staging index, x_0 and value offset, so that lookups stay on chip.
+constexpr int kMaxHeadList = 256;
+struct HeadTab {
+    int pos[kMaxHeadList];
+    uint32_t prv[kMaxHeadList];
+    unsigned long long vo[kMaxHeadList];
+    uint32_t bits[kHeadWords];
+};
+
+// Where the list heads come from: byte offsets, value offsets and x_0 of
+// every list (prevs may be null: x_0 = 0).
+struct HeadSrc {
+    const uint64_t *bo;
+    const uint64_t *vo;
+    const uint32_t *prevs;
+};
+
+// Fill T for the tile starting at stream offset trel (threads of a CTA of
+// nthreads take part; the caller syncs before and after as documented).
+__device__ __forceinline__ void fill_heads(const HeadSrc &p, long long trel, uint64_t ha, uint64_t he, HeadTab &T,
+                                           bool want_prev, bool want_vo, int nthreads)
+{
+    const int tid = threadIdx.x;
+    const long long w0 = trel - kHalo;
+    const uint64_t nh = he - ha;
+    for (uint64_t i = tid; i < nh; i += nthreads) {
+        const uint64_t j = ha + i;
+        const long long d = static_cast<long long>(p.bo[j]) - w0;
+        if (d >= 0 && d < kHalo + kHeadTile) atomicOr(T.bits + (d >> 5), 1u << (d & 31));
+        if (i < static_cast<uint64_t>(kMaxHeadList)) {
+            T.pos[i] = d < 0 ? -1 : (d > (1 << 30) ? (1 << 30) : static_cast<int>(d));
+            if (want_prev) T.prv[i] = p.prevs ? p.prevs[j] : 0u;
+            if (want_vo) T.vo[i] = p.vo[j];
+        }
+    }
+}
+
+// Fill T for the tile starting at stream offset trel.  All threads take part.
+__device__ __forceinline__ void build_heads(const HeadSrc &p, long long trel, uint64_t ha, uint64_t he, HeadTab &T,
+                                            bool want_prev, bool want_vo)
+{
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kHeadWords; i += static_cast<int>(blockDim.x)) T.bits[i] = 0u;
+    __syncthreads();
+    const long long w0 = trel - kHalo;
+    const uint64_t nh = he - ha;
+    for (uint64_t i = tid; i < nh; i += blockDim.x) {
+        const uint64_t j = ha + i;
+        const long long d = static_cast<long long>(p.bo[j]) - w0;
+        if (d >= 0 && d < kHalo + kHeadTile) atomicOr(T.bits + (d >> 5), 1u << (d & 31));
+        if (i < static_cast<uint64_t>(kMaxHeadList)) {
+            T.pos[i] = d < 0 ? -1 : (d > (1 << 30) ? (1 << 30) : static_cast<int>(d));
+            if (want_prev) T.prv[i] = p.prevs ? p.prevs[j] : 0u;
+            if (want_vo) T.vo[i] = p.vo[j];
+        }
+    }
+    __syncthreads();
+}
+
+// Index of the last table entry whose staging index is <= q (-1 if none).
+__device__ __forceinline__ int tab_last_le(const HeadTab &T, int n, int q)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (T.pos[mid] <= q)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo - 1;
+}
+
+// The 24 staged bytes ending with tid's slice: terminator bits (t24) and head
+// bits (h24); bit i is staging byte kHalo + 16*tid - kHeadBack + i.
+struct HeadWin {
+    uint32_t t24, h24;
+};
+
+__device__ __forceinline__ HeadWin head_window(const uint32_t *sw, const uint32_t *bits, int tid, uint32_t tl)
+{
+    HeadWin h;
+    const int q = (kHalo + tid * kBPT) / 4;
+    h.t24 = term4(sw[q - 2]) | (term4(sw[q - 1]) << 4) | (tl << 8);
+    const int b0 = kHalo + tid * kBPT - kHeadBack;   // a multiple of 8
+    h.h24 = __funnelshift_r(bits[b0 >> 5], bits[(b0 >> 5) + 1], b0 & 31) & 0xFFFFFFu;
+    return h;
+}
+
+// Terminators (slice bits) that end the first integer of a list: the integer
+// starting at a head bit h ends at the first terminator at or after h.  Adding
+// h to the non-terminator mask carries from h through the continuation bytes
+// into exactly that terminator.
+__device__ __forceinline__ uint32_t head_terms(const HeadWin &h, uint32_t tc)
+{
+    const uint32_t r = ~h.t24 & 0xFFFFFFu;
+    return (((r + h.h24) & h.t24) >> kHeadBack) & tc;
+}
+
+// Index of the last list in [ha, he) whose byte offset is pos (a head bit was
+// set from one of them); ha - 1 if none.
+__device__ __forceinline__ long long last_list_at(const HeadSrc &p, uint64_t ha, uint64_t he, long long pos)
+{
+    uint64_t lo = ha, hi = he;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (static_cast<long long>(p.bo[mid]) <= pos)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return static_cast<long long>(lo) - 1;
+}
+
+// x_0 of the list whose first integer ends at slice bit o (a head_terms bit):
+// that integer starts after the previous terminator; the head bit in between
+// names the list.  srel: stream offset of the slice's first byte.
+__device__ __forceinline__ uint32_t head_prev(const HeadSrc &p, const HeadTab &T, const HeadWin &h, int o, int tid,
+                                              long long srel, uint64_t ha, uint64_t he)
+{
+    const int P = o + kHeadBack;
+    const uint32_t below = h.t24 & ((1u << P) - 1u);
+    const int q = below ? 31 - __clz(below) : -1;          // previous terminator
+    const uint32_t above_q = q >= 0 ? ~((2u << q) - 1u) : ~0u;
+    const uint32_t hb = h.h24 & ((2u << P) - 1u) & above_q;   // heads in (q, P]
+    if (!hb) return 0u;
+    const int k = 31 - __clz(hb);
+    if (he - ha <= static_cast<uint64_t>(kMaxHeadList)) {
+        const int qs = kHalo + tid * kBPT - kHeadBack + k;   // staging index of the head
+        const int i = tab_last_le(T, static_cast<int>(he - ha), qs);
+        return (i >= 0 && T.pos[i] == qs) ? T.prv[i] : 0u;
+    }
+    const long long j = last_list_at(p, ha, he, srel - kHeadBack + k);
+    if (j < static_cast<long long>(ha) || p.prevs == nullptr) return 0u;
+    return p.prevs[j];
+}
+
+// Per-terminator assembly as assemble_all, also passing each terminator's
+// slice bit to emit(o, value).
+template <typename F>
+__device__ __forceinline__ void assemble_all_o(const uint32_t *sw, int tid, uint32_t tl, uint32_t t20, uint32_t tc,
+                                               F emit)
+{
+    uint32_t m = tl;
+    int prevo = 27 - __clz(t20 & 0xFu);
+    while (m) {
+        const int o = __ffs(m) - 1;
+        m &= m - 1u;
+        const int L = min(o - prevo, 5);
+        prevo = o;
+        if ((tc >> o) & 1u) {
+            const int q = kHalo + tid * kBPT + o;
+            const uint32_t A = sw[(q >> 2) - 1];
+            const uint32_t B = sw[q >> 2];
+            const uint32_t lo4 = __funnelshift_r(A, B, 8 * q);
+            const uint32_t x = (B >> (8 * (q & 3))) & 0xFFu;
+            emit(o, assemble(lo4, x, L));
+        }
+    }
+}
+
+// Segmented sum of a slice that holds list heads (ht != 0): the sum since the
+// last head, starting from that list's x_0.
+__device__ __forceinline__ uint32_t slice_seg_sum(const HeadSrc &p, const HeadTab &T, const uint32_t *sw, int tid,
+                                                  uint32_t tl, uint32_t t20, uint32_t tc, const HeadWin &h,
+                                                  uint32_t ht, long long srel, uint64_t ha, uint64_t he)
+{
+    uint32_t s = 0;
+    assemble_all_o(sw, tid, tl, t20, tc, [&](int o, uint32_t v) {
+        if ((ht >> o) & 1u)
+            s = head_prev(p, T, h, o, tid, srel, ha, he) + v;
+        else
+            s += v;
+    });
+    return s;
+}
+
 }  // namespace vbk

@@ -10,7 +10,7 @@
 
 namespace vbk {
 
-constexpr uint64_t kDefaultLeadSlack = 1024;
+constexpr uint64_t kDefaultLeadSlack = 2560;
 
 // Per device: SM count and the decode kernels' occupancy (CTAs per SM) for
 // plain / delta, single-stream (occ) and batched (occ_seg).
@@ -66,6 +66,16 @@ int reserve_workspace(cudaStream_t s, size_t nbytes);
 int status_word(cudaStream_t s, uint32_t **word);
 // Free s's workspace (queued on s; call before destroying s).
 void release_workspace(cudaStream_t s);
+
+// For every 4 KiB tile of `in` (tile 0 at `in` rounded down to 16 bytes):
+// the range of lists whose first byte lies in [tile start - 8, tile end),
+// as two uint64 per tile in hr; also checks the offset arrays' contract.
+int enqueue_head_ranges(const uint8_t *in, size_t nbytes, const uint64_t *bo, const uint64_t *vo, size_t L,
+                        size_t n, uint64_t *hr, uint32_t *status, int sms, cudaStream_t s);
+// Batched decode with the single-stream kernel's structure (vbyte_stream.cu).
+size_t sbatched_workspace_bytes(const BatchArgs &a);
+int sbatched_max_ctas(bool delta);   // CTAs per SM of that kernel
+int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cudaStream_t s);
 
 // A piece of a gather: len bytes from src + src_off to dst + dst_off.
 struct GatherPiece {

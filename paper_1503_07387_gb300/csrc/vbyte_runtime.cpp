@@ -49,11 +49,11 @@ int time_cfg(const vbk::BatchArgs &a, uint8_t *ws, const vbk::LaunchCfg &cfg, co
         cudaEventDestroy(e0);
         return VBYTE_ECUDA;
     }
-    int rc = vbk::enqueue_batched(a, ws, cfg, di, s);
+    int rc = vbk::enqueue_sbatched(a, ws, cfg, s);
     std::vector<float> t;
     for (int r = 0; r < reps && rc == VBYTE_OK; ++r) {
         cudaEventRecord(e0, s);
-        rc = vbk::enqueue_batched(a, ws, cfg, di, s);
+        rc = vbk::enqueue_sbatched(a, ws, cfg, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = VBYTE_ECUDA;
         float x = 0.f;
@@ -103,7 +103,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
     // inputs may still be in flight on the caller's stream
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return fail(VBYTE_ECUDA);
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(VBYTE_ECUDA);
-    if (cudaMalloc(&P->ws, vbk::batch_workspace_bytes(a)) != cudaSuccess) return fail(VBYTE_ENOMEM);
+    if (cudaMalloc(&P->ws, vbk::sbatched_workspace_bytes(a)) != cudaSuccess) return fail(VBYTE_ENOMEM);
     if (cudaMemsetAsync(P->ws, 0, sizeof(uint32_t), s) != cudaSuccess) return fail(VBYTE_ECUDA);
 
     if (autotune) {
@@ -120,8 +120,8 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
             }
         }
         if (!cached) {
-            const int occ = di.occ_seg[a.delta];
-            const uint64_t slacks[] = {0, 512, 1024, 2048};
+            const int occ = vbk::sbatched_max_ctas(a.delta);
+            const uint64_t slacks[] = {1536, 2560, 3584};
             float best = 0.f;
             for (int c = 1; c <= occ; ++c) {
                 for (uint64_t sl : slacks) {
@@ -147,7 +147,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
     }
 
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(VBYTE_ECUDA);
-    rc = vbk::enqueue_batched(a, P->ws, P->cfg, di, s);
+    rc = vbk::enqueue_sbatched(a, P->ws, P->cfg, s);
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (rc != VBYTE_OK) return fail(rc);
     if (ce != cudaSuccess) return fail(VBYTE_ECUDA);

@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "vbyte.h"
 #include "vbyte_device.cuh"
@@ -81,6 +82,13 @@ struct Params {
     uint32_t *status;
     uint32_t prev;             // x_0
     uint64_t lead;             // tickets [0, lead) only count
+    // batched lists only
+    const uint64_t *bo;        // list byte offsets [L + 1]
+    const uint64_t *vo;        // list value offsets [L + 1]
+    const uint32_t *prevs;     // per-list x_0 (nullptr: 0)
+    uint64_t L;
+    const uint64_t *hr;        // per tile: [first, end) of the lists whose head may own a terminator in it
+    uint64_t *tpre;            // per tile: values before it, running x before it
 };
 
 struct Shared {
@@ -100,6 +108,20 @@ struct Shared {
     uint32_t gss[kWarps];
     long long scan_c;                              // chunk this CTA completed (scans it), or -1
 };
+// Batched lists: the list heads of the count and the decode tile, per-warp
+// segment flags, and the segmented chunk scan's partials.
+struct SharedS : Shared {
+    alignas(16) unsigned long long hrc[2][2];   // head ranges of the staged count tiles (cp.async targets)
+    alignas(16) unsigned long long hrd[2][2];   // ... of the staged decode tiles
+    HeadTab hc, hd;                             // heads of the count and the decode tile
+    uint32_t cflag[kWarps];                     // count: a list head was crossed in this warp
+    uint32_t dflag[kWarps];                     // decode: the same
+    uint32_t dhf[kWarps];                       // decode: this warp's first rank after a head (values from it on are absolute)
+    unsigned long long csc[kWarps];             // segmented chunk scan partials
+    uint32_t css[kWarps], csf[kWarps];
+};
+static_assert(offsetof(SharedS, hrc) % 16 == 0 && offsetof(SharedS, hrd) % 16 == 0, "head range alignment");
+
 static_assert(offsetof(Shared, cbytes) % 16 == 0 && kByteBuf % 16 == 0, "cbytes alignment");
 static_assert(offsetof(Shared, dbytes) % 16 == 0 && offsetof(Shared, vals) % 16 == 0, "dbytes/vals alignment");
 static_assert((kWarpValBuf * 4) % 16 == 0, "per-warp value buffers keep 16-byte alignment");
@@ -507,12 +529,337 @@ __device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
     }
 }
 
+// After the middle barrier: this warp's values to the output, coalesced.
+// The same for batched lists: the warp's base is the segmented running value
+// before it, added only to ranks below the warp's first head value.
+template <bool kDelta>
+__device__ __forceinline__ void decode_emit_seg(const Params &p, const SharedS &S)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
+    const long long n = static_cast<long long>(p.n);
+    uint32_t wbase = 0;
+    Seg wsb;
+    wsb.f = wsb.s = 0u;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+        wbase += (q < warp) ? S.dcnt[q] : 0u;
+        if (kDelta && q < warp) {
+            Seg e;
+            e.f = S.dflag[q];
+            e.s = S.dsum[q];
+            wsb = seg_op(wsb, e);
+        }
+    }
+    const uint32_t wc = S.dcnt[warp];
+    const long long G0 = static_cast<long long>(S.R0 + wbase);   // global rank of warp rank 0
+    const uint32_t add = kDelta ? seg_apply(S.S0, wsb) : 0u;
+    const int hf = kDelta ? static_cast<int>(min(S.dhf[warp], wc)) : static_cast<int>(wc);   // ranks [hf, wc) are absolute
+    const int sh = static_cast<int>((out_word + static_cast<uint32_t>(G0)) & 3u);
+    const uint32_t *vals = S.vals[warp];
+    // Output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
+    // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of
+    // V = vals[4q+4..].  Quads [qa, qb) are whole (inside this warp's ranks
+    // and below n); the others are written element by element.
+    const int nq = (static_cast<int>(wc) + sh + 3) >> 2;
+    const long long lim = n - G0 + sh;   // quads with 4q + 4 <= lim end below n
+    int qb = (static_cast<int>(wc) + sh) >> 2;
+    if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
+    const int qa = sh ? 1 : 0;
+    uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
+    auto quad = [&](int q) -> uint4 {
+        const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
+        const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
+        uint4 e;
+        switch (sh) {
+        case 0: e = V; break;
+        case 1: e = make_uint4(U.w, V.x, V.y, V.z); break;
+        case 2: e = make_uint4(U.z, U.w, V.x, V.y); break;
+        default: e = make_uint4(U.y, U.z, U.w, V.x); break;
+        }
+        const int r0 = 4 * q - sh;
+        e.x += (r0 < hf) ? add : 0u;
+        e.y += (r0 + 1 < hf) ? add : 0u;
+        e.z += (r0 + 2 < hf) ? add : 0u;
+        e.w += (r0 + 3 < hf) ? add : 0u;
+        return e;
+    };
+    for (int q = qa + lane; q < qb; q += kLanes) st_quad(oq + 4 * q, quad(q));
+    // edge quads: the first (partly before this warp's ranks) and those from qb on
+    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
+        const uint4 e = quad(q);
+        const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
+        const int r0 = 4 * q - sh;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (r0 + j >= 0 && r0 + j < static_cast<int>(wc) && G0 + r0 + j < n) oq[4 * q + j] = e4[j];
+    }
+}
+
+// ---- batched lists (segmented sums restart at every list head)
+
+__device__ __forceinline__ HeadSrc head_src(const Params &p) { return HeadSrc{p.bo, p.vo, p.prevs}; }
+
+// Count partials of a tile with list heads: the lane's sum since its last
+// head (from that list's x_0), and the warp's segmented aggregate.
+__device__ __forceinline__ void count_partials_seg(const Params &p, uint64_t t, SharedS &S, const uint8_t *bytes,
+                                                   uint64_t ha, uint64_t he)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+    const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
+    const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
+    const uint32_t cnt = __popc(m.tc);
+    const uint32_t c20 = ~m.t20 & 0xFFFFFu;
+    if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
+        atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
+    if (t == p.ntiles - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((m.tl >> (hi - 1 - va)) & 1u))
+        atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+    const long long trel = static_cast<long long>(tstart) - static_cast<long long>(lo);
+    const HeadWin h = head_window(sw, S.hc.bits, tid, m.tl);
+    const uint32_t ht = head_terms(h, m.tc);
+    Seg sg;
+    sg.f = ht ? 1u : 0u;
+    sg.s = 0u;
+    if (ht) {
+        sg.s = slice_seg_sum(head_src(p), S.hc, sw, tid, m.tl, m.t20, m.tc, h, ht, trel + tid * kBPT, ha, he);
+    } else if (interior && !(c20 & (c20 << 1) & 0xFFFF8u)) {
+        sg.s = sum_le2_fast(m.w, m.wprev);
+    } else {
+        assemble_all(sw, tid, m.tl, m.t20, m.tc, [&](uint32_t v) { sg.s += v; });
+    }
+    sg = warp_seg_incl(sg, lane);
+    const uint32_t wc = __reduce_add_sync(~0u, cnt);
+    if (lane == 31) {
+        S.ccnt[warp] = wc;
+        S.csum[warp] = sg.s;
+        S.cflag[warp] = sg.f;
+    }
+}
+
+// One warp, after the middle barrier: the tile's segmented descriptor.
+template <bool kDelta>
+__device__ __forceinline__ unsigned int count_publish_seg(const Params &p, uint64_t t, const SharedS &S, int lane)
+{
+    const uint32_t tc = __reduce_add_sync(~0u, lane < kWarps ? S.ccnt[lane] : 0u);
+    Seg ws;
+    ws.f = (kDelta && lane < kWarps) ? S.cflag[lane] : 0u;
+    ws.s = (kDelta && lane < kWarps) ? S.csum[lane] : 0u;
+    ws = warp_seg_incl(ws, lane);
+    const uint32_t f = __shfl_sync(~0u, ws.f, 31), sm = __shfl_sync(~0u, ws.s, 31);
+    unsigned int old = 0;
+    if (lane == 0) {
+        *reinterpret_cast<ulonglong2 *>(p.tdesc + 2 * t) =
+            make_ulonglong2(tc, (static_cast<unsigned long long>(f) << 32) | sm);
+        old = atom_add_acq_rel(p.cdone + t / kChunk, 1u);
+    }
+    return old;
+}
+
+// Per-tile prefixes of chunk c from its tile descriptors (segmented), by the
+// CTA that completed the chunk's count.
+__device__ void chunk_scan_seg(const Params &p, uint64_t c, SharedS &S)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kPer = static_cast<int>(kChunk / kThreads);   // 8
+    const uint64_t c0 = c * kChunk;
+    const uint64_t c1 = (c0 + kChunk < p.ntiles) ? c0 + kChunk : p.ntiles;
+    uint64_t pc = 0;
+    uint32_t ps = 0;
+    if (c > 0) {
+        cta_wait_flag(p.cready + (c - 1), 1u, p.status);
+        pc = __ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1)));
+        ps = static_cast<uint32_t>(__ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1) + 1)));
+    }
+    const uint64_t tb = c0 + static_cast<uint64_t>(kPer) * tid;
+    uint64_t tcn = 0;
+    Seg ts;
+    ts.f = ts.s = 0u;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        if (tb + i < c1) {
+            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + 2 * (tb + i)));
+            Seg e;
+            e.f = static_cast<uint32_t>(d.y >> 32);
+            e.s = static_cast<uint32_t>(d.y);
+            tcn += d.x;
+            ts = seg_op(ts, e);
+        }
+    }
+    const uint64_t icn = warp_incl_scan64(tcn, lane);
+    const Seg is = warp_seg_incl(ts, lane);
+    if (lane == 31) {
+        S.csc[warp] = icn;
+        S.css[warp] = is.s;
+        S.csf[warp] = is.f;
+    }
+    __syncthreads();
+    uint64_t wc0 = 0, call = 0;
+    Seg w0, wall;
+    w0.f = w0.s = wall.f = wall.s = 0u;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+        Seg e;
+        e.f = S.csf[q];
+        e.s = S.css[q];
+        if (q < warp) {
+            wc0 += S.csc[q];
+            w0 = seg_op(w0, e);
+        }
+        call += S.csc[q];
+        wall = seg_op(wall, e);
+    }
+    Seg ex;
+    ex.f = __shfl_up_sync(~0u, is.f, 1);
+    ex.s = __shfl_up_sync(~0u, is.s, 1);
+    if (lane == 0) ex.f = ex.s = 0u;
+    uint64_t rc = pc + wc0 + icn - tcn;
+    uint32_t x = seg_apply(ps, seg_op(w0, ex));
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        if (tb + i < c1) {
+            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + 2 * (tb + i)));
+            *reinterpret_cast<ulonglong2 *>(p.tpre + 2 * (tb + i)) = make_ulonglong2(rc, x);
+            Seg e;
+            e.f = static_cast<uint32_t>(d.y >> 32);
+            e.s = static_cast<uint32_t>(d.y);
+            rc += d.x;
+            x = seg_apply(x, e);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        p.cnext[2 * c] = pc + call;
+        p.cnext[2 * c + 1] = seg_apply(ps, wall);
+        if (c1 == p.ntiles && pc + call != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        __threadfence();
+        *reinterpret_cast<volatile unsigned int *>(p.cready + c) = 1u;
+    }
+    __syncthreads();
+}
+
+// Decode staging of a tile with list heads (every warp takes the general
+// path): values with restarts at heads; values from the warp's first head on
+// are absolute, earlier ones relative to the warp's first value.
+template <bool kDelta>
+__device__ __forceinline__ void decode_stage_seg(const Params &p, uint64_t t, SharedS &S, const uint8_t *bytes,
+                                                 uint64_t ha, uint64_t he)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+    const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
+    const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
+    const uint32_t cnt = __popc(m.tc);
+    const uint32_t inc = warp_incl_scan(cnt, lane);
+    const uint32_t wc = __shfl_sync(~0u, inc, 31);
+    uint32_t *const dst = S.vals[warp] + 4 + inc - cnt;
+    uint32_t hf = 0xFFFFFFFFu, wsum = 0, wflag = 0;
+    if (kDelta) {
+        const long long srel = static_cast<long long>(tstart) - static_cast<long long>(lo) + tid * kBPT;
+        const HeadWin h = head_window(sw, S.hd.bits, tid, m.tl);
+        const uint32_t ht = head_terms(h, m.tc);
+        Seg sg;
+        sg.f = ht ? 1u : 0u;
+        sg.s = 0u;
+        // pass 1: values assembled once; a head restarts the lane's running sum
+        int qi = 0;
+        assemble_all_o(sw, tid, m.tl, m.t20, m.tc, [&](int o, uint32_t v) {
+            dst[qi++] = v;
+            if ((ht >> o) & 1u)
+                sg.s = head_prev(head_src(p), S.hd, h, o, tid, srel, ha, he) + v;
+            else
+                sg.s += v;
+        });
+        const Seg incl = warp_seg_incl(sg, lane);
+        wsum = __shfl_sync(~0u, incl.s, 31);
+        wflag = __shfl_sync(~0u, incl.f, 31);
+        Seg ex;
+        ex.f = __shfl_up_sync(~0u, incl.f, 1);
+        ex.s = __shfl_up_sync(~0u, incl.s, 1);
+        if (lane == 0) ex.f = ex.s = 0u;
+        // pass 2: running values (absolute after a head, else relative)
+        uint32_t run = ex.s;
+        uint32_t mm = m.tc;
+        for (int i = 0; mm; ++i) {
+            const int o = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            if ((ht >> o) & 1u)
+                run = head_prev(head_src(p), S.hd, h, o, tid, srel, ha, he) + dst[i];
+            else
+                run += dst[i];
+            dst[i] = run;
+        }
+        // the warp's first absolute rank: its first head value
+        if (ht) hf = inc - cnt + __popc(m.tc & ((1u << (__ffs(ht) - 1)) - 1u));
+        hf = __reduce_min_sync(~0u, hf);
+    }
+    if (lane == 0) {
+        S.dcnt[warp] = wc;
+        S.dsum[warp] = wsum;
+        S.dflag[warp] = wflag;
+        S.dhf[warp] = hf;
+    }
+}
+
+// After the middle barrier, tiles with heads: each list head in my slice must
+// start at rank vo[j] and follow a terminator.
+__device__ __forceinline__ void check_heads(const Params &p, uint64_t t, SharedS &S, const uint8_t *bytes,
+                                            uint64_t ha, uint64_t he, unsigned long long R0)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
+    const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
+    const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
+    const uint32_t cnt = __popc(m.tc);
+    const uint32_t inc = warp_incl_scan(cnt, lane);
+    uint32_t wbase = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) wbase += (q < warp) ? S.dcnt[q] : 0u;
+    const HeadWin h = head_window(sw, S.hd.bits, tid, m.tl);
+    uint32_t hs = (h.h24 >> kHeadBack) & 0xFFFFu;
+    const long long srel = static_cast<long long>(tstart) - static_cast<long long>(lo) + tid * kBPT;
+    while (hs) {
+        const int k = __ffs(hs) - 1;
+        hs &= hs - 1u;
+        const long long pos = srel + k;
+        if (pos < 0 || pos >= static_cast<long long>(p.nbytes)) continue;
+        if (pos > 0 && !((h.t24 >> (kHeadBack + k - 1)) & 1u)) atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+        const uint64_t rank = R0 + wbase + inc - cnt + __popc(m.tc & ((1u << k) - 1u));
+        if (he - ha <= static_cast<uint64_t>(kMaxHeadList)) {
+            const int qs = kHalo + tid * kBPT + k;
+            for (int i = tab_last_le(S.hd, static_cast<int>(he - ha), qs); i >= 0; --i) {
+                if (S.hd.pos[i] != qs) break;
+                if (S.hd.vo[i] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+            }
+        } else {
+            for (long long j = last_list_at(head_src(p), ha, he, pos); j >= static_cast<long long>(ha); --j) {
+                if (static_cast<long long>(p.bo[j]) != pos) break;
+                if (p.vo[j] != rank) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+            }
+        }
+    }
+}
+
 // ---- kernel
 
-template <bool kDelta>
-__global__ void __launch_bounds__(kThreads, 5) sdecode_kernel(const Params p)
+template <bool kDelta, bool kSeg>
+__global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const Params p)
 {
-    __shared__ Shared S;
+    using Sm = typename std::conditional<kSeg, SharedS, Shared>::type;
+    __shared__ Sm S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t total = p.ntiles + p.lead;
     const uint64_t nchunks = (p.ntiles + kChunk - 1) / kChunk;
@@ -534,9 +881,17 @@ __global__ void __launch_bounds__(kThreads, 5) sdecode_kernel(const Params p)
             const uint64_t t = tk - p.lead;
             issue_stage(p, t, tid, S.dbytes[b]);
             if (t % kChunk != 0 && static_cast<long long>(t / kChunk) <= ready) {
-                if (warp == 0) stage_prefix(p, t, lane, S, b);
+                if constexpr (kSeg) {
+                    if (tid == 0) cp_async16(&S.pgpre[b], p.tpre + 2 * t);   // the tile's own prefix
+                } else {
+                    if (warp == 0) stage_prefix(p, t, lane, S, b);
+                }
                 pf = 1;
             }
+        }
+        if constexpr (kSeg) {   // the tiles' list-head ranges travel with them
+            if (tid == 32 && tk < p.ntiles) cp_async16(S.hrc[b], p.hr + 2 * tk);
+            if (tid == 64 && tk >= p.lead && tk < total) cp_async16(S.hrd[b], p.hr + 2 * (tk - p.lead));
         }
         if (tid == 0) S.pf[b] = pf;
         cp_async_commit();
@@ -560,16 +915,74 @@ __global__ void __launch_bounds__(kThreads, 5) sdecode_kernel(const Params p)
         }
         if (kn < total) stage(kn, b ^ 1);
         // the count this CTA published last iteration completed its chunk
-        if (S.scan_c >= 0) chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);   // CTA-uniform
+        if (S.scan_c >= 0) {   // CTA-uniform
+            if constexpr (kSeg)
+                chunk_scan_seg(p, static_cast<uint64_t>(S.scan_c), S);
+            else
+                chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);
+        }
 
         const bool dec = k >= p.lead;
         const uint64_t t = k - p.lead;
-        if (k < p.ntiles) count_partials<kDelta>(p, k, S, S.cbytes[b]);
+        // batched lists: the heads of the count tile (delta only) and of the decode tile
+        bool cheads = false, dheads = false;
+        uint64_t cha = 0, che = 0, dha = 0, dhe = 0;
+        if constexpr (kSeg) {
+            if (kDelta && k < p.ntiles) {
+                cha = S.hrc[b][0];
+                che = S.hrc[b][1];
+                cheads = cha < che;
+            }
+            if (dec) {
+                dha = S.hrd[b][0];
+                dhe = S.hrd[b][1];
+                dheads = dha < dhe;
+            }
+            if (cheads || dheads) {   // CTA-uniform
+                for (int i = tid; i < kHeadWords; i += kThreads) {
+                    S.hc.bits[i] = 0u;
+                    S.hd.bits[i] = 0u;
+                }
+                __syncthreads();
+                if (cheads) fill_heads(head_src(p), static_cast<long long>(p.base + k * kTile) -
+                                                         static_cast<long long>(reinterpret_cast<uintptr_t>(p.in)),
+                                       cha, che, S.hc, true, false, kThreads);
+                if (dheads) fill_heads(head_src(p), static_cast<long long>(p.base + t * kTile) -
+                                                         static_cast<long long>(reinterpret_cast<uintptr_t>(p.in)),
+                                       dha, dhe, S.hd, kDelta, true, kThreads);
+                __syncthreads();
+            }
+        }
+        if (k < p.ntiles) {
+            if constexpr (kSeg) {
+                if (cheads)
+                    count_partials_seg(p, k, S, S.cbytes[b], cha, che);
+                else {
+                    count_partials<kDelta>(p, k, S, S.cbytes[b]);
+                    if (lane == 0) S.cflag[warp] = 0u;
+                }
+            } else {
+                count_partials<kDelta>(p, k, S, S.cbytes[b]);
+            }
+        }
         if (dec) {
             if (warp == 0) {
                 unsigned long long R0;
                 uint32_t S0;
-                if (S.pf[b]) {
+                if constexpr (kSeg) {
+                    if (!S.pf[b]) {
+                        if (lane == 0) spin_flag(p.cready + t / kChunk, p.status);
+                        __syncwarp();
+                        ready = std::max<long long>(ready, static_cast<long long>(t / kChunk));
+                        if (lane == 0) {
+                            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tpre + 2 * t));
+                            S.pgpre[b] = d;
+                        }
+                        __syncwarp();
+                    }
+                    R0 = S.pgpre[b].x;
+                    S0 = static_cast<uint32_t>(S.pgpre[b].y);
+                } else if (S.pf[b]) {
                     fold_staged(t, lane, S, b, R0, S0);
                 } else {
                     if (lane == 0) spin_flag(p.cready + t / kChunk, p.status);
@@ -582,16 +995,38 @@ __global__ void __launch_bounds__(kThreads, 5) sdecode_kernel(const Params p)
                     S.S0 = S0;
                 }
             }
-            decode_stage<kDelta>(p, t, S, S.dbytes[b]);
+            if constexpr (kSeg) {
+                if (kDelta && dheads) {
+                    decode_stage_seg<kDelta>(p, t, S, S.dbytes[b], dha, dhe);
+                } else {
+                    decode_stage<kDelta>(p, t, S, S.dbytes[b]);
+                    if (lane == 0) {
+                        S.dflag[warp] = 0u;
+                        S.dhf[warp] = 0xFFFFFFFFu;
+                    }
+                }
+            } else {
+                decode_stage<kDelta>(p, t, S, S.dbytes[b]);
+            }
         }
         __syncthreads();   // count partials, decode partials and the prefix are in place
         long long pend_c = -1;
         unsigned int pend_old = 0;
         if (k < p.ntiles && warp == kWarps - 1) {
-            pend_old = count_publish<kDelta>(p, k, S, lane);
+            if constexpr (kSeg)
+                pend_old = count_publish_seg<kDelta>(p, k, S, lane);
+            else
+                pend_old = count_publish<kDelta>(p, k, S, lane);
             pend_c = static_cast<long long>(k / kChunk);
         }
-        if (dec) decode_emit<kDelta>(p, S);
+        if (dec) {
+            if constexpr (kSeg) {
+                decode_emit_seg<kDelta>(p, S);
+                if (dheads) check_heads(p, t, S, S.dbytes[b], dha, dhe, S.R0);
+            } else {
+                decode_emit<kDelta>(p, S);
+            }
+        }
         // did this count complete its chunk?  (read after the emission, so the
         // atomic has had time to return); the scan runs after the next barrier,
         // before any decode of this CTA waits
@@ -601,7 +1036,12 @@ __global__ void __launch_bounds__(kThreads, 5) sdecode_kernel(const Params p)
         k = kn;
     }
     __syncthreads();
-    if (S.scan_c >= 0) chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);
+    if (S.scan_c >= 0) {
+        if constexpr (kSeg)
+            chunk_scan_seg(p, static_cast<uint64_t>(S.scan_c), S);
+        else
+            chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);
+    }
     cp_async_wait_all();
 }
 
@@ -634,7 +1074,8 @@ uint64_t tiles_for(uintptr_t addr, size_t nbytes) { return nbytes ? ((addr & 15u
 
 struct Dev {
     int sms = 0;
-    int occ[2] = {0, 0};
+    int occ[2] = {0, 0};       // single stream: plain, delta
+    int occ_seg[2] = {0, 0};   // batched lists: plain, delta
 };
 std::mutex g_mu;
 std::map<int, Dev> g_dev;
@@ -647,9 +1088,12 @@ int dev_info(Dev *out)
     Dev &d = g_dev[dev];
     if (d.sms == 0) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return VBYTE_ECUDA;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], sdecode_kernel<false>, kThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], sdecode_kernel<true>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], sdecode_kernel<false, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], sdecode_kernel<true, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_seg[0], sdecode_kernel<false, true>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_seg[1], sdecode_kernel<true, true>, kThreads, 0);
         for (int &o : d.occ) o = std::max(o, 1);
+        for (int &o : d.occ_seg) o = std::max(o, 1);
     }
     *out = d;
     return VBYTE_OK;
@@ -696,9 +1140,91 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     p.lead = std::min<uint64_t>(sd::kChunk + sd::kSlack, ntiles);
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
     if (delta)
-        sd::sdecode_kernel<true><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+        sd::sdecode_kernel<true, false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
     else
-        sd::sdecode_kernel<false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+        sd::sdecode_kernel<false, false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
+// ---- batched lists
+
+namespace sd {
+// Workspace of a batched decode: status head, ticket counter, per chunk
+// cnext/cdone/cready, per tile a descriptor, a prefix and a head range.
+struct LayoutB {
+    size_t ctr, cnext, cdone, cready, tdesc, tpre, hr, total, clear;
+};
+
+LayoutB layout_b(uint64_t ntiles)
+{
+    LayoutB L;
+    const uint64_t nchunks = (ntiles + kChunk - 1) / kChunk;
+    L.ctr = 256;
+    L.cnext = L.ctr + 16;
+    L.cdone = L.cnext + 16 * nchunks;
+    L.cready = L.cdone + 4 * nchunks;
+    L.tdesc = (L.cready + 4 * nchunks + 15) / 16 * 16;
+    L.tpre = L.tdesc + 16 * ntiles;
+    L.hr = L.tpre + 16 * ntiles;
+    L.total = L.hr + 16 * ntiles;
+    L.clear = L.tdesc - L.ctr;
+    return L;
+}
+}  // namespace sd
+
+int sbatched_max_ctas(bool delta)
+{
+    sd::Dev di;
+    return sd::dev_info(&di) == VBYTE_OK ? di.occ_seg[delta] : 1;
+}
+
+size_t sbatched_workspace_bytes(const BatchArgs &a)
+{
+    return sd::layout_b(sd::tiles_for(reinterpret_cast<uintptr_t>(a.in), a.nbytes)).total;
+}
+
+int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cudaStream_t s)
+{
+    sd::Dev di;
+    int rc = sd::dev_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(a.in);
+    const uint64_t ntiles = sd::tiles_for(addr, a.nbytes);
+    const sd::LayoutB Y = sd::layout_b(ntiles);
+    uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+    uint64_t *hr = reinterpret_cast<uint64_t *>(ws + Y.hr);
+    rc = enqueue_head_ranges(a.in, a.nbytes, a.bo, a.vo, a.L, a.n, hr, status, di.sms, s);
+    if (rc != VBYTE_OK) return rc;
+    if (a.nbytes == 0) return a.n > 0 ? set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s) : VBYTE_OK;
+    if (cudaMemsetAsync(ws + Y.ctr, 0, Y.clear, s) != cudaSuccess) return VBYTE_ECUDA;
+    sd::Params p = {};
+    p.in = a.in;
+    p.nbytes = a.nbytes;
+    p.out = a.out;
+    p.n = a.n;
+    p.ntiles = ntiles;
+    p.base = addr & ~static_cast<uintptr_t>(15);
+    p.tdesc = reinterpret_cast<uint64_t *>(ws + Y.tdesc);
+    p.cnext = reinterpret_cast<uint64_t *>(ws + Y.cnext);
+    p.cdone = reinterpret_cast<unsigned int *>(ws + Y.cdone);
+    p.cready = reinterpret_cast<unsigned int *>(ws + Y.cready);
+    p.ctr = reinterpret_cast<unsigned long long *>(ws + Y.ctr);
+    p.status = status;
+    p.prev = 0u;
+    p.lead = std::min<uint64_t>(sd::kChunk + cfg.lead_slack, ntiles);
+    p.bo = a.bo;
+    p.vo = a.vo;
+    p.prevs = a.prevs;
+    p.L = a.L;
+    p.hr = hr;
+    p.tpre = reinterpret_cast<uint64_t *>(ws + Y.tpre);
+    const int occ = di.occ_seg[a.delta];
+    const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
+    const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * per_sm);
+    if (a.delta)
+        sd::sdecode_kernel<true, true><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    else
+        sd::sdecode_kernel<false, true><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
