@@ -1,7 +1,8 @@
-// Internal interface between the decode kernels (vbyte_decode.cu) and the
-// host runtime built on them (vbyte_runtime.cpp: batched plans, the
-// one-call-per-list form, the serving loop).  Not installed; not part of the
-// C ABI.
+// Internal interface between the decode kernels (vbyte_stream.cu), the host
+// side of the library (vbyte_api.cu: workspaces, entry points) and the
+// runtime built on them (vbyte_runtime.cpp: batched plans and the
+// one-call-per-list form; vbyte_server.cpp: the serving loop).  Not
+// installed; not part of the C ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,14 +12,6 @@
 namespace vbk {
 
 constexpr uint64_t kDefaultLeadSlack = 2560;
-
-// Per device: SM count and the decode kernels' occupancy (CTAs per SM) for
-// plain / delta, single-stream (occ) and batched (occ_seg).
-struct DeviceInfo {
-    int sms = 0;
-    int occ[2] = {0, 0};
-    int occ_seg[2] = {0, 0};
-};
 
 // One batched decode: list j is bytes [bo[j], bo[j+1]) of in and values
 // [vo[j], vo[j+1]) of out (bo, vo, prevs in device memory).
@@ -40,20 +33,20 @@ struct LaunchCfg {
     uint64_t lead_slack = kDefaultLeadSlack;    // tickets between a chunk's last count and first decode
 };
 
-int device_info(DeviceInfo *di);
 int check_batch(const BatchArgs &a);
-uint64_t batch_tiles(const BatchArgs &a);
-size_t batch_workspace_bytes(const BatchArgs &a);
-// Queue a checked batch (L > 0) on s with its scratch in ws (at least
-// batch_workspace_bytes(a) bytes; ws[0..4) is the status word).
-int enqueue_batched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, const DeviceInfo &di, cudaStream_t s);
 // The per-stream workspace of s (current device) with at least need bytes;
 // its first 4 bytes are the stream's status word.
 int stream_workspace(cudaStream_t s, size_t need, uint8_t **ptr);
 // OR bits into a device status word, on s.
 int set_status_async(uint32_t *status, uint32_t bits, cudaStream_t s);
-// Workspace bytes of the single-stream decoder for an nbytes input.
-size_t wdecode_workspace_bytes(size_t nbytes);
+// Workspace bytes of the single-stream decoder for an input at `in`.
+size_t stream_workspace_bytes(const uint8_t *in, size_t nbytes);
+// Enough workspace for any single-stream or batched call on nbytes.
+size_t workspace_bound(size_t nbytes);
+// Queue a checked single-stream decode (nbytes > 0) with its scratch in ws
+// (stream_workspace_bytes) and data errors OR-ed into *status.
+int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
+                   uint8_t *ws, uint32_t *status, cudaStream_t s);
 // The single-stream call with the per-stream workspace.
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
                   cudaStream_t s);
@@ -72,9 +65,12 @@ void release_workspace(cudaStream_t s);
 // as two uint64 per tile in hr; also checks the offset arrays' contract.
 int enqueue_head_ranges(const uint8_t *in, size_t nbytes, const uint64_t *bo, const uint64_t *vo, size_t L,
                         size_t n, uint64_t *hr, uint32_t *status, int sms, cudaStream_t s);
-// Batched decode with the single-stream kernel's structure (vbyte_stream.cu).
+// Batched decode (vbyte_stream.cu): its scratch in ws (sbatched_workspace_bytes;
+// ws[0..4) is the status word).
 size_t sbatched_workspace_bytes(const BatchArgs &a);
 int sbatched_max_ctas(bool delta);   // CTAs per SM of that kernel
+// Load the decoders' code and query their occupancy now (not at first use).
+int load_kernels();
 int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cudaStream_t s);
 
 // A piece of a gather: len bytes from src + src_off to dst + dst_off.

@@ -40,8 +40,8 @@ ClassKey class_of(int dev, const vbk::BatchArgs &a)
 }
 
 // Median time of `reps` runs of cfg on s (after one untimed run).
-int time_cfg(const vbk::BatchArgs &a, uint8_t *ws, const vbk::LaunchCfg &cfg, const vbk::DeviceInfo &di,
-             cudaStream_t s, int reps, float *ms)
+int time_cfg(const vbk::BatchArgs &a, uint8_t *ws, const vbk::LaunchCfg &cfg, cudaStream_t s, int reps,
+             float *ms)
 {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return VBYTE_ECUDA;
@@ -83,9 +83,6 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
     int rc = vbk::check_batch(a);
     if (rc != VBYTE_OK) return rc;
     if (num_lists == 0) return VBYTE_EINVAL;
-    vbk::DeviceInfo di;
-    rc = vbk::device_info(&di);
-    if (rc != VBYTE_OK) return rc;
     vbyte_plan *P = new vbyte_plan();
     P->a = a;
     cudaGetDevice(&P->dev);
@@ -129,7 +126,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
                     cfg.ctas_per_sm = c;
                     cfg.lead_slack = sl;
                     float ms = 0.f;
-                    rc = time_cfg(a, P->ws, cfg, di, s, 3, &ms);
+                    rc = time_cfg(a, P->ws, cfg, s, 3, &ms);
                     if (rc != VBYTE_OK) return fail(rc);
                     if (P->tuned == 0 || ms < best) {
                         best = ms;

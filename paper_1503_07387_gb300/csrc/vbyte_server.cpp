@@ -393,8 +393,7 @@ int vbyte_server_create(vbyte_server **out, const uint8_t *d_pool, size_t pool_b
         if (cudaStreamSynchronize(sl.stream) != cudaSuccess) return fail(VBYTE_ECUDA);
     }
     // kernel code is loaded now, not at the first query
-    vbk::DeviceInfo di;
-    if (vbk::device_info(&di) != VBYTE_OK || vbk::load_gather_kernel() != VBYTE_OK) return fail(VBYTE_ECUDA);
+    if (vbk::load_kernels() != VBYTE_OK || vbk::load_gather_kernel() != VBYTE_OK) return fail(VBYTE_ECUDA);
     S->worker = std::thread([S] { S->run(); });
     *out = S;
     return VBYTE_OK;

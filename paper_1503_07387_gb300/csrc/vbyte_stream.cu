@@ -1101,7 +1101,10 @@ int dev_info(Dev *out)
 
 }  // namespace sd
 
-size_t wdecode_workspace_bytes(size_t nbytes) { return sd::layout(sd::tiles_for(15, nbytes)).total; }
+size_t stream_workspace_bytes(const uint8_t *in, size_t nbytes)
+{
+    return sd::layout(sd::tiles_for(reinterpret_cast<uintptr_t>(in), nbytes)).total;
+}
 
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
                   cudaStream_t s)
@@ -1109,16 +1112,22 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     if (nbytes == 0 && n == 0) return VBYTE_OK;
     if ((nbytes && !in) || (n && !out)) return VBYTE_EINVAL;
     if (reinterpret_cast<uintptr_t>(out) & 3u) return VBYTE_EINVAL;
-    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
-    const uint64_t ntiles = sd::tiles_for(a, nbytes);
-    const sd::Layout L = sd::layout(ntiles);
     uint8_t *ws = nullptr;
-    int rc = stream_workspace(s, L.total, &ws);
+    const int rc = stream_workspace(s, stream_workspace_bytes(in, nbytes), &ws);
     if (rc != VBYTE_OK) return rc;
     uint32_t *status = reinterpret_cast<uint32_t *>(ws);
     if (nbytes == 0) return set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s);   // n > 0 from no bytes
+    return enqueue_stream(in, nbytes, out, n, delta, prev, ws, status, s);
+}
+
+int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
+                   uint8_t *ws, uint32_t *status, cudaStream_t s)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
+    const uint64_t ntiles = sd::tiles_for(a, nbytes);
+    const sd::Layout L = sd::layout(ntiles);
     sd::Dev di;
-    rc = sd::dev_info(&di);
+    const int rc = sd::dev_info(&di);
     if (rc != VBYTE_OK) return rc;
     if (cudaMemsetAsync(ws + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
     sd::Params p = {};
@@ -1171,6 +1180,18 @@ LayoutB layout_b(uint64_t ntiles)
     return L;
 }
 }  // namespace sd
+
+size_t workspace_bound(size_t nbytes)
+{
+    const uint64_t ntiles = sd::tiles_for(15, nbytes);   // the worst alignment
+    return std::max(sd::layout(ntiles).total, sd::layout_b(ntiles).total);
+}
+
+int load_kernels()
+{
+    sd::Dev di;
+    return sd::dev_info(&di);
+}
 
 int sbatched_max_ctas(bool delta)
 {
