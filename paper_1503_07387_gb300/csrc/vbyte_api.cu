@@ -222,7 +222,7 @@ int launch_decode_batched(const BatchArgs &a, cudaStream_t s)
 // ---- scratch for vbyte_decode_noalloc
 // A file-scope device array replaces the per-stream workspace for callers
 // that cannot allocate device memory.  It holds the single-stream layout of
-// an input of up to VBYTE_NOALLOC_MAX_BYTES bytes (about 545 KiB); every call
+// an input of up to VBYTE_NOALLOC_MAX_BYTES bytes (about 513 KiB); every call
 // on a device shares it.
 constexpr size_t kStaticScratchBytes = size_t(576) << 10;
 static __device__ __align__(256) uint8_t g_scratch[kStaticScratchBytes];

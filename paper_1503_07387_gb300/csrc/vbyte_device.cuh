@@ -42,23 +42,6 @@ __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.w
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Fire-and-forget increment with release semantics: every global write this
-// thread made before is visible to whoever observes the new value.
-__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Atomic add with acquire-release semantics at GPU scope; returns the old
-// value.  The last of several publishers learns that it is last and sees
-// everything the others released before their increments.
-__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v)
-{
-    unsigned int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
@@ -66,26 +49,40 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+// Words published between CTAs carry their own validity: bit 0 is set in
+// every written value and the workspace is cleared before each launch, so a
+// reader needs no fence -- one 64-bit relaxed access is the whole protocol.
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p)
 {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// One thread waits (acquire) until *flag != 0, bounded by the global timer;
-// on expiry the status word gets VBYTE_ERR_TIMEOUT and the caller carries on.
-__device__ __forceinline__ void spin_flag(const unsigned int *flag, uint32_t *status)
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// One thread waits until *p has bit 0 set, bounded by the global timer; on
+// expiry, or once another wait of the launch has expired, the status word has
+// VBYTE_ERR_TIMEOUT and 0 is returned.
+__device__ __forceinline__ uint64_t wait_word(const uint64_t *p, uint32_t *status)
 {
     uint64_t t0 = 0;
-    for (int spin = 0; ld_acquire_u32(flag) == 0u; ++spin) {
+    for (int spin = 0;; ++spin) {
+        const uint64_t v = ld_relaxed_u64(p);
+        if (v & 1u) return v;
         const uint64_t now = global_ns();
         if (t0 == 0) t0 = now;
         if (now - t0 > kWaitLimitNs) {
             atomicOr(status, VBYTE_ERR_TIMEOUT);
-            break;
+            return 0u;
         }
-        if (spin > 4) __nanosleep(200);
+        if (spin > 4) {
+            if (*reinterpret_cast<volatile uint32_t *>(status) & VBYTE_ERR_TIMEOUT) return 0u;
+            __nanosleep(200);
+        }
     }
 }
 

@@ -17,15 +17,19 @@
 //     processed.
 //   * Count (a): per warp, terminator counts and (delta) value sums of its
 //     slices; after the iteration's middle barrier one warp publishes the
-//     tile's descriptor, adds it to its group's aggregates and releases the
-//     chunk's counter.  The data-error contract is checked here.
-//   * Chunk scan: the CTA whose count completes a chunk (its acquire-release
-//     increment of the chunk's counter returns the last value) scans the
-//     chunk's 64 group aggregates at the start of its next iteration, once
-//     the chunk before it is scanned -- before the chunk's first decode
-//     ticket, and before any decode of its own that could wait on it.
-//   * Decode (b, c): the tile prefix is the group prefix plus the earlier
-//     tiles of the group (staged an iteration ahead by warp 0).  Each warp
+//     tile's descriptor word and increments the chunk's counter.  The
+//     data-error contract is checked here.
+//   * Chunk scan: the CTA whose count completes a chunk (its increment of the
+//     chunk's counter returns the last value) scans the chunk's 2048 tile
+//     descriptors at the start of its next iteration: one prefix word per
+//     tile, relative to the chunk's start, then the chunk's totals chained
+//     to the chunk before it -- before the chunk's first decode ticket, and
+//     before any decode of its own that could wait on it.
+//   * Every word passed between CTAs (tile descriptors, tile prefixes, chunk
+//     totals) carries a validity bit and is written and read with one 64-bit
+//     relaxed access, so no step takes a memory fence.
+//   * Decode (b, c): the tile prefix (its word and the totals of the chunk
+//     before it) is staged an iteration ahead.  Each warp
 //     stages its 512 bytes' values in its own buffer -- one-byte integers
 //     straight from the bytes, codes of at most two bytes by a SWAR byte-pair
 //     merge, longer codes by per-terminator assembly, each value assembled
@@ -56,14 +60,29 @@ constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * kLanes;
 constexpr int kTile = kThreads * kBPT;          // 4 KiB per tile
 constexpr int kWarpBytes = kLanes * kBPT;       // 512 bytes per warp
-constexpr int kGroup = 32;                      // tiles per group
 constexpr uint64_t kChunk = 2048;               // tiles per chunk (8 MiB)
-constexpr int kGroupsPerChunk = static_cast<int>(kChunk / kGroup);   // 64
 constexpr uint64_t kSlack = 2560;               // tickets between a chunk's last count ticket and its first decode
 constexpr int kByteBuf = kHalo + kTile + 16;
 constexpr int kWarpValBuf = kWarpBytes + 16;    // staged values of one warp (528)
 constexpr int kStages = 2;                      // tickets in flight per CTA (processed + staged)
-static_assert(kGroupsPerChunk <= kThreads && kGroupsPerChunk % 32 == 0, "chunk scan: one thread per group");
+static_assert(kChunk % kThreads == 0, "chunk scan: whole tiles per thread");
+static_assert(kChunk * kTile < (1ull << 24), "relative tile prefixes fit 23 bits");
+
+// Published words (bit 0 = written):
+//   tile descriptor  sum << 32 | f << 14 | count << 1 | 1   (count <= 4096)
+//   tile prefix      s << 32 | f << 24 | rel << 1 | 1       (rel < 2^23: values
+//                    in the chunk before the tile; (f, s) the segmented sum
+//                    of the chunk's earlier tiles, f = 0 without list heads)
+//   chunk totals     count << 1 | 1, x << 32 | 1            (values and running
+//                    x after the chunk)
+__device__ __forceinline__ uint64_t desc_word(uint32_t cnt, uint32_t f, uint32_t sum)
+{
+    return (static_cast<uint64_t>(sum) << 32) | (static_cast<uint64_t>(f) << 14) |
+           (static_cast<uint64_t>(cnt) << 1) | 1u;
+}
+__device__ __forceinline__ uint32_t desc_count(uint64_t w) { return static_cast<uint32_t>(w >> 1) & 0x1FFFu; }
+__device__ __forceinline__ uint32_t desc_flag(uint64_t w) { return static_cast<uint32_t>(w >> 14) & 1u; }
+__device__ __forceinline__ uint32_t word_hi(uint64_t w) { return static_cast<uint32_t>(w >> 32); }
 
 struct Params {
     const uint8_t *in;
@@ -72,12 +91,10 @@ struct Params {
     uint64_t n;
     uint64_t ntiles;
     uintptr_t base;            // 16-byte aligned address of tile 0
-    uint64_t *tdesc;           // per tile: count, value sum
-    unsigned long long *gagg;  // per group: count, value sum (atomic accumulators)
-    uint64_t *gpre;            // per group: values before it, running x before it
-    uint64_t *cnext;           // per chunk: values and running x after it
+    uint64_t *tdesc;           // per tile: descriptor word
+    uint64_t *tpre;            // per tile: prefix word
+    uint64_t *cnext;           // per chunk: totals words (values, running x after it)
     unsigned int *cdone;       // per chunk: tiles counted
-    unsigned int *cready;      // per chunk: group prefixes published
     unsigned long long *ctr;   // tickets
     uint32_t *status;
     uint32_t prev;             // x_0
@@ -88,7 +105,6 @@ struct Params {
     const uint32_t *prevs;     // per-list x_0 (nullptr: 0)
     uint64_t L;
     const uint64_t *hr;        // per tile: [first, end) of the lists whose head may own a terminator in it
-    uint64_t *tpre;            // per tile: values before it, running x before it
 };
 
 struct Shared {
@@ -99,13 +115,11 @@ struct Shared {
     uint32_t dcnt[kWarps], dsum[kWarps];           // decode: per-warp totals
     unsigned long long R0;                         // decode: values before the tile
     uint32_t S0;                                   // decode: running x before the tile
-    alignas(16) ulonglong2 pdesc[kStages][kGroup];   // prefetched: earlier tiles of the decode tile's group
-    alignas(16) ulonglong2 pgpre[kStages];         // prefetched: the group's prefix
-    uint32_t pf[kStages];                          // prefetch issued for this buffer
+    alignas(16) ulonglong2 pcn[kStages];           // prefetched: totals of the chunk before the decode tile's
+    alignas(16) ulonglong2 ptp[kStages];           // prefetched: the decode tile's prefix word (and its pair's)
     unsigned long long tnext;                      // the ticket to stage next
     unsigned long long tinit[2];                   // the first two tickets
-    unsigned long long gsc[kWarps];                // chunk scan
-    uint32_t gss[kWarps];
+    uint32_t csc[kWarps], css[kWarps], csf[kWarps];   // chunk scan partials
     long long scan_c;                              // chunk this CTA completed (scans it), or -1
 };
 // Batched lists: the list heads of the count and the decode tile, per-warp
@@ -117,15 +131,13 @@ struct SharedS : Shared {
     uint32_t cflag[kWarps];                     // count: a list head was crossed in this warp
     uint32_t dflag[kWarps];                     // decode: the same
     uint32_t dhf[kWarps];                       // decode: this warp's first rank after a head (values from it on are absolute)
-    unsigned long long csc[kWarps];             // segmented chunk scan partials
-    uint32_t css[kWarps], csf[kWarps];
 };
 static_assert(offsetof(SharedS, hrc) % 16 == 0 && offsetof(SharedS, hrd) % 16 == 0, "head range alignment");
 
 static_assert(offsetof(Shared, cbytes) % 16 == 0 && kByteBuf % 16 == 0, "cbytes alignment");
 static_assert(offsetof(Shared, dbytes) % 16 == 0 && offsetof(Shared, vals) % 16 == 0, "dbytes/vals alignment");
 static_assert((kWarpValBuf * 4) % 16 == 0, "per-warp value buffers keep 16-byte alignment");
-static_assert(offsetof(Shared, pdesc) % 16 == 0 && offsetof(Shared, pgpre) % 16 == 0, "prefix buffers alignment");
+static_assert(offsetof(Shared, pcn) % 16 == 0 && offsetof(Shared, ptp) % 16 == 0, "prefix buffers alignment");
 
 // Stage tile t (its 16-byte slices, the 16 bytes before it, zeros outside
 // the stream) into `bytes`; the caller commits, waits and syncs.
@@ -204,8 +216,8 @@ __device__ __forceinline__ void count_partials(const Params &p, uint64_t t, Shar
     }
 }
 
-// One warp, after the middle barrier: publish tile t's totals.  Lane 0
-// returns the chunk counter's old value (read an iteration later).
+// One warp, after the middle barrier: publish tile t's descriptor.  Lane 0
+// returns the chunk counter's old value (read at the end of the iteration).
 template <bool kDelta>
 __device__ __forceinline__ unsigned int count_publish(const Params &p, uint64_t t, const Shared &S, int lane)
 {
@@ -213,11 +225,8 @@ __device__ __forceinline__ unsigned int count_publish(const Params &p, uint64_t 
     const uint32_t ts = kDelta ? __reduce_add_sync(~0u, lane < kWarps ? S.csum[lane] : 0u) : 0u;
     unsigned int old = 0;
     if (lane == 0) {
-        const uint64_t g = t / kGroup;
-        *reinterpret_cast<ulonglong2 *>(p.tdesc + 2 * t) = make_ulonglong2(tc, ts);
-        atomicAdd(p.gagg + 2 * g, static_cast<unsigned long long>(tc));
-        if (kDelta) atomicAdd(p.gagg + 2 * g + 1, static_cast<unsigned long long>(ts));
-        old = atom_add_acq_rel(p.cdone + t / kChunk, 1u);
+        st_relaxed_u64(p.tdesc + t, desc_word(tc, 0u, ts));
+        old = atomicAdd(p.cdone + t / kChunk, 1u);
     }
     return old;
 }
@@ -230,136 +239,121 @@ __device__ __forceinline__ uint64_t chunk_tiles(const Params &p, long long c)
     return ((c0 + kChunk < p.ntiles) ? c0 + kChunk : p.ntiles) - c0;
 }
 
-__device__ __forceinline__ void cta_wait_flag(const unsigned int *flag, unsigned int target, uint32_t *status)
-{
-    if (threadIdx.x == 0) {
-        uint64_t t0 = 0;
-        for (int spin = 0; ld_acquire_u32(flag) < target; ++spin) {
-            const uint64_t now = global_ns();
-            if (t0 == 0) t0 = now;
-            if (now - t0 > kWaitLimitNs) {
-                atomicOr(status, VBYTE_ERR_TIMEOUT);
-                break;
-            }
-            if (spin > 4) __nanosleep(200);
-        }
-    }
-    __syncthreads();
-}
-
-template <bool kDelta>
+// Prefix words of chunk c's tiles from their descriptors (segmented sums
+// when kSeg), then the chunk's totals chained to the chunk before it.  Run by
+// the CTA that completed the chunk's count.
+template <bool kSeg>
 __device__ void chunk_scan(const Params &p, uint64_t c, Shared &S)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kPer = static_cast<int>(kChunk / kThreads);   // 8
     const uint64_t c0 = c * kChunk;
     const uint64_t c1 = (c0 + kChunk < p.ntiles) ? c0 + kChunk : p.ntiles;
-    uint64_t pc = 0;
-    uint32_t ps = p.prev;
-    if (c > 0) {
-        cta_wait_flag(p.cready + (c - 1), 1u, p.status);
-        pc = __ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1)));
-        ps = static_cast<uint32_t>(__ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1) + 1)));
-    }
-    const uint64_t ng = (p.ntiles + kGroup - 1) / kGroup;
-    const uint64_t g = c * kGroupsPerChunk + tid;
-    uint64_t ac = 0;
-    uint32_t as = 0;
-    if (tid < kGroupsPerChunk && g < ng) {
-        const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2 *>(p.gagg + 2 * g));
-        ac = a.x;
-        as = static_cast<uint32_t>(a.y);
-    }
-    const uint64_t ic = warp_incl_scan64(ac, lane);
-    const uint32_t is = warp_incl_scan(as, lane);
-    if (lane == 31) {
-        S.gsc[warp] = ic;
-        S.gss[warp] = is;
-    }
-    __syncthreads();
-    uint64_t wc0 = 0, tc_all = 0;
-    uint32_t ws0 = 0, ts_all = 0;
+    const uint64_t tb = c0 + static_cast<uint64_t>(kPer) * tid;
+    // the thread's descriptors in one batch of loads (words past the chunk
+    // stay inside the workspace and are ignored), then waits for any not yet
+    // published
+    uint64_t d[kPer];
 #pragma unroll
-    for (int q = 0; q < kGroupsPerChunk / 32; ++q) {
-        wc0 += (q < warp) ? S.gsc[q] : 0ull;
-        ws0 += (q < warp) ? S.gss[q] : 0u;
-        tc_all += S.gsc[q];
-        ts_all += S.gss[q];
+    for (int i = 0; i < kPer; i += 2) {
+        ulonglong2 v = make_ulonglong2(0ull, 0ull);
+        if (tb + i < c1) v = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + tb + i));
+        d[i] = v.x;
+        d[i + 1] = v.y;
     }
-    if (tid < kGroupsPerChunk && g < ng)
-        *reinterpret_cast<ulonglong2 *>(p.gpre + 2 * g) =
-            make_ulonglong2(pc + wc0 + ic - ac, static_cast<uint32_t>(ps + ws0 + is - as));
-    __threadfence();
+    uint32_t tcn = 0;
+    Seg ts;
+    ts.f = ts.s = 0u;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        if (tb + i < c1) {
+            if (!(d[i] & 1u)) d[i] = wait_word(p.tdesc + tb + i, p.status);
+            Seg e;
+            e.f = kSeg ? desc_flag(d[i]) : 0u;
+            e.s = word_hi(d[i]);
+            tcn += desc_count(d[i]);
+            ts = seg_op(ts, e);
+        }
+    }
+    const uint32_t icn = warp_incl_scan(tcn, lane);
+    const Seg is = warp_seg_incl(ts, lane);
+    if (lane == 31) {
+        S.csc[warp] = icn;
+        S.css[warp] = is.s;
+        S.csf[warp] = is.f;
+    }
     __syncthreads();
+    uint32_t wc0 = 0, call = 0;
+    Seg w0, wall;
+    w0.f = w0.s = wall.f = wall.s = 0u;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+        Seg e;
+        e.f = S.csf[q];
+        e.s = S.css[q];
+        if (q < warp) {
+            wc0 += S.csc[q];
+            w0 = seg_op(w0, e);
+        }
+        call += S.csc[q];
+        wall = seg_op(wall, e);
+    }
+    Seg ex;
+    ex.f = __shfl_up_sync(~0u, is.f, 1);
+    ex.s = __shfl_up_sync(~0u, is.s, 1);
+    if (lane == 0) ex.f = ex.s = 0u;
+    uint32_t rel = wc0 + icn - tcn;
+    Seg x = seg_op(w0, ex);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        if (tb + i < c1) {
+            st_relaxed_u64(p.tpre + tb + i, (static_cast<uint64_t>(x.s) << 32) |
+                                                (static_cast<uint64_t>(x.f) << 24) |
+                                                (static_cast<uint64_t>(rel) << 1) | 1u);
+            Seg e;
+            e.f = kSeg ? desc_flag(d[i]) : 0u;
+            e.s = word_hi(d[i]);
+            rel += desc_count(d[i]);
+            x = seg_op(x, e);
+        }
+    }
     if (tid == 0) {
-        p.cnext[2 * c] = pc + tc_all;
-        p.cnext[2 * c + 1] = static_cast<uint32_t>(ps + ts_all);
-        if (c1 == p.ntiles && pc + tc_all != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
-        __threadfence();
-        *reinterpret_cast<volatile unsigned int *>(p.cready + c) = 1u;
+        uint64_t pc = 0;
+        uint32_t ps = p.prev;
+        if (c > 0) {
+            pc = wait_word(p.cnext + 2 * (c - 1), p.status) >> 1;
+            ps = word_hi(wait_word(p.cnext + 2 * (c - 1) + 1, p.status));
+        }
+        st_relaxed_u64(p.cnext + 2 * c, ((pc + call) << 1) | 1u);
+        st_relaxed_u64(p.cnext + 2 * c + 1, (static_cast<uint64_t>(seg_apply(ps, wall)) << 32) | 1u);
+        if (c1 == p.ntiles && pc + call != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
     }
-    __syncthreads();
 }
 
-// ---- tile prefixes (warp 0)
+// ---- tile prefixes
 
-struct PrefixLoads {
-    uint64_t pa, pb, ga, gb;
-    bool ok;
-};
-
-__device__ __forceinline__ PrefixLoads load_prefix(const Params &p, uint64_t t, int lane)
+// One thread: the decode tile's values before it (R0) and running x before
+// it (S0), from the words staged an iteration ahead, re-read (bounded) if
+// they were not yet published then.  After a timeout R0 = n, so nothing is
+// written.
+__device__ __forceinline__ void tile_prefix(const Params &p, uint64_t t, Shared &S, int b)
 {
-    PrefixLoads r;
-    r.pa = r.pb = r.ga = r.gb = 0;
-    r.ok = true;
-    const uint64_t g = t / kGroup;
-    const uint64_t j = g * kGroup + lane;
-    if (j < t) {
-        const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + 2 * j));
-        r.pa = d.x;
-        r.pb = d.y;
+    const uint64_t c = t / kChunk;
+    uint64_t tp = (t & 1u) ? S.ptp[b].y : S.ptp[b].x;
+    uint64_t cn0 = 1u, cn1 = (static_cast<uint64_t>(p.prev) << 32) | 1u;
+    if (c > 0) {
+        cn0 = S.pcn[b].x;
+        cn1 = S.pcn[b].y;
     }
-    if (lane == 0) {
-        const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.gpre + 2 * g));
-        r.ga = d.x;
-        r.gb = d.y;
+    if (!(tp & cn0 & cn1 & 1u)) {   // not yet published when staged
+        if (!(tp & 1u)) tp = wait_word(p.tpre + t, p.status);
+        if (!(cn0 & 1u)) cn0 = wait_word(p.cnext + 2 * (c - 1), p.status);
+        if (!(cn1 & 1u)) cn1 = wait_word(p.cnext + 2 * (c - 1) + 1, p.status);
     }
-    return r;
-}
-
-// Warp 0: stage tile t's prefix descriptors (its group's prefix and the
-// earlier tiles of its group) with cp.async, once its chunk is known scanned.
-__device__ __forceinline__ void stage_prefix(const Params &p, uint64_t t, int lane, Shared &S, int b)
-{
-    const uint64_t g = t / kGroup;
-    const uint64_t j = g * kGroup + lane;
-    if (j < t) cp_async16(&S.pdesc[b][lane], p.tdesc + 2 * j);
-    if (lane == 0) cp_async16(&S.pgpre[b], p.gpre + 2 * g);
-}
-
-__device__ __forceinline__ void fold_staged(uint64_t t, int lane, const Shared &S, int b, unsigned long long &R0,
-                                            uint32_t &S0)
-{
-    const uint64_t j = (t / kGroup) * kGroup + lane;
-    uint32_t c = 0, x = 0;
-    if (j < t) {
-        const ulonglong2 d = S.pdesc[b][lane];
-        c = static_cast<uint32_t>(d.x);
-        x = static_cast<uint32_t>(d.y);
-    }
-    c = __reduce_add_sync(~0u, c);
-    x = __reduce_add_sync(~0u, x);
-    R0 = S.pgpre[b].x + c;
-    S0 = static_cast<uint32_t>(S.pgpre[b].y) + x;
-}
-
-__device__ __forceinline__ void fold(const PrefixLoads &r, int lane, unsigned long long &R0, uint32_t &S0)
-{
-    const uint32_t c = __reduce_add_sync(~0u, static_cast<uint32_t>(r.pa));
-    const uint32_t x = __reduce_add_sync(~0u, static_cast<uint32_t>(r.pb));
-    R0 = __shfl_sync(~0u, r.ga, 0) + c;
-    S0 = static_cast<uint32_t>(__shfl_sync(~0u, r.gb, 0)) + x;
-    (void)lane;
+    const uint32_t rel = static_cast<uint32_t>(tp >> 1) & 0x7FFFFFu;
+    const uint32_t s = word_hi(tp);
+    S.R0 = (tp & cn0 & cn1 & 1u) ? (cn0 >> 1) + rel : p.n;
+    S.S0 = ((tp >> 24) & 1u) ? s : word_hi(cn1) + s;
 }
 
 // ---- decoding
@@ -653,94 +647,10 @@ __device__ __forceinline__ unsigned int count_publish_seg(const Params &p, uint6
     const uint32_t f = __shfl_sync(~0u, ws.f, 31), sm = __shfl_sync(~0u, ws.s, 31);
     unsigned int old = 0;
     if (lane == 0) {
-        *reinterpret_cast<ulonglong2 *>(p.tdesc + 2 * t) =
-            make_ulonglong2(tc, (static_cast<unsigned long long>(f) << 32) | sm);
-        old = atom_add_acq_rel(p.cdone + t / kChunk, 1u);
+        st_relaxed_u64(p.tdesc + t, desc_word(tc, f, sm));
+        old = atomicAdd(p.cdone + t / kChunk, 1u);
     }
     return old;
-}
-
-// Per-tile prefixes of chunk c from its tile descriptors (segmented), by the
-// CTA that completed the chunk's count.
-__device__ void chunk_scan_seg(const Params &p, uint64_t c, SharedS &S)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kPer = static_cast<int>(kChunk / kThreads);   // 8
-    const uint64_t c0 = c * kChunk;
-    const uint64_t c1 = (c0 + kChunk < p.ntiles) ? c0 + kChunk : p.ntiles;
-    uint64_t pc = 0;
-    uint32_t ps = 0;
-    if (c > 0) {
-        cta_wait_flag(p.cready + (c - 1), 1u, p.status);
-        pc = __ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1)));
-        ps = static_cast<uint32_t>(__ldcg(reinterpret_cast<const unsigned long long *>(p.cnext + 2 * (c - 1) + 1)));
-    }
-    const uint64_t tb = c0 + static_cast<uint64_t>(kPer) * tid;
-    uint64_t tcn = 0;
-    Seg ts;
-    ts.f = ts.s = 0u;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        if (tb + i < c1) {
-            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + 2 * (tb + i)));
-            Seg e;
-            e.f = static_cast<uint32_t>(d.y >> 32);
-            e.s = static_cast<uint32_t>(d.y);
-            tcn += d.x;
-            ts = seg_op(ts, e);
-        }
-    }
-    const uint64_t icn = warp_incl_scan64(tcn, lane);
-    const Seg is = warp_seg_incl(ts, lane);
-    if (lane == 31) {
-        S.csc[warp] = icn;
-        S.css[warp] = is.s;
-        S.csf[warp] = is.f;
-    }
-    __syncthreads();
-    uint64_t wc0 = 0, call = 0;
-    Seg w0, wall;
-    w0.f = w0.s = wall.f = wall.s = 0u;
-#pragma unroll
-    for (int q = 0; q < kWarps; ++q) {
-        Seg e;
-        e.f = S.csf[q];
-        e.s = S.css[q];
-        if (q < warp) {
-            wc0 += S.csc[q];
-            w0 = seg_op(w0, e);
-        }
-        call += S.csc[q];
-        wall = seg_op(wall, e);
-    }
-    Seg ex;
-    ex.f = __shfl_up_sync(~0u, is.f, 1);
-    ex.s = __shfl_up_sync(~0u, is.s, 1);
-    if (lane == 0) ex.f = ex.s = 0u;
-    uint64_t rc = pc + wc0 + icn - tcn;
-    uint32_t x = seg_apply(ps, seg_op(w0, ex));
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        if (tb + i < c1) {
-            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tdesc + 2 * (tb + i)));
-            *reinterpret_cast<ulonglong2 *>(p.tpre + 2 * (tb + i)) = make_ulonglong2(rc, x);
-            Seg e;
-            e.f = static_cast<uint32_t>(d.y >> 32);
-            e.s = static_cast<uint32_t>(d.y);
-            rc += d.x;
-            x = seg_apply(x, e);
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        p.cnext[2 * c] = pc + call;
-        p.cnext[2 * c + 1] = seg_apply(ps, wall);
-        if (c1 == p.ntiles && pc + call != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
-        __threadfence();
-        *reinterpret_cast<volatile unsigned int *>(p.cready + c) = 1u;
-    }
-    __syncthreads();
 }
 
 // Decode staging of a tile with list heads (every warp takes the general
@@ -862,7 +772,6 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
     __shared__ Sm S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t total = p.ntiles + p.lead;
-    const uint64_t nchunks = (p.ntiles + kChunk - 1) / kChunk;
     if (tid == 0) {
         S.tinit[0] = atomicAdd(p.ctr, 1ull);
         S.tnext = atomicAdd(p.ctr, 1ull);
@@ -870,30 +779,20 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
     }
     __syncthreads();
     uint64_t k = S.tinit[0];
-    // warp 0 knows chunks [0, ready] are scanned (they are scanned in order);
-    // it reads the next chunk's flag one iteration before using it
-    long long ready = -1, probe = -1;
-    unsigned int rflag = 0;
     auto stage = [&](uint64_t tk, int b) {
         if (tk < p.ntiles) issue_stage(p, tk, tid, S.cbytes[b]);
-        uint32_t pf = 0;
         if (tk >= p.lead && tk < total) {
             const uint64_t t = tk - p.lead;
             issue_stage(p, t, tid, S.dbytes[b]);
-            if (t % kChunk != 0 && static_cast<long long>(t / kChunk) <= ready) {
-                if constexpr (kSeg) {
-                    if (tid == 0) cp_async16(&S.pgpre[b], p.tpre + 2 * t);   // the tile's own prefix
-                } else {
-                    if (warp == 0) stage_prefix(p, t, lane, S, b);
-                }
-                pf = 1;
-            }
+            // the prefix words, probably published by now (checked on use;
+            // 16-byte copies bypass L1, which may hold a stale line)
+            if (tid == 96) cp_async16(&S.ptp[b], p.tpre + (t & ~1ull));
+            if (tid == 128 && t >= kChunk) cp_async16(&S.pcn[b], p.cnext + 2 * (t / kChunk - 1));
         }
         if constexpr (kSeg) {   // the tiles' list-head ranges travel with them
             if (tid == 32 && tk < p.ntiles) cp_async16(S.hrc[b], p.hr + 2 * tk);
             if (tid == 64 && tk >= p.lead && tk < total) cp_async16(S.hrd[b], p.hr + 2 * (tk - p.lead));
         }
-        if (tid == 0) S.pf[b] = pf;
         cp_async_commit();
     };
     stage(k, 0);
@@ -903,24 +802,9 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
         const uint64_t kn = S.tnext;   // staged now, processed next iteration
         unsigned long long knn = 0;
         if (tid == 0) knn = atomicAdd(p.ctr, 1ull);
-        if (warp == 0) {
-            if (probe >= 0 && __shfl_sync(~0u, rflag, 0)) ready = std::max(ready, probe);
-            probe = -1;
-            // probe the chunk after `ready` while the tickets near it
-            if (kn >= p.lead && kn < total && static_cast<long long>((kn - p.lead) / kChunk) >= ready &&
-                static_cast<uint64_t>(ready + 1) < nchunks) {
-                probe = ready + 1;
-                if (lane == 0) rflag = ld_acquire_u32(p.cready + probe);
-            }
-        }
         if (kn < total) stage(kn, b ^ 1);
         // the count this CTA published last iteration completed its chunk
-        if (S.scan_c >= 0) {   // CTA-uniform
-            if constexpr (kSeg)
-                chunk_scan_seg(p, static_cast<uint64_t>(S.scan_c), S);
-            else
-                chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);
-        }
+        if (S.scan_c >= 0) chunk_scan<kSeg>(p, static_cast<uint64_t>(S.scan_c), S);   // CTA-uniform
 
         const bool dec = k >= p.lead;
         const uint64_t t = k - p.lead;
@@ -966,35 +850,7 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
             }
         }
         if (dec) {
-            if (warp == 0) {
-                unsigned long long R0;
-                uint32_t S0;
-                if constexpr (kSeg) {
-                    if (!S.pf[b]) {
-                        if (lane == 0) spin_flag(p.cready + t / kChunk, p.status);
-                        __syncwarp();
-                        ready = std::max<long long>(ready, static_cast<long long>(t / kChunk));
-                        if (lane == 0) {
-                            const ulonglong2 d = __ldcg(reinterpret_cast<const ulonglong2 *>(p.tpre + 2 * t));
-                            S.pgpre[b] = d;
-                        }
-                        __syncwarp();
-                    }
-                    R0 = S.pgpre[b].x;
-                    S0 = static_cast<uint32_t>(S.pgpre[b].y);
-                } else if (S.pf[b]) {
-                    fold_staged(t, lane, S, b, R0, S0);
-                } else {
-                    if (lane == 0) spin_flag(p.cready + t / kChunk, p.status);
-                    __syncwarp();
-                    fold(load_prefix(p, t, lane), lane, R0, S0);
-                    ready = std::max<long long>(ready, static_cast<long long>(t / kChunk));
-                }
-                if (lane == 0) {
-                    S.R0 = R0;
-                    S.S0 = S0;
-                }
-            }
+            if (tid == 0) tile_prefix(p, t, S, b);
             if constexpr (kSeg) {
                 if (kDelta && dheads) {
                     decode_stage_seg<kDelta>(p, t, S, S.dbytes[b], dha, dhe);
@@ -1036,39 +892,40 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
         k = kn;
     }
     __syncthreads();
-    if (S.scan_c >= 0) {
-        if constexpr (kSeg)
-            chunk_scan_seg(p, static_cast<uint64_t>(S.scan_c), S);
-        else
-            chunk_scan<kDelta>(p, static_cast<uint64_t>(S.scan_c), S);
-    }
+    if (S.scan_c >= 0) chunk_scan<kSeg>(p, static_cast<uint64_t>(S.scan_c), S);
     cp_async_wait_all();
 }
 
 // ---- host
 
+// Workspace of one launch: status head, ticket counter, per chunk its
+// totals words and counter, per tile a descriptor and a prefix word, and
+// (batched lists) per tile a head range.  Everything before the head ranges
+// is cleared before each launch.  Prefix words are read in 16-byte pairs; the
+// padding after them covers the pair of an odd last tile.
 struct Layout {
-    uint64_t ntiles, ngroups, nchunks;
-    size_t ctr, cnext, cdone, cready, gagg, gpre, tdesc, total, clear;
+    size_t ctr, cnext, cdone, tdesc, tpre, hr, total, clear, total_b;
 };
 
 Layout layout(uint64_t ntiles)
 {
     Layout L;
-    L.ntiles = ntiles;
-    L.ngroups = (ntiles + kGroup - 1) / kGroup;
-    L.nchunks = (ntiles + kChunk - 1) / kChunk;
+    const uint64_t nchunks = (ntiles + kChunk - 1) / kChunk;
     L.ctr = 256;   // after the status head
     L.cnext = L.ctr + 16;
-    L.cdone = L.cnext + 16 * L.nchunks;
-    L.cready = L.cdone + 4 * L.nchunks;
-    L.gagg = (L.cready + 4 * L.nchunks + 15) / 16 * 16;
-    L.gpre = L.gagg + 16 * L.ngroups;
-    L.tdesc = L.gpre + 16 * L.ngroups;
-    L.total = L.tdesc + 16 * ntiles;
-    L.clear = L.gpre - L.ctr;   // ticket counter, chunk words, group accumulators
+    L.cdone = L.cnext + 16 * nchunks;
+    L.tdesc = (L.cdone + 4 * nchunks + 15) / 16 * 16;
+    L.tpre = (L.tdesc + 8 * ntiles + 15) / 16 * 16;   // 16-byte copies read it
+    L.hr = (L.tpre + 8 * ntiles + 15) / 16 * 16;
+    L.total = L.hr;
+    L.clear = L.hr - L.ctr;
+    L.total_b = L.hr + 16 * ntiles;
     return L;
 }
+
+// Every array read with 16-byte copies starts on a 16-byte boundary (the
+// workspace itself is at least 256-byte aligned).
+bool aligned(const Layout &L) { return ((L.cnext | L.tdesc | L.tpre | L.hr) & 15u) == 0; }
 
 uint64_t tiles_for(uintptr_t addr, size_t nbytes) { return nbytes ? ((addr & 15u) + nbytes + kTile - 1) / kTile : 0; }
 
@@ -1126,6 +983,7 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
     const uintptr_t a = reinterpret_cast<uintptr_t>(in);
     const uint64_t ntiles = sd::tiles_for(a, nbytes);
     const sd::Layout L = sd::layout(ntiles);
+    if (!sd::aligned(L) || (reinterpret_cast<uintptr_t>(ws) & 15u)) return VBYTE_EINVAL;
     sd::Dev di;
     const int rc = sd::dev_info(&di);
     if (rc != VBYTE_OK) return rc;
@@ -1138,11 +996,9 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
     p.ntiles = ntiles;
     p.base = a & ~static_cast<uintptr_t>(15);
     p.tdesc = reinterpret_cast<uint64_t *>(ws + L.tdesc);
-    p.gagg = reinterpret_cast<unsigned long long *>(ws + L.gagg);
-    p.gpre = reinterpret_cast<uint64_t *>(ws + L.gpre);
+    p.tpre = reinterpret_cast<uint64_t *>(ws + L.tpre);
     p.cnext = reinterpret_cast<uint64_t *>(ws + L.cnext);
     p.cdone = reinterpret_cast<unsigned int *>(ws + L.cdone);
-    p.cready = reinterpret_cast<unsigned int *>(ws + L.cready);
     p.ctr = reinterpret_cast<unsigned long long *>(ws + L.ctr);
     p.status = status;
     p.prev = prev;
@@ -1157,34 +1013,10 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
 
 // ---- batched lists
 
-namespace sd {
-// Workspace of a batched decode: status head, ticket counter, per chunk
-// cnext/cdone/cready, per tile a descriptor, a prefix and a head range.
-struct LayoutB {
-    size_t ctr, cnext, cdone, cready, tdesc, tpre, hr, total, clear;
-};
-
-LayoutB layout_b(uint64_t ntiles)
-{
-    LayoutB L;
-    const uint64_t nchunks = (ntiles + kChunk - 1) / kChunk;
-    L.ctr = 256;
-    L.cnext = L.ctr + 16;
-    L.cdone = L.cnext + 16 * nchunks;
-    L.cready = L.cdone + 4 * nchunks;
-    L.tdesc = (L.cready + 4 * nchunks + 15) / 16 * 16;
-    L.tpre = L.tdesc + 16 * ntiles;
-    L.hr = L.tpre + 16 * ntiles;
-    L.total = L.hr + 16 * ntiles;
-    L.clear = L.tdesc - L.ctr;
-    return L;
-}
-}  // namespace sd
-
 size_t workspace_bound(size_t nbytes)
 {
     const uint64_t ntiles = sd::tiles_for(15, nbytes);   // the worst alignment
-    return std::max(sd::layout(ntiles).total, sd::layout_b(ntiles).total);
+    return sd::layout(ntiles).total_b;
 }
 
 int load_kernels()
@@ -1201,7 +1033,7 @@ int sbatched_max_ctas(bool delta)
 
 size_t sbatched_workspace_bytes(const BatchArgs &a)
 {
-    return sd::layout_b(sd::tiles_for(reinterpret_cast<uintptr_t>(a.in), a.nbytes)).total;
+    return sd::layout(sd::tiles_for(reinterpret_cast<uintptr_t>(a.in), a.nbytes)).total_b;
 }
 
 int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cudaStream_t s)
@@ -1211,7 +1043,8 @@ int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cuda
     if (rc != VBYTE_OK) return rc;
     const uintptr_t addr = reinterpret_cast<uintptr_t>(a.in);
     const uint64_t ntiles = sd::tiles_for(addr, a.nbytes);
-    const sd::LayoutB Y = sd::layout_b(ntiles);
+    const sd::Layout Y = sd::layout(ntiles);
+    if (!sd::aligned(Y) || (reinterpret_cast<uintptr_t>(ws) & 15u)) return VBYTE_EINVAL;
     uint32_t *status = reinterpret_cast<uint32_t *>(ws);
     uint64_t *hr = reinterpret_cast<uint64_t *>(ws + Y.hr);
     rc = enqueue_head_ranges(a.in, a.nbytes, a.bo, a.vo, a.L, a.n, hr, status, di.sms, s);
@@ -1226,9 +1059,9 @@ int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cuda
     p.ntiles = ntiles;
     p.base = addr & ~static_cast<uintptr_t>(15);
     p.tdesc = reinterpret_cast<uint64_t *>(ws + Y.tdesc);
+    p.tpre = reinterpret_cast<uint64_t *>(ws + Y.tpre);
     p.cnext = reinterpret_cast<uint64_t *>(ws + Y.cnext);
     p.cdone = reinterpret_cast<unsigned int *>(ws + Y.cdone);
-    p.cready = reinterpret_cast<unsigned int *>(ws + Y.cready);
     p.ctr = reinterpret_cast<unsigned long long *>(ws + Y.ctr);
     p.status = status;
     p.prev = 0u;
@@ -1238,7 +1071,6 @@ int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cuda
     p.prevs = a.prevs;
     p.L = a.L;
     p.hr = hr;
-    p.tpre = reinterpret_cast<uint64_t *>(ws + Y.tpre);
     const int occ = di.occ_seg[a.delta];
     const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * per_sm);
