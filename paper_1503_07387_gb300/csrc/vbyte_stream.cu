@@ -61,10 +61,10 @@ constexpr int kThreads = kWarps * kLanes;
 constexpr int kTile = kThreads * kBPT;          // 4 KiB per tile
 constexpr int kWarpBytes = kLanes * kBPT;       // 512 bytes per warp
 constexpr uint64_t kChunk = 2048;               // tiles per chunk (8 MiB)
-constexpr uint64_t kSlack = 2560;               // tickets between a chunk's last count ticket and its first decode
+constexpr uint64_t kSlack = 3584;               // tickets between a chunk's last count ticket and its first decode
 constexpr int kByteBuf = kHalo + kTile + 16;
 constexpr int kWarpValBuf = kWarpBytes + 16;    // staged values of one warp (528)
-constexpr int kStages = 2;                      // tickets in flight per CTA (processed + staged)
+constexpr int kStages = 2;                      // tickets in flight per CTA (processed + staged ahead)
 static_assert(kChunk % kThreads == 0, "chunk scan: whole tiles per thread");
 static_assert(kChunk * kTile < (1ull << 24), "relative tile prefixes fit 23 bits");
 
@@ -118,15 +118,15 @@ struct Shared {
     alignas(16) ulonglong2 pcn[kStages];           // prefetched: totals of the chunk before the decode tile's
     alignas(16) ulonglong2 ptp[kStages];           // prefetched: the decode tile's prefix word (and its pair's)
     unsigned long long tnext;                      // the ticket to stage next
-    unsigned long long tinit[2];                   // the first two tickets
+    unsigned long long tinit[kStages];             // the first tickets
     uint32_t csc[kWarps], css[kWarps], csf[kWarps];   // chunk scan partials
     long long scan_c;                              // chunk this CTA completed (scans it), or -1
 };
 // Batched lists: the list heads of the count and the decode tile, per-warp
 // segment flags, and the segmented chunk scan's partials.
 struct SharedS : Shared {
-    alignas(16) unsigned long long hrc[2][2];   // head ranges of the staged count tiles (cp.async targets)
-    alignas(16) unsigned long long hrd[2][2];   // ... of the staged decode tiles
+    alignas(16) unsigned long long hrc[kStages][2];   // head ranges of the staged count tiles (cp.async targets)
+    alignas(16) unsigned long long hrd[kStages][2];   // ... of the staged decode tiles
     HeadTab hc, hd;                             // heads of the count and the decode tile
     uint32_t cflag[kWarps];                     // count: a list head was crossed in this warp
     uint32_t dflag[kWarps];                     // decode: the same
@@ -140,7 +140,8 @@ static_assert((kWarpValBuf * 4) % 16 == 0, "per-warp value buffers keep 16-byte 
 static_assert(offsetof(Shared, pcn) % 16 == 0 && offsetof(Shared, ptp) % 16 == 0, "prefix buffers alignment");
 
 // Stage tile t (its 16-byte slices, the 16 bytes before it, zeros outside
-// the stream) into `bytes`; the caller commits, waits and syncs.
+// the stream) into `bytes`; the caller commits, waits and syncs.  The 16 bytes
+// after the tile are zeroed once, at the kernel's start.
 __device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid, uint8_t *bytes)
 {
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
@@ -151,7 +152,6 @@ __device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid
     if (t > 0 && tstart + kTile <= hi && tstart >= lo + 16) {   // interior tile: no checks
         cp_async16(dst, reinterpret_cast<const void *>(va));
         if (tid == 0) cp_async16(bytes, reinterpret_cast<const void *>(tstart - 16));
-        if (tid == kThreads - 1) *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
         return;
     }
     if (va >= lo && va + kBPT <= hi) {
@@ -172,7 +172,6 @@ __device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid
         else
             *reinterpret_cast<uint4 *>(bytes) = make_uint4(0u, 0u, 0u, 0u);
     }
-    if (tid == kThreads - 1) *reinterpret_cast<uint4 *>(bytes + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // ---- counting
@@ -474,12 +473,9 @@ __device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
     const long long n = static_cast<long long>(p.n);
-    uint32_t wbase = 0, wsb = 0;
-#pragma unroll
-    for (int q = 0; q < kWarps; ++q) {
-        wbase += (q < warp) ? S.dcnt[q] : 0u;
-        if (kDelta) wsb += (q < warp) ? S.dsum[q] : 0u;
-    }
+    // the warps before this one: their value counts and sums
+    const uint32_t wbase = __reduce_add_sync(~0u, lane < warp ? S.dcnt[lane] : 0u);
+    const uint32_t wsb = kDelta ? __reduce_add_sync(~0u, lane < warp ? S.dsum[lane] : 0u) : 0u;
     const uint32_t wc = S.dcnt[warp];
     const long long G0 = static_cast<long long>(S.R0 + wbase);   // global rank of warp rank 0
     const uint32_t add = kDelta ? S.S0 + wsb : 0u;
@@ -772,13 +768,20 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
     __shared__ Sm S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t total = p.ntiles + p.lead;
+    if (tid < 2 * kStages) {   // the zeros after each staging buffer
+        uint8_t *buf = (tid < kStages) ? S.cbytes[tid] : S.dbytes[tid - kStages];
+        *reinterpret_cast<uint4 *>(buf + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid == 0) {
-        S.tinit[0] = atomicAdd(p.ctr, 1ull);
+        for (int j = 0; j < kStages - 1; ++j) S.tinit[j] = atomicAdd(p.ctr, 1ull);
         S.tnext = atomicAdd(p.ctr, 1ull);
         S.scan_c = -1;
     }
     __syncthreads();
-    uint64_t k = S.tinit[0];
+    // tickets of the buffers b, b + 1, ... (mod kStages): processed now, staged
+    uint64_t q[kStages - 1];
+#pragma unroll
+    for (int j = 0; j < kStages - 1; ++j) q[j] = S.tinit[j];
     auto stage = [&](uint64_t tk, int b) {
         if (tk < p.ntiles) issue_stage(p, tk, tid, S.cbytes[b]);
         if (tk >= p.lead && tk < total) {
@@ -795,14 +798,16 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
         }
         cp_async_commit();
     };
-    stage(k, 0);
-    for (int b = 0; k < total; b ^= 1) {
-        cp_async_wait_all();   // ticket k's group is complete
-        __syncthreads();       // ... for every thread; the previous iteration is over
-        const uint64_t kn = S.tnext;   // staged now, processed next iteration
+#pragma unroll
+    for (int j = 0; j < kStages - 1; ++j) stage(q[j], j);
+    for (int b = 0; q[0] < total; b = (b == kStages - 1) ? 0 : b + 1) {
+        const uint64_t k = q[0];
+        cp_async_wait_prior<kStages - 2>();   // ticket k's group is complete
+        __syncthreads();                      // ... for every thread; the previous iteration is over
+        const uint64_t kn = S.tnext;          // staged now, processed kStages - 1 iterations later
         unsigned long long knn = 0;
         if (tid == 0) knn = atomicAdd(p.ctr, 1ull);
-        if (kn < total) stage(kn, b ^ 1);
+        stage(kn, (b == 0) ? kStages - 1 : b - 1);
         // the count this CTA published last iteration completed its chunk
         if (S.scan_c >= 0) chunk_scan<kSeg>(p, static_cast<uint64_t>(S.scan_c), S);   // CTA-uniform
 
@@ -889,7 +894,9 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
         if (warp == kWarps - 1 && lane == 0)
             S.scan_c = (pend_c >= 0 && static_cast<uint64_t>(pend_old) + 1 == chunk_tiles(p, pend_c)) ? pend_c : -1;
         if (tid == 0) S.tnext = knn;
-        k = kn;
+#pragma unroll
+        for (int j = 0; j < kStages - 2; ++j) q[j] = q[j + 1];
+        q[kStages - 2] = kn;
     }
     __syncthreads();
     if (S.scan_c >= 0) chunk_scan<kSeg>(p, static_cast<uint64_t>(S.scan_c), S);
