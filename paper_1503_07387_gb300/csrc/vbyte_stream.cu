@@ -360,10 +360,17 @@ __device__ __forceinline__ void tile_prefix(const Params &p, uint64_t t, Shared 
 // Before the middle barrier each warp stages its values in its own buffer:
 // warp rank r at vals[4 + r], running sums (delta) relative to the warp's
 // first value.  After it, one coalesced copy-out adds the warp's base and
-// realigns to 16-byte output quads.
+// realigns to 16-byte output quads.  A warp of one-byte integers only may
+// instead keep its values in registers until the copy-out (kKeep).
 
-template <bool kDelta>
-__device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes)
+// A warp of one-byte integers only may skip the buffer (kKeep): it writes
+// its values at the copy-out straight from the staged bytes.
+struct RegA {
+    bool on;   // warp-uniform: nothing is in the value buffer
+};
+
+template <bool kDelta, bool kKeep>
+__device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes, RegA &ra)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
@@ -375,7 +382,12 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared
     const bool mineA = interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u);
     uint32_t *vals = S.vals[warp];
     uint32_t wc, ws = 0;
-    if (__all_sync(~0u, mineA)) {
+    if (kKeep && __all_sync(~0u, mineA)) {
+        // one-byte integers only: written from the bytes at the copy-out
+        if (kDelta) ws = __reduce_add_sync(~0u, byte_sum4(w0));
+        ra.on = true;
+        wc = kWarpBytes;
+    } else if (__all_sync(~0u, mineA)) {
         // one-byte integers only: lane l holds warp ranks 16l .. 16l+15
         uint4 q[4] = {bytes_as_values(w0.x), bytes_as_values(w0.y), bytes_as_values(w0.z),
                       bytes_as_values(w0.w)};
@@ -397,6 +409,7 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared
         for (int j = 0; j < 4; ++j) d4[j] = q[j];
         wc = kWarpBytes;
     } else {
+        ra.on = false;
         const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
         const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
         const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
@@ -466,9 +479,130 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared
     }
 }
 
+// Output quad q of a warp holds its ranks 4q - SH .. 4q - SH + 3, staged at
+// vals[4q + 4 - SH ..]: the tail of U = vals[4q..] and the head of
+// V = vals[4q+4..].
+template <int SH>
+__device__ __forceinline__ uint4 staged_quad(const uint32_t *vals, int q)
+{
+    const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
+    if (SH == 0) return V;
+    const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
+    if (SH == 1) return make_uint4(U.w, V.x, V.y, V.z);
+    if (SH == 2) return make_uint4(U.z, U.w, V.x, V.y);
+    return make_uint4(U.y, U.z, U.w, V.x);
+}
+
+__device__ __forceinline__ uint4 staged_quad(const uint32_t *vals, int q, int sh)
+{
+    switch (sh) {
+    case 0: return staged_quad<0>(vals, q);
+    case 1: return staged_quad<1>(vals, q);
+    case 2: return staged_quad<2>(vals, q);
+    default: return staged_quad<3>(vals, q);
+    }
+}
+
+// Whole quads q0, q0 + 32, ... below qb to oq + 4q, `add` added to the ranks
+// below hf (kHf; all ranks otherwise).
+template <int SH, bool kHf>
+__device__ __forceinline__ void store_quads(uint32_t *oq, const uint32_t *vals, int q0, int qb, uint32_t add, int hf)
+{
+#pragma unroll 2
+    for (int q = q0; q < qb; q += kLanes) {
+        uint4 e = staged_quad<SH>(vals, q);
+        const int r0 = 4 * q - SH;
+        e.x += (!kHf || r0 < hf) ? add : 0u;
+        e.y += (!kHf || r0 + 1 < hf) ? add : 0u;
+        e.z += (!kHf || r0 + 2 < hf) ? add : 0u;
+        e.w += (!kHf || r0 + 3 < hf) ? add : 0u;
+        st_quad(oq + 4 * q, e);
+    }
+}
+
+template <bool kHf>
+__device__ __forceinline__ void store_quads(uint32_t *oq, const uint32_t *vals, int q0, int qb, uint32_t add, int hf,
+                                            int sh)
+{
+    switch (sh) {   // warp-uniform: one loop per alignment
+    case 0: store_quads<0, kHf>(oq, vals, q0, qb, add, hf); break;
+    case 1: store_quads<1, kHf>(oq, vals, q0, qb, add, hf); break;
+    case 2: store_quads<2, kHf>(oq, vals, q0, qb, add, hf); break;
+    default: store_quads<3, kHf>(oq, vals, q0, qb, add, hf); break;
+    }
+}
+
+// The copy-out of a one-byte warp from its staged bytes (wb: its first byte;
+// the 4 bytes before and after it are staged too).  Output quad Q = 32m + l,
+// taken by lane l, holds ranks 4Q - SH .. 4Q - SH + 3, whose bytes start at
+// wb + 4Q - SH.  In delta mode the sums before each quad come from two
+// packed warp scans (a quad's sum is at most 4 * 127, so 16 bits hold a
+// warp's prefix).  Quad 0 skips the SH ranks before the warp; lane 31 writes
+// the last SH ranks after quad 127.
+template <int SH, bool kDelta>
+__device__ __forceinline__ void emit_bytes_a(uint32_t *oq, const uint8_t *wb, uint32_t add, int lane)
+{
+    const uint32_t *ww = reinterpret_cast<const uint32_t *>(wb);
+    uint32_t x[4], qs[4], P[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int k = 32 * m + lane;
+        x[m] = SH == 0 ? ww[k] : __funnelshift_r(ww[k - 1], ww[k], 8 * (4 - SH));
+    }
+    if (SH > 0 && lane == 0) x[0] &= 0xFFFFFFFFu << (8 * SH);   // ranks before the warp
+    if (kDelta) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) qs[m] = __dp4a(x[m], 0x01010101u, 0u);
+        const uint32_t o01 = qs[0] | (qs[1] << 16), o23 = qs[2] | (qs[3] << 16);
+        const uint32_t s01 = warp_incl_scan(o01, lane), s23 = warp_incl_scan(o23, lane);
+        const uint32_t t01 = __shfl_sync(~0u, s01, 31), t23 = __shfl_sync(~0u, s23, 31);
+        const uint32_t e01 = s01 - o01, e23 = s23 - o23;
+        P[0] = e01 & 0xFFFFu;
+        P[1] = (t01 & 0xFFFFu) + (e01 >> 16);
+        P[2] = (t01 & 0xFFFFu) + (t01 >> 16) + (e23 & 0xFFFFu);
+        P[3] = (t01 & 0xFFFFu) + (t01 >> 16) + (t23 & 0xFFFFu) + (e23 >> 16);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        uint32_t e[4];
+        uint32_t run = kDelta ? add + P[m] : add;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t b = (x[m] >> (8 * j)) & 0xFFu;
+            if (kDelta) {
+                run += b;
+                e[j] = run;
+            } else {
+                e[j] = b + add;
+            }
+        }
+        uint32_t *const o = oq + 4 * (32 * m + lane);
+        if (SH == 0 || m > 0 || lane > 0) {
+            st_quad(o, make_uint4(e[0], e[1], e[2], e[3]));
+        } else {
+#pragma unroll
+            for (int j = SH; j < 4; ++j) o[j] = e[j];
+        }
+    }
+    if (SH > 0 && lane == kLanes - 1) {   // quad 128: ranks 512 - SH .. 511
+        const uint32_t xt = __funnelshift_r(ww[127], ww[128], 8 * (4 - SH));
+        uint32_t run = kDelta ? add + P[3] + qs[3] : add;
+#pragma unroll
+        for (int j = 0; j < SH; ++j) {
+            const uint32_t b = (xt >> (8 * j)) & 0xFFu;
+            if (kDelta) {
+                run += b;
+                oq[4 * 128 + j] = run;
+            } else {
+                oq[4 * 128 + j] = b + add;
+            }
+        }
+    }
+}
+
 // After the middle barrier: this warp's values to the output, coalesced.
 template <bool kDelta>
-__device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
+__device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const RegA &ra, const uint8_t *bytes)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
@@ -480,7 +614,38 @@ __device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
     const long long G0 = static_cast<long long>(S.R0 + wbase);   // global rank of warp rank 0
     const uint32_t add = kDelta ? S.S0 + wsb : 0u;
     const int sh = static_cast<int>((out_word + static_cast<uint32_t>(G0)) & 3u);
-    const uint32_t *vals = S.vals[warp];
+    uint32_t *vals = S.vals[warp];
+    uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
+    if (ra.on) {   // warp-uniform
+        const uint8_t *wb = bytes + kHalo + warp * kWarpBytes;
+        if (G0 + kWarpBytes <= n) {
+            switch (sh) {
+            case 0: emit_bytes_a<0, kDelta>(oq, wb, add, lane); break;
+            case 1: emit_bytes_a<1, kDelta>(oq, wb, add, lane); break;
+            case 2: emit_bytes_a<2, kDelta>(oq, wb, add, lane); break;
+            default: emit_bytes_a<3, kDelta>(oq, wb, add, lane); break;
+            }
+            return;
+        }
+        // near the end of the output: through the buffer, with the checks
+        const uint4 w = *reinterpret_cast<const uint4 *>(wb + lane * kBPT);
+        uint4 q[4] = {bytes_as_values(w.x), bytes_as_values(w.y), bytes_as_values(w.z), bytes_as_values(w.w)};
+        if (kDelta) {
+            const uint32_t mine = byte_sum4(w);
+            uint32_t run = warp_incl_scan(mine, lane) - mine;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                run += q[j].x; q[j].x = run;
+                run += q[j].y; q[j].y = run;
+                run += q[j].z; q[j].z = run;
+                run += q[j].w; q[j].w = run;
+            }
+        }
+        uint4 *d4 = reinterpret_cast<uint4 *>(vals + 4 + 16 * lane);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d4[j] = q[j];
+        __syncwarp();
+    }
     // Output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
     // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of
     // V = vals[4q+4..].  Quads [qa, qb) are whole (inside this warp's ranks
@@ -490,27 +655,14 @@ __device__ __forceinline__ void decode_emit(const Params &p, const Shared &S)
     int qb = (static_cast<int>(wc) + sh) >> 2;
     if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
     const int qa = sh ? 1 : 0;
-    uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
-    auto quad = [&](int q) -> uint4 {
-        const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
-        const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
-        uint4 e;
-        switch (sh) {
-        case 0: e = V; break;
-        case 1: e = make_uint4(U.w, V.x, V.y, V.z); break;
-        case 2: e = make_uint4(U.z, U.w, V.x, V.y); break;
-        default: e = make_uint4(U.y, U.z, U.w, V.x); break;
-        }
+    store_quads<false>(oq, vals, qa + lane, qb, add, 0, sh);
+    // edge quads: the first (partly before this warp's ranks) and those from qb on
+    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
+        uint4 e = staged_quad(vals, q, sh);
         e.x += add;
         e.y += add;
         e.z += add;
         e.w += add;
-        return e;
-    };
-    for (int q = qa + lane; q < qb; q += kLanes) st_quad(oq + 4 * q, quad(q));
-    // edge quads: the first (partly before this warp's ranks) and those from qb on
-    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
-        const uint4 e = quad(q);
         const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
         const int r0 = 4 * q - sh;
 #pragma unroll
@@ -557,29 +709,16 @@ __device__ __forceinline__ void decode_emit_seg(const Params &p, const SharedS &
     if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
     const int qa = sh ? 1 : 0;
     uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
-    auto quad = [&](int q) -> uint4 {
-        const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
-        const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
-        uint4 e;
-        switch (sh) {
-        case 0: e = V; break;
-        case 1: e = make_uint4(U.w, V.x, V.y, V.z); break;
-        case 2: e = make_uint4(U.z, U.w, V.x, V.y); break;
-        default: e = make_uint4(U.y, U.z, U.w, V.x); break;
-        }
+    store_quads<true>(oq, vals, qa + lane, qb, add, hf, sh);
+    // edge quads: the first (partly before this warp's ranks) and those from qb on
+    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
+        uint4 e = staged_quad(vals, q, sh);
         const int r0 = 4 * q - sh;
         e.x += (r0 < hf) ? add : 0u;
         e.y += (r0 + 1 < hf) ? add : 0u;
         e.z += (r0 + 2 < hf) ? add : 0u;
         e.w += (r0 + 3 < hf) ? add : 0u;
-        return e;
-    };
-    for (int q = qa + lane; q < qb; q += kLanes) st_quad(oq + 4 * q, quad(q));
-    // edge quads: the first (partly before this warp's ranks) and those from qb on
-    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
-        const uint4 e = quad(q);
         const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
-        const int r0 = 4 * q - sh;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (r0 + j >= 0 && r0 + j < static_cast<int>(wc) && G0 + r0 + j < n) oq[4 * q + j] = e4[j];
@@ -812,6 +951,8 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
         if (S.scan_c >= 0) chunk_scan<kSeg>(p, static_cast<uint64_t>(S.scan_c), S);   // CTA-uniform
 
         const bool dec = k >= p.lead;
+        RegA ra;
+        ra.on = false;
         const uint64_t t = k - p.lead;
         // batched lists: the heads of the count tile (delta only) and of the decode tile
         bool cheads = false, dheads = false;
@@ -860,14 +1001,14 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
                 if (kDelta && dheads) {
                     decode_stage_seg<kDelta>(p, t, S, S.dbytes[b], dha, dhe);
                 } else {
-                    decode_stage<kDelta>(p, t, S, S.dbytes[b]);
+                    decode_stage<kDelta, false>(p, t, S, S.dbytes[b], ra);
                     if (lane == 0) {
                         S.dflag[warp] = 0u;
                         S.dhf[warp] = 0xFFFFFFFFu;
                     }
                 }
             } else {
-                decode_stage<kDelta>(p, t, S, S.dbytes[b]);
+                decode_stage<kDelta, true>(p, t, S, S.dbytes[b], ra);
             }
         }
         __syncthreads();   // count partials, decode partials and the prefix are in place
@@ -885,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
                 decode_emit_seg<kDelta>(p, S);
                 if (dheads) check_heads(p, t, S, S.dbytes[b], dha, dhe, S.R0);
             } else {
-                decode_emit<kDelta>(p, S);
+                decode_emit<kDelta>(p, S, ra, S.dbytes[b]);
             }
         }
         // did this count complete its chunk?  (read after the emission, so the
