@@ -66,6 +66,7 @@ constexpr int kByteBuf = kHalo + kTile + 16;
 constexpr int kWarpValBuf = kWarpBytes + 16;    // staged values of one warp (528)
 constexpr int kStages = 2;                      // tickets in flight per CTA (processed + staged ahead)
 static_assert(kChunk % kThreads == 0, "chunk scan: whole tiles per thread");
+static_assert(kTile == 1 << 12, "tile addresses are t << 12");
 static_assert(kChunk * kTile < (1ull << 24), "relative tile prefixes fit 23 bits");
 
 // Published words (bit 0 = written):
@@ -91,11 +92,12 @@ struct Params {
     uint64_t n;
     uint64_t ntiles;
     uintptr_t base;            // 16-byte aligned address of tile 0
+    uint32_t t_in_lo, t_in_hi; // tiles [t_in_lo, t_in_hi) lie wholly inside the stream
     uint64_t *tdesc;           // per tile: descriptor word
     uint64_t *tpre;            // per tile: prefix word
     uint64_t *cnext;           // per chunk: totals words (values, running x after it)
     unsigned int *cdone;       // per chunk: tiles counted
-    unsigned long long *ctr;   // tickets
+    unsigned int *ctr;         // tickets
     uint32_t *status;
     uint32_t prev;             // x_0
     uint64_t lead;             // tickets [0, lead) only count
@@ -117,8 +119,8 @@ struct Shared {
     uint32_t S0;                                   // decode: running x before the tile
     alignas(16) ulonglong2 pcn[kStages];           // prefetched: totals of the chunk before the decode tile's
     alignas(16) ulonglong2 ptp[kStages];           // prefetched: the decode tile's prefix word (and its pair's)
-    unsigned long long tnext;                      // the ticket to stage next
-    unsigned long long tinit[kStages];             // the first tickets
+    uint32_t tnext;                                // the ticket to stage next
+    uint32_t tinit[kStages];                       // the first tickets
     uint32_t csc[kWarps], css[kWarps], csf[kWarps];   // chunk scan partials
     long long scan_c;                              // chunk this CTA completed (scans it), or -1
 };
@@ -139,21 +141,23 @@ static_assert(offsetof(Shared, dbytes) % 16 == 0 && offsetof(Shared, vals) % 16 
 static_assert((kWarpValBuf * 4) % 16 == 0, "per-warp value buffers keep 16-byte alignment");
 static_assert(offsetof(Shared, pcn) % 16 == 0 && offsetof(Shared, ptp) % 16 == 0, "prefix buffers alignment");
 
+__device__ __forceinline__ bool inside(const Params &p, uint32_t t) { return t >= p.t_in_lo && t < p.t_in_hi; }
+
 // Stage tile t (its 16-byte slices, the 16 bytes before it, zeros outside
 // the stream) into `bytes`; the caller commits, waits and syncs.  The 16 bytes
 // after the tile are zeroed once, at the kernel's start.
-__device__ __forceinline__ void issue_stage(const Params &p, uint64_t t, int tid, uint8_t *bytes)
+__device__ __forceinline__ void issue_stage(const Params &p, uint32_t t, int tid, uint8_t *bytes)
 {
-    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
-    const uintptr_t hi = lo + p.nbytes;
-    const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
+    const uintptr_t tstart = p.base + (static_cast<uintptr_t>(t) << 12);
     const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
     uint8_t *dst = bytes + kHalo + tid * kBPT;
-    if (t > 0 && tstart + kTile <= hi && tstart >= lo + 16) {   // interior tile: no checks
+    if (t > 0 && t < p.t_in_hi) {   // interior tile (its 16 bytes before too): no checks
         cp_async16(dst, reinterpret_cast<const void *>(va));
         if (tid == 0) cp_async16(bytes, reinterpret_cast<const void *>(tstart - 16));
         return;
     }
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
     if (va >= lo && va + kBPT <= hi) {
         cp_async16(dst, reinterpret_cast<const void *>(va));
     } else {
@@ -183,7 +187,7 @@ __device__ __forceinline__ void count_partials(const Params &p, uint64_t t, Shar
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
-    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const bool interior = inside(p, static_cast<uint32_t>(t));
     const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
     const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
     uint32_t cnt, vsum = 0;
@@ -376,7 +380,7 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
-    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const bool interior = inside(p, static_cast<uint32_t>(t));
     const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
     const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
     const bool mineA = interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u);
@@ -738,7 +742,7 @@ __device__ __forceinline__ void count_partials_seg(const Params &p, uint64_t t, 
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
-    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const bool interior = inside(p, static_cast<uint32_t>(t));
     const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
     const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
     const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
@@ -799,7 +803,7 @@ __device__ __forceinline__ void decode_stage_seg(const Params &p, uint64_t t, Sh
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
-    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const bool interior = inside(p, static_cast<uint32_t>(t));
     const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
     const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
     const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
@@ -864,7 +868,7 @@ __device__ __forceinline__ void check_heads(const Params &p, uint64_t t, SharedS
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
     const uintptr_t tstart = p.base + static_cast<uintptr_t>(t) * kTile;
-    const bool interior = tstart >= lo && tstart + kTile <= hi;
+    const bool interior = inside(p, static_cast<uint32_t>(t));
     const uintptr_t va = tstart + static_cast<uintptr_t>(tid) * kBPT;
     const uint32_t *const sw = reinterpret_cast<const uint32_t *>(bytes);
     const SliceMasks m = slice_masks(bytes, tid, interior, va, lo, hi);
@@ -906,59 +910,61 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
     using Sm = typename std::conditional<kSeg, SharedS, Shared>::type;
     __shared__ Sm S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t total = p.ntiles + p.lead;
+    // tickets and tile indices fit 32 bits (checked by the host)
+    const uint32_t ntiles = static_cast<uint32_t>(p.ntiles), lead = static_cast<uint32_t>(p.lead);
+    const uint32_t total = ntiles + lead;
     if (tid < 2 * kStages) {   // the zeros after each staging buffer
         uint8_t *buf = (tid < kStages) ? S.cbytes[tid] : S.dbytes[tid - kStages];
         *reinterpret_cast<uint4 *>(buf + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (tid == 0) {
-        for (int j = 0; j < kStages - 1; ++j) S.tinit[j] = atomicAdd(p.ctr, 1ull);
-        S.tnext = atomicAdd(p.ctr, 1ull);
+        for (int j = 0; j < kStages - 1; ++j) S.tinit[j] = atomicAdd(p.ctr, 1u);
+        S.tnext = atomicAdd(p.ctr, 1u);
         S.scan_c = -1;
     }
     __syncthreads();
     // tickets of the buffers b, b + 1, ... (mod kStages): processed now, staged
-    uint64_t q[kStages - 1];
+    uint32_t q[kStages - 1];
 #pragma unroll
     for (int j = 0; j < kStages - 1; ++j) q[j] = S.tinit[j];
-    auto stage = [&](uint64_t tk, int b) {
-        if (tk < p.ntiles) issue_stage(p, tk, tid, S.cbytes[b]);
-        if (tk >= p.lead && tk < total) {
-            const uint64_t t = tk - p.lead;
+    auto stage = [&](uint32_t tk, int b) {
+        if (tk < ntiles) issue_stage(p, tk, tid, S.cbytes[b]);
+        if (tk >= lead && tk < total) {
+            const uint32_t t = tk - lead;
             issue_stage(p, t, tid, S.dbytes[b]);
             // the prefix words, probably published by now (checked on use;
             // 16-byte copies bypass L1, which may hold a stale line)
-            if (tid == 96) cp_async16(&S.ptp[b], p.tpre + (t & ~1ull));
+            if (tid == 96) cp_async16(&S.ptp[b], p.tpre + (t & ~1u));
             if (tid == 128 && t >= kChunk) cp_async16(&S.pcn[b], p.cnext + 2 * (t / kChunk - 1));
         }
         if constexpr (kSeg) {   // the tiles' list-head ranges travel with them
-            if (tid == 32 && tk < p.ntiles) cp_async16(S.hrc[b], p.hr + 2 * tk);
-            if (tid == 64 && tk >= p.lead && tk < total) cp_async16(S.hrd[b], p.hr + 2 * (tk - p.lead));
+            if (tid == 32 && tk < ntiles) cp_async16(S.hrc[b], p.hr + 2 * static_cast<uint64_t>(tk));
+            if (tid == 64 && tk >= lead && tk < total) cp_async16(S.hrd[b], p.hr + 2 * static_cast<uint64_t>(tk - lead));
         }
         cp_async_commit();
     };
 #pragma unroll
     for (int j = 0; j < kStages - 1; ++j) stage(q[j], j);
     for (int b = 0; q[0] < total; b = (b == kStages - 1) ? 0 : b + 1) {
-        const uint64_t k = q[0];
+        const uint32_t k = q[0];
         cp_async_wait_prior<kStages - 2>();   // ticket k's group is complete
         __syncthreads();                      // ... for every thread; the previous iteration is over
-        const uint64_t kn = S.tnext;          // staged now, processed kStages - 1 iterations later
-        unsigned long long knn = 0;
-        if (tid == 0) knn = atomicAdd(p.ctr, 1ull);
+        const uint32_t kn = S.tnext;          // staged now, processed kStages - 1 iterations later
+        uint32_t knn = 0;
+        if (tid == 0) knn = atomicAdd(p.ctr, 1u);
         stage(kn, (b == 0) ? kStages - 1 : b - 1);
         // the count this CTA published last iteration completed its chunk
         if (S.scan_c >= 0) chunk_scan<kSeg>(p, static_cast<uint64_t>(S.scan_c), S);   // CTA-uniform
 
-        const bool dec = k >= p.lead;
+        const bool dec = k >= lead;
         RegA ra;
         ra.on = false;
-        const uint64_t t = k - p.lead;
+        const uint32_t t = k - lead;
         // batched lists: the heads of the count tile (delta only) and of the decode tile
         bool cheads = false, dheads = false;
         uint64_t cha = 0, che = 0, dha = 0, dhe = 0;
         if constexpr (kSeg) {
-            if (kDelta && k < p.ntiles) {
+            if (kDelta && k < ntiles) {
                 cha = S.hrc[b][0];
                 che = S.hrc[b][1];
                 cheads = cha < che;
@@ -983,7 +989,7 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
                 __syncthreads();
             }
         }
-        if (k < p.ntiles) {
+        if (k < ntiles) {
             if constexpr (kSeg) {
                 if (cheads)
                     count_partials_seg(p, k, S, S.cbytes[b], cha, che);
@@ -1014,7 +1020,7 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
         __syncthreads();   // count partials, decode partials and the prefix are in place
         long long pend_c = -1;
         unsigned int pend_old = 0;
-        if (k < p.ntiles && warp == kWarps - 1) {
+        if (k < ntiles && warp == kWarps - 1) {
             if constexpr (kSeg)
                 pend_old = count_publish_seg<kDelta>(p, k, S, lane);
             else
@@ -1069,6 +1075,20 @@ Layout layout(uint64_t ntiles)
     L.clear = L.hr - L.ctr;
     L.total_b = L.hr + 16 * ntiles;
     return L;
+}
+
+// Tiles [t_in_lo, t_in_hi) lie wholly inside [in, in + nbytes).
+void inside_range(Params &p, uintptr_t in, size_t nbytes)
+{
+    p.t_in_lo = p.base == in ? 0u : 1u;
+    p.t_in_hi = static_cast<uint32_t>((in + nbytes - p.base) / kTile);
+}
+
+// Tickets (tiles plus lead, plus those the CTAs draw past the end) are
+// counted in 32 bits.
+bool tickets_fit(uint64_t ntiles, uint64_t lead, uint64_t grid)
+{
+    return ntiles + lead + grid * (kStages + 1) < (1ull << 32);
 }
 
 // Every array read with 16-byte copies starts on a 16-byte boundary (the
@@ -1143,15 +1163,17 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
     p.n = n;
     p.ntiles = ntiles;
     p.base = a & ~static_cast<uintptr_t>(15);
+    sd::inside_range(p, a, nbytes);
     p.tdesc = reinterpret_cast<uint64_t *>(ws + L.tdesc);
     p.tpre = reinterpret_cast<uint64_t *>(ws + L.tpre);
     p.cnext = reinterpret_cast<uint64_t *>(ws + L.cnext);
     p.cdone = reinterpret_cast<unsigned int *>(ws + L.cdone);
-    p.ctr = reinterpret_cast<unsigned long long *>(ws + L.ctr);
+    p.ctr = reinterpret_cast<unsigned int *>(ws + L.ctr);
     p.status = status;
     p.prev = prev;
     p.lead = std::min<uint64_t>(sd::kChunk + sd::kSlack, ntiles);
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
+    if (!sd::tickets_fit(ntiles, p.lead, grid)) return VBYTE_EINVAL;
     if (delta)
         sd::sdecode_kernel<true, false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
     else
@@ -1206,11 +1228,12 @@ int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cuda
     p.n = a.n;
     p.ntiles = ntiles;
     p.base = addr & ~static_cast<uintptr_t>(15);
+    sd::inside_range(p, addr, a.nbytes);
     p.tdesc = reinterpret_cast<uint64_t *>(ws + Y.tdesc);
     p.tpre = reinterpret_cast<uint64_t *>(ws + Y.tpre);
     p.cnext = reinterpret_cast<uint64_t *>(ws + Y.cnext);
     p.cdone = reinterpret_cast<unsigned int *>(ws + Y.cdone);
-    p.ctr = reinterpret_cast<unsigned long long *>(ws + Y.ctr);
+    p.ctr = reinterpret_cast<unsigned int *>(ws + Y.ctr);
     p.status = status;
     p.prev = 0u;
     p.lead = std::min<uint64_t>(sd::kChunk + cfg.lead_slack, ntiles);
@@ -1222,6 +1245,7 @@ int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cuda
     const int occ = di.occ_seg[a.delta];
     const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * per_sm);
+    if (!sd::tickets_fit(ntiles, p.lead, grid)) return VBYTE_EINVAL;
     if (a.delta)
         sd::sdecode_kernel<true, true><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
     else
