@@ -497,16 +497,6 @@ __device__ __forceinline__ uint4 staged_quad(const uint32_t *vals, int q)
     return make_uint4(U.y, U.z, U.w, V.x);
 }
 
-__device__ __forceinline__ uint4 staged_quad(const uint32_t *vals, int q, int sh)
-{
-    switch (sh) {
-    case 0: return staged_quad<0>(vals, q);
-    case 1: return staged_quad<1>(vals, q);
-    case 2: return staged_quad<2>(vals, q);
-    default: return staged_quad<3>(vals, q);
-    }
-}
-
 // Whole quads q0, q0 + 32, ... below qb to oq + 4q, `add` added to the ranks
 // below hf (kHf; all ranks otherwise).
 template <int SH, bool kHf>
@@ -653,26 +643,19 @@ __device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const Re
     // Output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
     // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of
     // V = vals[4q+4..].  Quads [qa, qb) are whole (inside this warp's ranks
-    // and below n); the others are written element by element.
-    const int nq = (static_cast<int>(wc) + sh + 3) >> 2;
+    // and below n); the ranks outside them are written one per lane.
     const long long lim = n - G0 + sh;   // quads with 4q + 4 <= lim end below n
     int qb = (static_cast<int>(wc) + sh) >> 2;
     if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
     const int qa = sh ? 1 : 0;
     store_quads<false>(oq, vals, qa + lane, qb, add, 0, sh);
-    // edge quads: the first (partly before this warp's ranks) and those from qb on
-    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
-        uint4 e = staged_quad(vals, q, sh);
-        e.x += add;
-        e.y += add;
-        e.z += add;
-        e.w += add;
-        const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
-        const int r0 = 4 * q - sh;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (r0 + j >= 0 && r0 + j < static_cast<int>(wc) && G0 + r0 + j < n) oq[4 * q + j] = e4[j];
-    }
+    const int whole = qb > qa;
+    const int hb = whole ? min(4 * qa - sh, static_cast<int>(wc)) : static_cast<int>(wc);   // ranks [0, hb)
+    const int tb = whole ? 4 * qb - sh : static_cast<int>(wc);                              // ranks [tb, wc)
+    for (int r = lane; r < hb; r += kLanes)
+        if (G0 + r < n) oq[sh + r] = vals[4 + r] + add;
+    for (int r = tb + lane; r < static_cast<int>(wc); r += kLanes)
+        if (G0 + r < n) oq[sh + r] = vals[4 + r] + add;
 }
 
 // After the middle barrier: this warp's values to the output, coalesced.
@@ -706,27 +689,20 @@ __device__ __forceinline__ void decode_emit_seg(const Params &p, const SharedS &
     // Output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
     // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of
     // V = vals[4q+4..].  Quads [qa, qb) are whole (inside this warp's ranks
-    // and below n); the others are written element by element.
-    const int nq = (static_cast<int>(wc) + sh + 3) >> 2;
+    // and below n); the ranks outside them are written one per lane.
     const long long lim = n - G0 + sh;   // quads with 4q + 4 <= lim end below n
     int qb = (static_cast<int>(wc) + sh) >> 2;
     if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
     const int qa = sh ? 1 : 0;
     uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
     store_quads<true>(oq, vals, qa + lane, qb, add, hf, sh);
-    // edge quads: the first (partly before this warp's ranks) and those from qb on
-    for (int q = (lane == 0 ? 0 : qb + lane - 1); q < nq && (lane == 0 ? q < qa : true); q += kLanes) {
-        uint4 e = staged_quad(vals, q, sh);
-        const int r0 = 4 * q - sh;
-        e.x += (r0 < hf) ? add : 0u;
-        e.y += (r0 + 1 < hf) ? add : 0u;
-        e.z += (r0 + 2 < hf) ? add : 0u;
-        e.w += (r0 + 3 < hf) ? add : 0u;
-        const uint32_t e4[4] = {e.x, e.y, e.z, e.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (r0 + j >= 0 && r0 + j < static_cast<int>(wc) && G0 + r0 + j < n) oq[4 * q + j] = e4[j];
-    }
+    const int whole = qb > qa;
+    const int hb = whole ? min(4 * qa - sh, static_cast<int>(wc)) : static_cast<int>(wc);   // ranks [0, hb)
+    const int tb = whole ? 4 * qb - sh : static_cast<int>(wc);                              // ranks [tb, wc)
+    for (int r = lane; r < hb; r += kLanes)
+        if (G0 + r < n) oq[sh + r] = vals[4 + r] + (r < hf ? add : 0u);
+    for (int r = tb + lane; r < static_cast<int>(wc); r += kLanes)
+        if (G0 + r < n) oq[sh + r] = vals[4 + r] + (r < hf ? add : 0u);
 }
 
 // ---- batched lists (segmented sums restart at every list head)
