@@ -11,7 +11,7 @@
 
 namespace vbk {
 
-constexpr uint64_t kDefaultLeadSlack = 3584;
+constexpr uint64_t kDefaultLeadSlack = 4608;
 
 // One batched decode: list j is bytes [bo[j], bo[j+1]) of in and values
 // [vo[j], vo[j+1]) of out (bo, vo, prevs in device memory).

@@ -118,7 +118,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
         }
         if (!cached) {
             const int occ = vbk::sbatched_max_ctas(a.delta);
-            const uint64_t slacks[] = {2560, 3584, 4608};
+            const uint64_t slacks[] = {3584, 4608, 5632};
             float best = 0.f;
             for (int c = 1; c <= occ; ++c) {
                 for (uint64_t sl : slacks) {

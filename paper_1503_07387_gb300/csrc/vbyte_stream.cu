@@ -61,7 +61,7 @@ constexpr int kThreads = kWarps * kLanes;
 constexpr int kTile = kThreads * kBPT;          // 4 KiB per tile
 constexpr int kWarpBytes = kLanes * kBPT;       // 512 bytes per warp
 constexpr uint64_t kChunk = 2048;               // tiles per chunk (8 MiB)
-constexpr uint64_t kSlack = 3584;               // tickets between a chunk's last count ticket and its first decode
+constexpr uint64_t kSlack = 4608;               // tickets between a chunk's last count ticket and its first decode
 constexpr int kByteBuf = kHalo + kTile + 16;
 constexpr int kWarpValBuf = kWarpBytes + 16;    // staged values of one warp (528)
 constexpr int kStages = 2;                      // tickets in flight per CTA (processed + staged ahead)
@@ -497,13 +497,21 @@ __device__ __forceinline__ uint4 staged_quad(const uint32_t *vals, int q)
     return make_uint4(U.y, U.z, U.w, V.x);
 }
 
-// Whole quads q0, q0 + 32, ... below qb to oq + 4q, `add` added to the ranks
-// below hf (kHf; all ranks otherwise).
+// A warp's staged values to the output, SH = (output word of rank 0) mod 4.
+// Output quad q holds ranks 4q - SH .. 4q - SH + 3, staged at
+// vals[4q + 4 - SH ..]; quads [qa, qb) are whole (inside the warp's ranks and
+// below `room`, the ranks the output still holds); the ranks outside them
+// are written one per lane.  `add` goes to the ranks below hf (kHf; to all
+// otherwise).
 template <int SH, bool kHf>
-__device__ __forceinline__ void store_quads(uint32_t *oq, const uint32_t *vals, int q0, int qb, uint32_t add, int hf)
+__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, int hf,
+                                            long long room, int lane)
 {
+    constexpr int qa = SH ? 1 : 0;
+    const int lim = room < wc ? (room > 0 ? static_cast<int>(room) : 0) : wc;   // ranks [0, lim) are written
+    const int qb = (lim + SH) >> 2;
 #pragma unroll 2
-    for (int q = q0; q < qb; q += kLanes) {
+    for (int q = qa + lane; q < qb; q += kLanes) {
         uint4 e = staged_quad<SH>(vals, q);
         const int r0 = 4 * q - SH;
         e.x += (!kHf || r0 < hf) ? add : 0u;
@@ -512,17 +520,22 @@ __device__ __forceinline__ void store_quads(uint32_t *oq, const uint32_t *vals, 
         e.w += (!kHf || r0 + 3 < hf) ? add : 0u;
         st_quad(oq + 4 * q, e);
     }
+    const bool whole = qb > qa;
+    const int hb = whole ? min(4 * qa - SH, lim) : lim;   // ranks [0, hb)
+    const int tb = whole ? 4 * qb - SH : lim;             // ranks [tb, lim)
+    for (int r = lane; r < hb; r += kLanes) oq[SH + r] = vals[4 + r] + ((!kHf || r < hf) ? add : 0u);
+    for (int r = tb + lane; r < lim; r += kLanes) oq[SH + r] = vals[4 + r] + ((!kHf || r < hf) ? add : 0u);
 }
 
 template <bool kHf>
-__device__ __forceinline__ void store_quads(uint32_t *oq, const uint32_t *vals, int q0, int qb, uint32_t add, int hf,
-                                            int sh)
+__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, int hf,
+                                            long long room, int lane, int sh)
 {
-    switch (sh) {   // warp-uniform: one loop per alignment
-    case 0: store_quads<0, kHf>(oq, vals, q0, qb, add, hf); break;
-    case 1: store_quads<1, kHf>(oq, vals, q0, qb, add, hf); break;
-    case 2: store_quads<2, kHf>(oq, vals, q0, qb, add, hf); break;
-    default: store_quads<3, kHf>(oq, vals, q0, qb, add, hf); break;
+    switch (sh) {   // warp-uniform
+    case 0: emit_staged<0, kHf>(oq, vals, wc, add, hf, room, lane); break;
+    case 1: emit_staged<1, kHf>(oq, vals, wc, add, hf, room, lane); break;
+    case 2: emit_staged<2, kHf>(oq, vals, wc, add, hf, room, lane); break;
+    default: emit_staged<3, kHf>(oq, vals, wc, add, hf, room, lane); break;
     }
 }
 
@@ -640,22 +653,7 @@ __device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const Re
         for (int j = 0; j < 4; ++j) d4[j] = q[j];
         __syncwarp();
     }
-    // Output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
-    // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of
-    // V = vals[4q+4..].  Quads [qa, qb) are whole (inside this warp's ranks
-    // and below n); the ranks outside them are written one per lane.
-    const long long lim = n - G0 + sh;   // quads with 4q + 4 <= lim end below n
-    int qb = (static_cast<int>(wc) + sh) >> 2;
-    if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
-    const int qa = sh ? 1 : 0;
-    store_quads<false>(oq, vals, qa + lane, qb, add, 0, sh);
-    const int whole = qb > qa;
-    const int hb = whole ? min(4 * qa - sh, static_cast<int>(wc)) : static_cast<int>(wc);   // ranks [0, hb)
-    const int tb = whole ? 4 * qb - sh : static_cast<int>(wc);                              // ranks [tb, wc)
-    for (int r = lane; r < hb; r += kLanes)
-        if (G0 + r < n) oq[sh + r] = vals[4 + r] + add;
-    for (int r = tb + lane; r < static_cast<int>(wc); r += kLanes)
-        if (G0 + r < n) oq[sh + r] = vals[4 + r] + add;
+    emit_staged<false>(oq, vals, static_cast<int>(wc), add, 0, n - G0, lane, sh);
 }
 
 // After the middle barrier: this warp's values to the output, coalesced.
@@ -686,23 +684,8 @@ __device__ __forceinline__ void decode_emit_seg(const Params &p, const SharedS &
     const int hf = kDelta ? static_cast<int>(min(S.dhf[warp], wc)) : static_cast<int>(wc);   // ranks [hf, wc) are absolute
     const int sh = static_cast<int>((out_word + static_cast<uint32_t>(G0)) & 3u);
     const uint32_t *vals = S.vals[warp];
-    // Output quad q holds warp ranks 4q - sh .. 4q - sh + 3, staged at
-    // vals[4q + 4 - sh ..]: the tail of U = vals[4q..] and the head of
-    // V = vals[4q+4..].  Quads [qa, qb) are whole (inside this warp's ranks
-    // and below n); the ranks outside them are written one per lane.
-    const long long lim = n - G0 + sh;   // quads with 4q + 4 <= lim end below n
-    int qb = (static_cast<int>(wc) + sh) >> 2;
-    if (lim < 4 * static_cast<long long>(qb)) qb = lim > 0 ? static_cast<int>(lim >> 2) : 0;
-    const int qa = sh ? 1 : 0;
     uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
-    store_quads<true>(oq, vals, qa + lane, qb, add, hf, sh);
-    const int whole = qb > qa;
-    const int hb = whole ? min(4 * qa - sh, static_cast<int>(wc)) : static_cast<int>(wc);   // ranks [0, hb)
-    const int tb = whole ? 4 * qb - sh : static_cast<int>(wc);                              // ranks [tb, wc)
-    for (int r = lane; r < hb; r += kLanes)
-        if (G0 + r < n) oq[sh + r] = vals[4 + r] + (r < hf ? add : 0u);
-    for (int r = tb + lane; r < static_cast<int>(wc); r += kLanes)
-        if (G0 + r < n) oq[sh + r] = vals[4 + r] + (r < hf ? add : 0u);
+    emit_staged<true>(oq, vals, static_cast<int>(wc), add, hf, n - G0, lane, sh);
 }
 
 // ---- batched lists (segmented sums restart at every list head)
