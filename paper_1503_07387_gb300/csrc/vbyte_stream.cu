@@ -685,7 +685,34 @@ __device__ __forceinline__ void decode_emit_seg(const Params &p, const SharedS &
     const int sh = static_cast<int>((out_word + static_cast<uint32_t>(G0)) & 3u);
     const uint32_t *vals = S.vals[warp];
     uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
-    emit_staged<true>(oq, vals, static_cast<int>(wc), add, hf, n - G0, lane, sh);
+    // the same bounds as emit_staged, with the alignment chosen per quad: one
+    // copy of the loop keeps this larger kernel's code small
+    const long long room = n - G0;
+    const int lim = room < wc ? (room > 0 ? static_cast<int>(room) : 0) : static_cast<int>(wc);
+    const int qa = sh ? 1 : 0;
+    const int qb = (lim + sh) >> 2;
+    for (int q = qa + lane; q < qb; q += kLanes) {
+        const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
+        const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
+        uint4 e;
+        switch (sh) {
+        case 0: e = V; break;
+        case 1: e = make_uint4(U.w, V.x, V.y, V.z); break;
+        case 2: e = make_uint4(U.z, U.w, V.x, V.y); break;
+        default: e = make_uint4(U.y, U.z, U.w, V.x); break;
+        }
+        const int r0 = 4 * q - sh;
+        e.x += (r0 < hf) ? add : 0u;
+        e.y += (r0 + 1 < hf) ? add : 0u;
+        e.z += (r0 + 2 < hf) ? add : 0u;
+        e.w += (r0 + 3 < hf) ? add : 0u;
+        st_quad(oq + 4 * q, e);
+    }
+    const bool whole = qb > qa;
+    const int hb = whole ? min(4 * qa - sh, lim) : lim;   // ranks [0, hb)
+    const int tb = whole ? 4 * qb - sh : lim;             // ranks [tb, lim)
+    for (int r = lane; r < hb; r += kLanes) oq[sh + r] = vals[4 + r] + (r < hf ? add : 0u);
+    for (int r = tb + lane; r < lim; r += kLanes) oq[sh + r] = vals[4 + r] + (r < hf ? add : 0u);
 }
 
 // ---- batched lists (segmented sums restart at every list head)
