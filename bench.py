@@ -437,8 +437,10 @@ def run_serving(args, pool):
     scheduled arrival to the scheduler seeing its batch complete."""
     import torch
     from paper_1503_07387_gb300 import vbyte
+    # in-flight outputs need a few tens of MB at these rates; a small arena
+    # keeps each server's set-up and tear-down cheap
     free, _ = torch.cuda.mem_get_info()
-    arena = int(min(free * 0.25, 32 << 30)) // 4096 * 4096
+    arena = int(min(free * 0.25, 1 << 30)) // 4096 * 4096
     cfg = dict(arena_bytes=arena, staging_bytes=512 << 20, max_inflight=4, max_batch_queries=64,
                max_batch_lists=512)
     rows = []
@@ -449,7 +451,7 @@ def run_serving(args, pool):
         row = {"rate_qps": rate, "queries": nq, "values": vals}
         for form, per_list in (("batched", False), ("per_list", True)):
             srv = vbyte.Server(pool["d"], pool["bo"], pool["vo"], True, pool["prev"], per_list=per_list, **cfg)
-            w = min(nq, 100)   # untimed warm-up at the same rate
+            w = min(nq, max(100, int(rate * 0.2)))   # untimed warm-up: 0.2 s at the same rate
             srv.replay(arr[:w], qoff[:w + 1], ql[:int(qoff[w])])
             s0 = srv.stats()
             t0 = time.perf_counter()
