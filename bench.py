@@ -278,6 +278,11 @@ def run_gpu(args):
     e2e_s = max_over_ranks(e2e_s, ws, "cuda")
     status |= vbyte.get_status()
 
+    # ---- the device encoder on the same streams (the step before the path)
+    encode = None
+    if not args.no_encode:
+        encode = run_encode(args, streams, stream, measured_peaks())
+
     # ---- batched lists: one tuned, graph-replayed launch vs one call per list
     batched = serving = None
     if ws == 1 and not args.no_batched:
@@ -345,6 +350,7 @@ def run_gpu(args):
             "api": "vbyte_decode_host (pinned host buffers, copies inside the call)",
         },
         "gpu_launches": len(streams) * args.steps,
+        "encode": encode,
         "batched": batched,
         "serving": serving,
         "status": status,
@@ -354,6 +360,44 @@ def run_gpu(args):
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_encode(args, streams, stream, peaks):
+    """Device encoding of the decoded streams (differential streams from their
+    document ids), checked byte for byte against the encoded input and timed
+    with CUDA events: Gints/s and the HBM roofline (4n read + bytes written)."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    bufs = [torch.empty(5 * s["n"], dtype=torch.uint8, device="cuda") for s in streams]
+    nbs = [torch.empty(1, dtype=torch.int64, device="cuda") for _ in streams]
+
+    def step():
+        for s, b, nb in zip(streams, bufs, nbs):
+            vbyte.encode_device(s["d_out"], delta=s["delta"], out=b, nbytes=nb, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    exact = all(int(nb.item()) == s["host"].size and torch.equal(b[:s["host"].size], s["d_in"])
+                for s, b, nb in zip(streams, bufs, nbs))
+    reps = max(5, min(args.steps, 200))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    n = sum(s["n"] for s in streams)
+    algo = sum(4 * s["n"] + s["host"].size for s in streams)
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = algo / (ms * 1e-3) / 1e9
+    del bufs
+    return {"value": round(n / (ms * 1e-3) / 1e9, 3), "unit": "Gints/s", "ms_per_step": round(ms, 5),
+            "form": "vbyte_encode_device / vbyte_encode_delta_device, one launch per stream",
+            "bit_exact_with_input": bool(exact), "status": int(vbyte.get_status()),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes_per_step": algo}}
 
 
 def run_batched(args, peaks):
@@ -583,6 +627,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-encode", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000, 50000])
     ap.add_argument("--serve-seconds", type=float, default=1.0)

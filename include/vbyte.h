@@ -93,6 +93,29 @@ size_t vbyte_encode_batched(const uint32_t *h_in, const uint64_t *h_val_off,
                             size_t num_lists, int delta, const uint32_t *h_prev,
                             uint8_t *h_out, uint64_t *h_byte_off);
 
+/* ---- GPU encoding -------------------------------------------------------- */
+
+/* Encode the n uint32 at d_in (4-byte aligned) into d_out, exactly as
+ * vbyte_encode would (Sec. 1, Table 1: 7-bit groups, least significant
+ * first, the high bit set on every byte but the last; the shortest form).
+ * d_out must hold vbyte_max_encoded_size(n) bytes.  The number of bytes
+ * written goes to *d_nbytes (device memory) when the stream reaches it; no
+ * host synchronisation.  All pointers are caller-owned device memory; the
+ * call uses the stream's workspace and allocates only when it grows.
+ * Returns VBYTE_OK; VBYTE_EINVAL for a null pointer with n > 0, a null
+ * d_nbytes or a misaligned d_in; VBYTE_ENOMEM / VBYTE_ECUDA for allocation
+ * or launch failures.  Every value is encodable, so the only data-dependent
+ * status bit is VBYTE_ERR_TIMEOUT (vbyte_get_status). */
+int vbyte_encode_device(const uint32_t *d_in, size_t n, uint8_t *d_out,
+                        uint64_t *d_nbytes, void *stream);
+
+/* Differential coding (Sec. 1) on the device: encode the gaps
+ * d_in[i] - d_in[i-1] modulo 2^32 with d_in[-1] = prev, as
+ * vbyte_encode_delta would.  Arguments and errors as vbyte_encode_device. */
+int vbyte_encode_delta_device(const uint32_t *d_in, size_t n, uint32_t prev,
+                              uint8_t *d_out, uint64_t *d_nbytes,
+                              void *stream);
+
 /* ---- single-stream GPU decoding ----------------------------------------- */
 
 /* Decode the nbytes-byte stream at d_in (any alignment) into the n uint32 at

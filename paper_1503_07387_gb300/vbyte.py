@@ -49,6 +49,8 @@ def _signatures(lib):
         "vbyte_encode": ([P, S, P], S),
         "vbyte_encode_delta": ([P, S, U32, P], S),
         "vbyte_encode_batched": ([P, P, S, I, P, P, P], S),
+        "vbyte_encode_device": ([P, S, P, P, P], I),
+        "vbyte_encode_delta_device": ([P, S, U32, P, P, P], I),
         "vbyte_decode": ([P, S, P, S, P], I),
         "vbyte_decode_delta": ([P, S, P, S, U32, P], I),
         "vbyte_decode_host": ([P, S, P, S, I, U32, P], I),
@@ -161,6 +163,33 @@ def _device_args(data, n, out):
     elif out.dtype not in (torch.uint32, torch.int32) or not out.is_contiguous() or out.numel() < n:
         raise ValueError("out must be a contiguous 32-bit CUDA tensor with at least n elements")
     return out
+
+
+def encode_device(values, delta: bool = False, prev: int = 0, out=None, nbytes=None, stream=None):
+    """Encode the CUDA uint32/int32 tensor `values` on the device (delta: its
+    gaps from prev).  Returns (out, nbytes): `out` is a uint8 tensor of
+    5 * n bytes whose first nbytes hold the encoding, `nbytes` a one-element
+    int64 CUDA tensor written when the stream gets there (no synchronisation)."""
+    import torch
+    if not isinstance(values, torch.Tensor) or not values.is_cuda or not values.is_contiguous() \
+            or values.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("values must be a contiguous CUDA int32/uint32 tensor")
+    n = values.numel()
+    if out is None:
+        out = torch.empty(max(5 * n, 1), dtype=torch.uint8, device=values.device)
+    elif out.dtype != torch.uint8 or not out.is_cuda or out.numel() < 5 * n or not out.is_contiguous():
+        raise TypeError("out must be a contiguous CUDA uint8 tensor of at least 5 * n bytes")
+    if nbytes is None:
+        nbytes = torch.empty(1, dtype=torch.int64, device=values.device)
+    lib, st = load(), _stream_handle(stream)
+    if delta:
+        rc = lib.vbyte_encode_delta_device(ctypes.c_void_p(values.data_ptr()), n, ctypes.c_uint32(prev & 0xFFFFFFFF),
+                                           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(nbytes.data_ptr()), st)
+    else:
+        rc = lib.vbyte_encode_device(ctypes.c_void_p(values.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(nbytes.data_ptr()), st)
+    _check(rc, "vbyte_encode_delta_device" if delta else "vbyte_encode_device")
+    return out, nbytes
 
 
 def decode(data, n: int, out=None, stream=None):
