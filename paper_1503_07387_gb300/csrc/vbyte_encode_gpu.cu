@@ -8,7 +8,7 @@
 // x_{-1} = prev (Sec. 1, "Differential coding").
 //
 // Design: one pass over the input with a decoupled look-back over tiles of
-// 2048 values.  Persistent CTAs take tiles in ticket order; a CTA loads its
+// 6144 values.  Persistent CTAs take tiles in ticket order; a CTA loads its
 // tile, computes every value's length, publishes the tile's byte count,
 // looks back over the words of earlier tiles for its byte offset, publishes
 // its inclusive offset, encodes the tile into shared memory and writes it
@@ -32,10 +32,11 @@ namespace enc {
 
 constexpr int kLanes = 32;
 constexpr int kThreads = 256;
-constexpr int kVPT = 8;                              // values per thread
-constexpr int kTileVals = kThreads * kVPT;           // 2048 values per tile
+constexpr int kVPT = 24;                             // values per thread
+constexpr int kTileVals = kThreads * kVPT;           // 6144 values per tile
 constexpr int kTileBytesMax = 5 * kTileVals;         // encoded bytes of a tile, at most
 constexpr int kBuf = kTileBytesMax + 16;
+static_assert(kVPT % 4 == 0, "vector loads of four values");
 
 struct Params {
     const uint32_t *in;
@@ -102,10 +103,14 @@ __global__ void __launch_bounds__(kThreads) encode_kernel(const Params p)
         // my values (zeros past n: they are not written)
         uint32_t x[kVPT];
         if (p.vec && v0 + kVPT <= p.n) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p.in + v0));
-            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p.in + v0 + 4));
-            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+#pragma unroll
+            for (int i = 0; i < kVPT; i += 4) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p.in + v0 + i));
+                x[i] = a.x;
+                x[i + 1] = a.y;
+                x[i + 2] = a.z;
+                x[i + 3] = a.w;
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < kVPT; ++i) x[i] = v0 + i < p.n ? __ldg(p.in + v0 + i) : 0u;
@@ -148,18 +153,23 @@ __global__ void __launch_bounds__(kThreads) encode_kernel(const Params p)
                 if (t == p.ntiles - 1) *p.nbytes = off + tot;
             }
         }
-        // encode my values into the staged tile
+        // encode my values into the staged tile: byte k of a value of length
+        // L is its k-th 7-bit group, with the high bit set while k < L - 1
+        // (the first four groups spread to the four bytes of one word)
         uint32_t o = wb + inc - len;
 #pragma unroll
         for (int i = 0; i < kVPT; ++i) {
             if (i < cnt) {
-                uint32_t v = x[i];
+                const uint32_t v = x[i];
                 const uint32_t L = vlen(v);
-                for (uint32_t k = 0; k + 1 < L; ++k) {
-                    S.bytes[o++] = static_cast<uint8_t>((v & 0x7Fu) | 0x80u);
-                    v >>= 7;
-                }
-                S.bytes[o++] = static_cast<uint8_t>(v);
+                const uint32_t g = (v & 0x7Fu) | ((v << 1) & 0x7F00u) | ((v << 2) & 0x7F0000u) | ((v << 3) & 0x7F000000u);
+                const uint32_t w = g | static_cast<uint32_t>(0x80808080ull >> (8 * (5 - L)));
+                S.bytes[o] = static_cast<uint8_t>(w);
+                if (L > 1) S.bytes[o + 1] = static_cast<uint8_t>(w >> 8);
+                if (L > 2) S.bytes[o + 2] = static_cast<uint8_t>(w >> 16);
+                if (L > 3) S.bytes[o + 3] = static_cast<uint8_t>(w >> 24);
+                if (L > 4) S.bytes[o + 4] = static_cast<uint8_t>(v >> 28);
+                o += L;
             }
         }
         __syncthreads();

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("CUDA not available", allow_module_level=True)
 
-TILE = 2048   # values per encoder tile
+TILE = 6144   # values per encoder tile
 
 
 def all_lengths(n, seed):
