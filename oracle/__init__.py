@@ -60,6 +60,10 @@ def _load():
     lib.oracle_decode.restype = S
     lib.oracle_decode_delta.argtypes = [P, S, P, S, U32]
     lib.oracle_decode_delta.restype = S
+    lib.oracle_encode_delta_m1.argtypes = [P, S, U32, P]
+    lib.oracle_encode_delta_m1.restype = S
+    lib.oracle_decode_delta_m1.argtypes = [P, S, P, S, U32]
+    lib.oracle_decode_delta_m1.restype = S
     lib.oracle_validate.argtypes = [P, S, S]
     lib.oracle_validate.restype = U32
     lib.oracle_decode_batched.argtypes = [P, P, P, S, ctypes.c_int, P, P]
@@ -121,6 +125,29 @@ def decode_delta(data, n: int | None = None, prev: int = 0) -> np.ndarray:
     if cnt > cap:
         out = np.empty(cnt, dtype=np.uint32)
         cnt = _load().oracle_decode_delta(_ptr(b), b.size, _ptr(out), cnt, p)
+    return out[:cnt].copy()
+
+
+def encode_delta_m1(values, prev: int = 0) -> np.ndarray:
+    """The differential variant of Sec. 1 for lists without repeated values:
+    store x_1 - x_0, then x_i - x_{i-1} - 1 (mod 2^32), x_0 = prev."""
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    out = np.empty(5 * v.size, dtype=np.uint8)
+    nb = _load().oracle_encode_delta_m1(_ptr(v), v.size, ctypes.c_uint32(prev & 0xFFFFFFFF), _ptr(out))
+    return out[:nb].copy()
+
+
+def decode_delta_m1(data, n: int | None = None, prev: int = 0) -> np.ndarray:
+    """Algorithm 1 with the running sum of that variant: one more for every
+    value after the first (uint32 wrap-around)."""
+    b = _u8(data)
+    cap = b.size if n is None else max(n, 0)
+    out = np.empty(max(cap, 1), dtype=np.uint32)
+    p = ctypes.c_uint32(prev & 0xFFFFFFFF)
+    cnt = _load().oracle_decode_delta_m1(_ptr(b), b.size, _ptr(out), cap, p)
+    if cnt > cap:
+        out = np.empty(cnt, dtype=np.uint32)
+        cnt = _load().oracle_decode_delta_m1(_ptr(b), b.size, _ptr(out), cnt, p)
     return out[:cnt].copy()
 
 

@@ -16,7 +16,10 @@
  *     bit;
  *   - differential coding: gaps x_i - x_{i-1} with x_0 = prev (0 by default),
  *     undone by keeping the last decoded value and adding it to each gap
- *     (Sec. 1 "Differential coding" and Sec. 2);
+ *     (Sec. 1 "Differential coding" and Sec. 2); and the variant for lists
+ *     without repeated values that Sec. 1 also names, which stores the first
+ *     gap as is and every later one minus one (x_1 - x_0, x_2 - x_1 - 1, ...),
+ *     undone by adding one more for every value after the first;
  *   - validation: a separate pass that states the data-error contract
  *     (a run of five or more bytes with the high bit set; a final byte with
  *     the high bit set; a terminator count that differs from the expected
@@ -68,13 +71,29 @@ size_t oracle_encode_delta(const uint32_t *in, size_t n, uint32_t prev,
     return w;
 }
 
+/* Sec. 1 "Differential coding", the variant for lists without repeated
+ * values: store x_1 - x_0, then x_i - x_{i-1} - 1; x_0 = prev. */
+size_t oracle_encode_delta_m1(const uint32_t *in, size_t n, uint32_t prev,
+                              uint8_t *out)
+{
+    size_t w = 0;
+    for (size_t i = 0; i < n; ++i) {
+        uint32_t gap = in[i] - prev - (i > 0 ? 1u : 0u);
+        prev = in[i];
+        w += oracle_encode_one(gap, out + w);
+    }
+    return w;
+}
+
 /* ---------------------------------------------------------------- decode -- */
 
 /* Algorithm 1, step by step.  Returns the number of integers Algorithm 1
  * appends; values beyond `cap` are counted but not stored.  If the input ends
  * inside an integer (readByte has nothing left to return), the partial
  * integer is dropped.  With delta != 0 the running value p starts at prev and
- * each decoded gap is added to it (Sec. 2, last paragraph before Alg. 1). */
+ * each decoded gap is added to it (Sec. 2, last paragraph before Alg. 1);
+ * with delta == 2 (gaps minus one) every value after the first adds one
+ * more. */
 static size_t algorithm1(const uint8_t *in, size_t nbytes, uint32_t *y,
                          size_t cap, int delta, uint32_t prev)
 {
@@ -88,7 +107,10 @@ static size_t algorithm1(const uint8_t *in, size_t nbytes, uint32_t *y,
 #define APPEND(val)                                  \
     do {                                             \
         uint32_t v_ = (uint32_t)(val);               \
-        if (delta) { p = p + v_; v_ = p; }           \
+        if (delta) {                                 \
+            p = p + v_ + (delta == 2 && count > 0);  \
+            v_ = p;                                  \
+        }                                            \
         if (count < cap) y[count] = v_;              \
         ++count;                                     \
     } while (0)
@@ -125,6 +147,12 @@ size_t oracle_decode_delta(const uint8_t *in, size_t nbytes, uint32_t *out,
                            size_t cap, uint32_t prev)
 {
     return algorithm1(in, nbytes, out, cap, 1, prev);
+}
+
+size_t oracle_decode_delta_m1(const uint8_t *in, size_t nbytes, uint32_t *out,
+                              size_t cap, uint32_t prev)
+{
+    return algorithm1(in, nbytes, out, cap, 2, prev);
 }
 
 /* -------------------------------------------------------------- validate -- */

@@ -25,8 +25,13 @@ size_t oracle_encode(const uint32_t *in, size_t n, uint8_t *out);
 size_t oracle_encode_delta(const uint32_t *in, size_t n, uint32_t prev,
                            uint8_t *out);
 
+size_t oracle_encode_delta_m1(const uint32_t *in, size_t n, uint32_t prev,
+                              uint8_t *out);
+
 size_t oracle_decode(const uint8_t *in, size_t nbytes, uint32_t *out,
                      size_t cap);
+size_t oracle_decode_delta_m1(const uint8_t *in, size_t nbytes, uint32_t *out,
+                              size_t cap, uint32_t prev);
 size_t oracle_decode_delta(const uint8_t *in, size_t nbytes, uint32_t *out,
                            size_t cap, uint32_t prev);
 uint32_t oracle_validate(const uint8_t *in, size_t nbytes, size_t n);

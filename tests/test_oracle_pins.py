@@ -196,6 +196,52 @@ def test_delta_wraps_modulo_2_32():
     assert np.array_equal(oracle.decode_delta(enc), x)
 
 
+# ---------------------------------- differential coding, gaps minus one --
+# Sec. 1 names a variant for lists without repeated values: x_1 - 0,
+# x_2 - x_1 - 1, x_3 - x_2 - 1, ...
+
+def test_m1_paper_form():
+    """The stored integers are exactly the paper's list (x_1 - 0, x_2 - x_1 - 1, ...)."""
+    x = np.array([3, 4, 7, 8, 100, 101], dtype=np.uint32)
+    stored = [3, 4 - 3 - 1, 7 - 4 - 1, 8 - 7 - 1, 100 - 8 - 1, 101 - 100 - 1]
+    enc = oracle.encode_delta_m1(x)
+    assert oracle.decode(enc).tolist() == stored
+    assert oracle.decode_delta_m1(enc).tolist() == x.tolist()
+
+
+def test_m1_consecutive_ids_are_all_zero_bytes():
+    """prev, prev+1, prev+2, ...: the first gap is 0 (x_1 - prev) and every
+    later one 1 - 1 = 0, so the stream is n zero bytes."""
+    x = (77 + np.arange(50_000, dtype=np.uint64)).astype(np.uint32)
+    enc = oracle.encode_delta_m1(x, prev=77)
+    assert enc.size == x.size and not enc.any()
+    assert np.array_equal(oracle.decode_delta_m1(enc, prev=77), x)
+
+
+def test_m1_generated_gaps_round_trip():
+    """Ids built from chosen gaps G (x_0 = prev + G_0, x_i = x_{i-1} + 1 + G_i):
+    the encoder stores exactly G and the decoder returns the ids, both checked
+    against the construction rather than against each other."""
+    rng = np.random.default_rng(9)
+    G = rng.geometric(0.01, 200_000).astype(np.uint64) - 1
+    prev = 12345
+    x = ((prev + np.cumsum(G) + np.arange(G.size, dtype=np.uint64)) & MASK32).astype(np.uint32)
+    enc = oracle.encode_delta_m1(x, prev=prev)
+    assert np.array_equal(oracle.decode(enc), G.astype(np.uint32))
+    assert np.array_equal(oracle.decode_delta_m1(enc, prev=prev), x)
+    # the plain differential decoder of the same bytes lags by one per value
+    lag = (oracle.decode_delta_m1(enc, prev=prev).astype(np.int64) -
+           oracle.decode_delta(enc, prev=prev).astype(np.int64)) % (1 << 32)
+    assert np.array_equal(lag, np.arange(G.size))
+
+
+def test_m1_wraps_modulo_2_32():
+    x = np.array([2**32 - 1, 0, 5, 5 + 2**31], dtype=np.uint32)   # 0 follows 2^32 - 1: gap 0
+    enc = oracle.encode_delta_m1(x, prev=2**32 - 3)
+    assert oracle.decode(enc).tolist() == [2, 0, 4, 2**31 - 1]
+    assert np.array_equal(oracle.decode_delta_m1(enc, prev=2**32 - 3), x)
+
+
 # ------------------------------------------------------------------ batched --
 
 def test_batched_matches_per_list_and_concatenation():
