@@ -84,6 +84,12 @@ size_t vbyte_encode(const uint32_t *h_in, size_t n, uint8_t *h_out);
 size_t vbyte_encode_delta(const uint32_t *h_in, size_t n, uint32_t prev,
                           uint8_t *h_out);
 
+/* The differential variant Sec. 1 names for lists without repeated values:
+ * encode h_in[0] - prev, then h_in[i] - h_in[i-1] - 1 (modulo 2^32).
+ * Returns the number of bytes written. */
+size_t vbyte_encode_delta_m1(const uint32_t *h_in, size_t n, uint32_t prev,
+                             uint8_t *h_out);
+
 /* Encode num_lists lists laid end to end: list j is
  * h_in[h_val_off[j] .. h_val_off[j+1]).  With delta != 0 each list is
  * differentially coded on its own, starting from h_prev[j] (0 when h_prev is
@@ -116,6 +122,12 @@ int vbyte_encode_delta_device(const uint32_t *d_in, size_t n, uint32_t prev,
                               uint8_t *d_out, uint64_t *d_nbytes,
                               void *stream);
 
+/* The gaps-minus-one variant (vbyte_encode_delta_m1) on the device.
+ * Arguments and errors as vbyte_encode_device. */
+int vbyte_encode_delta_m1_device(const uint32_t *d_in, size_t n, uint32_t prev,
+                                 uint8_t *d_out, uint64_t *d_nbytes,
+                                 void *stream);
+
 /* ---- single-stream GPU decoding ----------------------------------------- */
 
 /* Decode the nbytes-byte stream at d_in (any alignment) into the n uint32 at
@@ -133,6 +145,14 @@ int vbyte_decode(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size_t n,
  * for the next decodes a stream piece by piece. */
 int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
                        size_t n, uint32_t prev, void *stream);
+
+/* The gaps-minus-one variant (Sec. 1, "Differential coding": for lists
+ * without repeated values the stored gaps are x_1 - x_0, x_2 - x_1 - 1, ...):
+ * d_out[i] = prev + g_0 + ... + g_i + i modulo 2^32.  Arguments and errors as
+ * vbyte_decode_delta; the bytes are those vbyte_encode_delta_m1 writes.  For
+ * a piece after the first, pass as prev the last value before it plus one. */
+int vbyte_decode_delta_m1(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
+                          size_t n, uint32_t prev, void *stream);
 
 /* ---- batched GPU decoding ------------------------------------------------ */
 

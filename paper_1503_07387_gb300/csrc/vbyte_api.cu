@@ -290,6 +290,12 @@ int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size
     return vbk::launch_decode(d_in, nbytes, d_out, n, true, prev, static_cast<cudaStream_t>(stream));
 }
 
+int vbyte_decode_delta_m1(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size_t n, uint32_t prev,
+                          void *stream)
+{
+    return vbk::launch_decode(d_in, nbytes, d_out, n, true, prev, static_cast<cudaStream_t>(stream), true);
+}
+
 int vbyte_decode_batched(const uint8_t *d_in, size_t nbytes, const uint64_t *d_byte_off, uint32_t *d_out,
                          size_t n, const uint64_t *d_val_off, size_t num_lists, void *stream)
 {

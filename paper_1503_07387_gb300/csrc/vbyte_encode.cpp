@@ -48,12 +48,14 @@ size_t encode_plain(const uint32_t *in, size_t n, uint8_t *out)
     return static_cast<size_t>(o - out);
 }
 
-size_t encode_gaps(const uint32_t *in, size_t n, uint32_t prev, uint8_t *out)
+// Gaps x_i - x_{i-1} from x_{-1} = prev; with minus_one every gap after the
+// first is one less (the variant for lists without repeated values).
+size_t encode_gaps(const uint32_t *in, size_t n, uint32_t prev, uint8_t *out, bool minus_one = false)
 {
     uint8_t *o = out;
     for (size_t i = 0; i < n; ++i) {
         const uint32_t x = in[i];
-        o += put_value(x - prev, o);  // modulo 2^32
+        o += put_value(x - prev - ((minus_one && i > 0) ? 1u : 0u), o);  // modulo 2^32
         prev = x;
     }
     return static_cast<size_t>(o - out);
@@ -78,6 +80,13 @@ size_t vbyte_encode_delta(const uint32_t *h_in, size_t n, uint32_t prev,
     if (n == 0) return 0;
     if (!h_in || !h_out) return 0;
     return encode_gaps(h_in, n, prev, h_out);
+}
+
+size_t vbyte_encode_delta_m1(const uint32_t *h_in, size_t n, uint32_t prev, uint8_t *h_out)
+{
+    if (n == 0) return 0;
+    if (!h_in || !h_out) return 0;
+    return encode_gaps(h_in, n, prev, h_out, true);
 }
 
 size_t vbyte_encode_batched(const uint32_t *h_in, const uint64_t *h_val_off,

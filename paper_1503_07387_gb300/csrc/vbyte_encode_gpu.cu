@@ -5,7 +5,9 @@
 // byte, the high bit set on every byte but the last; its length is
 // 1 + [v >= 2^7] + [v >= 2^14] + [v >= 2^21] + [v >= 2^28].  In delta mode
 // the values written are the gaps x_i - x_{i-1} (mod 2^32) with
-// x_{-1} = prev (Sec. 1, "Differential coding").
+// x_{-1} = prev (Sec. 1, "Differential coding"); in the variant for lists
+// without repeated values (kM1, named in the same paragraph) every gap after
+// the first is one less.
 //
 // Design: one pass over the input with a decoupled look-back over tiles of
 // 6144 values.  Persistent CTAs take tiles in ticket order; a CTA loads its
@@ -89,7 +91,7 @@ __device__ uint64_t look_back(const Params &p, uint64_t t, int lane)
     return acc;
 }
 
-template <bool kDelta>
+template <bool kDelta, bool kM1 = false>
 __global__ void __launch_bounds__(kThreads) encode_kernel(const Params p)
 {
     __shared__ Shared S;
@@ -123,8 +125,8 @@ __global__ void __launch_bounds__(kThreads) encode_kernel(const Params p)
             if (lane == 0)
                 before = v0 == 0 ? p.prev : (v0 - 1 < p.n ? __ldg(p.in + v0 - 1) : 0u);
 #pragma unroll
-            for (int i = kVPT - 1; i > 0; --i) x[i] -= x[i - 1];
-            x[0] -= before;
+            for (int i = kVPT - 1; i > 0; --i) x[i] -= x[i - 1] + (kM1 ? 1u : 0u);
+            x[0] -= before + ((kM1 && v0 > 0) ? 1u : 0u);
         }
         uint32_t len = 0;
 #pragma unroll
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) encode_kernel(const Params p)
 namespace {
 
 int launch_encode(const uint32_t *in, size_t n, bool delta, uint32_t prev, uint8_t *out, uint64_t *d_nbytes,
-                  cudaStream_t s)
+                  cudaStream_t s, bool m1 = false)
 {
     if ((n && (!in || !out)) || !d_nbytes) return VBYTE_EINVAL;
     if (reinterpret_cast<uintptr_t>(in) & 3u) return VBYTE_EINVAL;
@@ -218,7 +220,9 @@ int launch_encode(const uint32_t *in, size_t n, bool delta, uint32_t prev, uint8
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return VBYTE_ECUDA;
-    if (delta)
+    if (m1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enc::encode_kernel<true, true>, enc::kThreads, 0);
+    else if (delta)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enc::encode_kernel<true>, enc::kThreads, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enc::encode_kernel<false>, enc::kThreads, 0);
@@ -234,7 +238,9 @@ int launch_encode(const uint32_t *in, size_t n, bool delta, uint32_t prev, uint8
     p.prev = prev;
     p.vec = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
     const uint64_t grid = std::min<uint64_t>(ntiles, static_cast<uint64_t>(sms) * std::max(occ, 1));
-    if (delta)
+    if (m1)
+        enc::encode_kernel<true, true><<<static_cast<unsigned>(grid), enc::kThreads, 0, s>>>(p);
+    else if (delta)
         enc::encode_kernel<true><<<static_cast<unsigned>(grid), enc::kThreads, 0, s>>>(p);
     else
         enc::encode_kernel<false><<<static_cast<unsigned>(grid), enc::kThreads, 0, s>>>(p);
@@ -255,6 +261,12 @@ int vbyte_encode_delta_device(const uint32_t *d_in, size_t n, uint32_t prev, uin
                               void *stream)
 {
     return vbk::launch_encode(d_in, n, true, prev, d_out, d_nbytes, static_cast<cudaStream_t>(stream));
+}
+
+int vbyte_encode_delta_m1_device(const uint32_t *d_in, size_t n, uint32_t prev, uint8_t *d_out,
+                                 uint64_t *d_nbytes, void *stream)
+{
+    return vbk::launch_encode(d_in, n, true, prev, d_out, d_nbytes, static_cast<cudaStream_t>(stream), true);
 }
 
 }  // extern "C"

@@ -44,12 +44,13 @@ size_t stream_workspace_bytes(const uint8_t *in, size_t nbytes);
 // Enough workspace for any single-stream or batched call on nbytes.
 size_t workspace_bound(size_t nbytes);
 // Queue a checked single-stream decode (nbytes > 0) with its scratch in ws
-// (stream_workspace_bytes) and data errors OR-ed into *status.
+// (stream_workspace_bytes) and data errors OR-ed into *status.  rank (delta
+// only): the gaps-minus-one variant, every value plus its rank.
 int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                   uint8_t *ws, uint32_t *status, cudaStream_t s);
+                   uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank = false);
 // The single-stream call with the per-stream workspace.
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                  cudaStream_t s);
+                  cudaStream_t s, bool rank = false);
 // The batched call with the per-stream workspace.
 int launch_decode_batched(const BatchArgs &a, cudaStream_t s);
 // Grow the per-stream workspace of s (current device) for single-stream and

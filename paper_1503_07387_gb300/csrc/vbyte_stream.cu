@@ -501,10 +501,10 @@ __device__ __forceinline__ uint4 staged_quad(const uint32_t *vals, int q)
 // Output quad q holds ranks 4q - SH .. 4q - SH + 3, staged at
 // vals[4q + 4 - SH ..]; quads [qa, qb) are whole (inside the warp's ranks and
 // below `room`, the ranks the output still holds); the ranks outside them
-// are written one per lane.  `add` goes to the ranks below hf (kHf; to all
-// otherwise).
-template <int SH, bool kHf>
-__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, int hf,
+// are written one per lane.  `add` goes to every rank; with kRank the rank
+// itself too, counted from rb (the gaps-minus-one variant).
+template <int SH, bool kRank>
+__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, uint32_t rb,
                                             long long room, int lane)
 {
     constexpr int qa = SH ? 1 : 0;
@@ -513,29 +513,31 @@ __device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, 
 #pragma unroll 2
     for (int q = qa + lane; q < qb; q += kLanes) {
         uint4 e = staged_quad<SH>(vals, q);
-        const int r0 = 4 * q - SH;
-        e.x += (!kHf || r0 < hf) ? add : 0u;
-        e.y += (!kHf || r0 + 1 < hf) ? add : 0u;
-        e.z += (!kHf || r0 + 2 < hf) ? add : 0u;
-        e.w += (!kHf || r0 + 3 < hf) ? add : 0u;
+        const uint32_t a0 = add + (kRank ? rb + static_cast<uint32_t>(4 * q - SH) : 0u);
+        e.x += a0;
+        e.y += a0 + (kRank ? 1u : 0u);
+        e.z += a0 + (kRank ? 2u : 0u);
+        e.w += a0 + (kRank ? 3u : 0u);
         st_quad(oq + 4 * q, e);
     }
     const bool whole = qb > qa;
     const int hb = whole ? min(4 * qa - SH, lim) : lim;   // ranks [0, hb)
     const int tb = whole ? 4 * qb - SH : lim;             // ranks [tb, lim)
-    for (int r = lane; r < hb; r += kLanes) oq[SH + r] = vals[4 + r] + ((!kHf || r < hf) ? add : 0u);
-    for (int r = tb + lane; r < lim; r += kLanes) oq[SH + r] = vals[4 + r] + ((!kHf || r < hf) ? add : 0u);
+    for (int r = lane; r < hb; r += kLanes)
+        oq[SH + r] = vals[4 + r] + add + (kRank ? rb + static_cast<uint32_t>(r) : 0u);
+    for (int r = tb + lane; r < lim; r += kLanes)
+        oq[SH + r] = vals[4 + r] + add + (kRank ? rb + static_cast<uint32_t>(r) : 0u);
 }
 
-template <bool kHf>
-__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, int hf,
+template <bool kRank>
+__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, uint32_t rb,
                                             long long room, int lane, int sh)
 {
     switch (sh) {   // warp-uniform
-    case 0: emit_staged<0, kHf>(oq, vals, wc, add, hf, room, lane); break;
-    case 1: emit_staged<1, kHf>(oq, vals, wc, add, hf, room, lane); break;
-    case 2: emit_staged<2, kHf>(oq, vals, wc, add, hf, room, lane); break;
-    default: emit_staged<3, kHf>(oq, vals, wc, add, hf, room, lane); break;
+    case 0: emit_staged<0, kRank>(oq, vals, wc, add, rb, room, lane); break;
+    case 1: emit_staged<1, kRank>(oq, vals, wc, add, rb, room, lane); break;
+    case 2: emit_staged<2, kRank>(oq, vals, wc, add, rb, room, lane); break;
+    default: emit_staged<3, kRank>(oq, vals, wc, add, rb, room, lane); break;
     }
 }
 
@@ -545,9 +547,10 @@ __device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, 
 // wb + 4Q - SH.  In delta mode the sums before each quad come from two
 // packed warp scans (a quad's sum is at most 4 * 127, so 16 bits hold a
 // warp's prefix).  Quad 0 skips the SH ranks before the warp; lane 31 writes
-// the last SH ranks after quad 127.
-template <int SH, bool kDelta>
-__device__ __forceinline__ void emit_bytes_a(uint32_t *oq, const uint8_t *wb, uint32_t add, int lane)
+// the last SH ranks after quad 127.  With kRank each value also gets its
+// rank, counted from rb.
+template <int SH, bool kDelta, bool kRank>
+__device__ __forceinline__ void emit_bytes_a(uint32_t *oq, const uint8_t *wb, uint32_t add, uint32_t rb, int lane)
 {
     const uint32_t *ww = reinterpret_cast<const uint32_t *>(wb);
     uint32_t x[4], qs[4], P[4];
@@ -583,6 +586,11 @@ __device__ __forceinline__ void emit_bytes_a(uint32_t *oq, const uint8_t *wb, ui
                 e[j] = b + add;
             }
         }
+        if (kRank) {
+            const uint32_t r0 = rb + static_cast<uint32_t>(4 * (32 * m + lane) - SH);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) e[j] += r0 + j;
+        }
         uint32_t *const o = oq + 4 * (32 * m + lane);
         if (SH == 0 || m > 0 || lane > 0) {
             st_quad(o, make_uint4(e[0], e[1], e[2], e[3]));
@@ -597,18 +605,20 @@ __device__ __forceinline__ void emit_bytes_a(uint32_t *oq, const uint8_t *wb, ui
 #pragma unroll
         for (int j = 0; j < SH; ++j) {
             const uint32_t b = (xt >> (8 * j)) & 0xFFu;
+            const uint32_t rk = kRank ? rb + static_cast<uint32_t>(4 * 128 + j - SH) : 0u;
             if (kDelta) {
                 run += b;
-                oq[4 * 128 + j] = run;
+                oq[4 * 128 + j] = run + rk;
             } else {
-                oq[4 * 128 + j] = b + add;
+                oq[4 * 128 + j] = b + add + rk;
             }
         }
     }
 }
 
-// After the middle barrier: this warp's values to the output, coalesced.
-template <bool kDelta>
+// After the middle barrier: this warp's values to the output, coalesced;
+// with kRank each value also gets its global rank (gaps minus one).
+template <bool kDelta, bool kRank>
 __device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const RegA &ra, const uint8_t *bytes)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -626,11 +636,12 @@ __device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const Re
     if (ra.on) {   // warp-uniform
         const uint8_t *wb = bytes + kHalo + warp * kWarpBytes;
         if (G0 + kWarpBytes <= n) {
+            const uint32_t rb = static_cast<uint32_t>(G0);
             switch (sh) {
-            case 0: emit_bytes_a<0, kDelta>(oq, wb, add, lane); break;
-            case 1: emit_bytes_a<1, kDelta>(oq, wb, add, lane); break;
-            case 2: emit_bytes_a<2, kDelta>(oq, wb, add, lane); break;
-            default: emit_bytes_a<3, kDelta>(oq, wb, add, lane); break;
+            case 0: emit_bytes_a<0, kDelta, kRank>(oq, wb, add, rb, lane); break;
+            case 1: emit_bytes_a<1, kDelta, kRank>(oq, wb, add, rb, lane); break;
+            case 2: emit_bytes_a<2, kDelta, kRank>(oq, wb, add, rb, lane); break;
+            default: emit_bytes_a<3, kDelta, kRank>(oq, wb, add, rb, lane); break;
             }
             return;
         }
@@ -653,7 +664,7 @@ __device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const Re
         for (int j = 0; j < 4; ++j) d4[j] = q[j];
         __syncwarp();
     }
-    emit_staged<false>(oq, vals, static_cast<int>(wc), add, 0, n - G0, lane, sh);
+    emit_staged<kRank>(oq, vals, static_cast<int>(wc), add, static_cast<uint32_t>(G0), n - G0, lane, sh);
 }
 
 // After the middle barrier: this warp's values to the output, coalesced.
@@ -890,7 +901,7 @@ __device__ __forceinline__ void check_heads(const Params &p, uint64_t t, SharedS
 
 // ---- kernel
 
-template <bool kDelta, bool kSeg>
+template <bool kDelta, bool kSeg, bool kRank = false>
 __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const Params p)
 {
     using Sm = typename std::conditional<kSeg, SharedS, Shared>::type;
@@ -1018,7 +1029,7 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
                 decode_emit_seg<kDelta>(p, S);
                 if (dheads) check_heads(p, t, S, S.dbytes[b], dha, dhe, S.R0);
             } else {
-                decode_emit<kDelta>(p, S, ra, S.dbytes[b]);
+                decode_emit<kDelta, kRank>(p, S, ra, S.dbytes[b]);
             }
         }
         // did this count complete its chunk?  (read after the emission, so the
@@ -1118,7 +1129,7 @@ size_t stream_workspace_bytes(const uint8_t *in, size_t nbytes)
 }
 
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                  cudaStream_t s)
+                  cudaStream_t s, bool rank)
 {
     if (nbytes == 0 && n == 0) return VBYTE_OK;
     if ((nbytes && !in) || (n && !out)) return VBYTE_EINVAL;
@@ -1128,12 +1139,13 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     if (rc != VBYTE_OK) return rc;
     uint32_t *status = reinterpret_cast<uint32_t *>(ws);
     if (nbytes == 0) return set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s);   // n > 0 from no bytes
-    return enqueue_stream(in, nbytes, out, n, delta, prev, ws, status, s);
+    return enqueue_stream(in, nbytes, out, n, delta, prev, ws, status, s, rank);
 }
 
 int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                   uint8_t *ws, uint32_t *status, cudaStream_t s)
+                   uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank)
 {
+    if (rank && !delta) return VBYTE_EINVAL;
     const uintptr_t a = reinterpret_cast<uintptr_t>(in);
     const uint64_t ntiles = sd::tiles_for(a, nbytes);
     const sd::Layout L = sd::layout(ntiles);
@@ -1160,7 +1172,9 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
     p.lead = std::min<uint64_t>(sd::kChunk + sd::kSlack, ntiles);
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
     if (!sd::tickets_fit(ntiles, p.lead, grid)) return VBYTE_EINVAL;
-    if (delta)
+    if (rank)
+        sd::sdecode_kernel<true, false, true><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    else if (delta)
         sd::sdecode_kernel<true, false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
     else
         sd::sdecode_kernel<false, false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);

@@ -48,6 +48,9 @@ def _signatures(lib):
         "vbyte_max_encoded_size": ([S], S),
         "vbyte_encode": ([P, S, P], S),
         "vbyte_encode_delta": ([P, S, U32, P], S),
+        "vbyte_encode_delta_m1": ([P, S, U32, P], S),
+        "vbyte_encode_delta_m1_device": ([P, S, U32, P, P, P], I),
+        "vbyte_decode_delta_m1": ([P, S, P, S, U32, P], I),
         "vbyte_encode_batched": ([P, P, S, I, P, P, P], S),
         "vbyte_encode_device": ([P, S, P, P, P], I),
         "vbyte_encode_delta_device": ([P, S, U32, P, P, P], I),
@@ -165,11 +168,22 @@ def _device_args(data, n, out):
     return out
 
 
-def encode_device(values, delta: bool = False, prev: int = 0, out=None, nbytes=None, stream=None):
+def encode_delta_m1(values, prev: int = 0) -> np.ndarray:
+    """Host encoding of the gaps-minus-one variant: x_0 - prev, then
+    x_i - x_{i-1} - 1 (mod 2^32)."""
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    out = np.empty(max(5 * v.size, 1), dtype=np.uint8)
+    nb = load().vbyte_encode_delta_m1(_np_ptr(v), v.size, ctypes.c_uint32(prev & 0xFFFFFFFF), _np_ptr(out))
+    return out[:nb]
+
+
+def encode_device(values, delta: bool = False, prev: int = 0, out=None, nbytes=None, stream=None,
+                  minus_one: bool = False):
     """Encode the CUDA uint32/int32 tensor `values` on the device (delta: its
-    gaps from prev).  Returns (out, nbytes): `out` is a uint8 tensor of
-    5 * n bytes whose first nbytes hold the encoding, `nbytes` a one-element
-    int64 CUDA tensor written when the stream gets there (no synchronisation)."""
+    gaps from prev; minus_one: every gap after the first one less).  Returns
+    (out, nbytes): `out` is a uint8 tensor of 5 * n bytes whose first nbytes
+    hold the encoding, `nbytes` a one-element int64 CUDA tensor written when
+    the stream gets there (no synchronisation)."""
     import torch
     if not isinstance(values, torch.Tensor) or not values.is_cuda or not values.is_contiguous() \
             or values.dtype not in (torch.int32, torch.uint32):
@@ -182,6 +196,12 @@ def encode_device(values, delta: bool = False, prev: int = 0, out=None, nbytes=N
     if nbytes is None:
         nbytes = torch.empty(1, dtype=torch.int64, device=values.device)
     lib, st = load(), _stream_handle(stream)
+    if minus_one:
+        rc = lib.vbyte_encode_delta_m1_device(ctypes.c_void_p(values.data_ptr()), n,
+                                              ctypes.c_uint32(prev & 0xFFFFFFFF), ctypes.c_void_p(out.data_ptr()),
+                                              ctypes.c_void_p(nbytes.data_ptr()), st)
+        _check(rc, "vbyte_encode_delta_m1_device")
+        return out, nbytes
     if delta:
         rc = lib.vbyte_encode_delta_device(ctypes.c_void_p(values.data_ptr()), n, ctypes.c_uint32(prev & 0xFFFFFFFF),
                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(nbytes.data_ptr()), st)
@@ -208,6 +228,17 @@ def decode_delta(data, n: int, prev: int = 0, out=None, stream=None):
                                    ctypes.c_void_p(out.data_ptr()), n,
                                    ctypes.c_uint32(prev & 0xFFFFFFFF), _stream_handle(stream))
     _check(rc, "vbyte_decode_delta")
+    return out
+
+
+def decode_delta_m1(data, n: int, prev: int = 0, out=None, stream=None):
+    """Decode the gaps-minus-one variant: prefix sums from prev plus each
+    value's rank (uint32 wrap-around)."""
+    out = _device_args(data, n, out)
+    rc = load().vbyte_decode_delta_m1(ctypes.c_void_p(data.data_ptr()), data.numel(),
+                                      ctypes.c_void_p(out.data_ptr()), n,
+                                      ctypes.c_uint32(prev & 0xFFFFFFFF), _stream_handle(stream))
+    _check(rc, "vbyte_decode_delta_m1")
     return out
 
 
