@@ -93,13 +93,16 @@ def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
     return ws * units_per_rank / seconds / 1e9
 
 
+# the translation unit of the decode kernels and every header it includes
+KERNEL_SOURCES = ["paper_1503_07387_gb300/csrc/vbyte_stream.cu", "paper_1503_07387_gb300/csrc/vbyte_device.cuh",
+                  "paper_1503_07387_gb300/csrc/vbyte_internal.h", "include/vbyte.h"]
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1503_07387_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for rel in KERNEL_SOURCES:
+        h.update(os.path.basename(rel).encode())
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()[:16]
 
 

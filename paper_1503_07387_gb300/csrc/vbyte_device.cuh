@@ -124,23 +124,6 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
     return x;
 }
 
-__device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t x, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(~0u, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
-__device__ __forceinline__ uint64_t warp_sum64(uint64_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
-    return v;
-}
-
 __device__ __forceinline__ uint32_t byte_sum4(uint4 w)
 {
     return __dp4a(w.x, 0x01010101u, __dp4a(w.y, 0x01010101u, __dp4a(w.z, 0x01010101u,
@@ -273,28 +256,6 @@ __device__ __forceinline__ uint32_t sum_le2_fast(uint4 w, uint32_t wprev)
     return s + 127u * hi;
 }
 
-// Per-thread count and (delta) value sum of the integers ending in its slice.
-template <bool kDelta>
-__device__ __forceinline__ void slice_count_sum(const SliceMasks &m, const uint32_t *sw, int tid, bool interior,
-                                                uint32_t &cnt, uint32_t &vsum, bool &notB)
-{
-    cnt = __popc(m.tc);
-    const uint32_t c20 = ~m.t20 & 0xFFFFFu;   // continuation bytes
-    const bool notA = !interior || (c20 & 0xFFFF8u);
-    notB = (c20 & (c20 << 1) & 0xFFFF8u) != 0;
-    vsum = 0;
-    if (kDelta) {
-        if (!notA) {
-            vsum = byte_sum4(m.w);
-        } else if (!notB) {
-            vsum = interior ? sum_le2_fast(m.w, m.wprev) : sum_le2(m.w, m.wprev, m.tc);
-        } else {
-            assemble_all(sw, tid, m.tl, m.t20, m.tc, [&](uint32_t v) { vsum += v; });
-        }
-    }
-}
-
-
 // ---- list heads (batched decoding) ---------------------------------------
 constexpr int kHeadTile = 4096;                          // tile bytes of the decoders using these
 constexpr int kHeadBack = 8;                             // window start before a tile or slice
@@ -369,28 +330,6 @@ __device__ __forceinline__ void fill_heads(const HeadSrc &p, long long trel, uin
             if (want_vo) T.vo[i] = p.vo[j];
         }
     }
-}
-
-// Fill T for the tile starting at stream offset trel.  All threads take part.
-__device__ __forceinline__ void build_heads(const HeadSrc &p, long long trel, uint64_t ha, uint64_t he, HeadTab &T,
-                                            bool want_prev, bool want_vo)
-{
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kHeadWords; i += static_cast<int>(blockDim.x)) T.bits[i] = 0u;
-    __syncthreads();
-    const long long w0 = trel - kHalo;
-    const uint64_t nh = he - ha;
-    for (uint64_t i = tid; i < nh; i += blockDim.x) {
-        const uint64_t j = ha + i;
-        const long long d = static_cast<long long>(p.bo[j]) - w0;
-        if (d >= 0 && d < kHalo + kHeadTile) atomicOr(T.bits + (d >> 5), 1u << (d & 31));
-        if (i < static_cast<uint64_t>(kMaxHeadList)) {
-            T.pos[i] = d < 0 ? -1 : (d > (1 << 30) ? (1 << 30) : static_cast<int>(d));
-            if (want_prev) T.prv[i] = p.prevs ? p.prevs[j] : 0u;
-            if (want_vo) T.vo[i] = p.vo[j];
-        }
-    }
-    __syncthreads();
 }
 
 // Index of the last table entry whose staging index is <= q (-1 if none).
