@@ -484,10 +484,10 @@ def run_serving(args, pool):
     scheduled arrival to the scheduler seeing its batch complete."""
     import torch
     from paper_1503_07387_gb300 import vbyte
-    # a query's output is about 27 MB (lists drawn in proportion to length),
-    # so the arena bounds how many queries are in flight
+    # a query's output is about 27 MB (lists drawn in proportion to length):
+    # 8 GiB holds four full batches of 64 queries in flight
     free, _ = torch.cuda.mem_get_info()
-    arena = int(min(free * 0.25, 32 << 30)) // 4096 * 4096
+    arena = int(min(free * 0.25, 8 << 30)) // 4096 * 4096
     cfg = dict(arena_bytes=arena, staging_bytes=512 << 20, max_inflight=4, max_batch_queries=64,
                max_batch_lists=512)
     rows = []
