@@ -220,6 +220,22 @@ def test_decode_host_round_trip():
     assert vbyte.get_status() == 0
 
 
+@pytest.mark.parametrize("off", [0, 1, 3])
+def test_decode_host_into_page_locked_output(off):
+    """Page-locked output (the form bench.py's end-to-end number uses): same
+    values, and the words around the output untouched (offset views)."""
+    v = inputs.one_two_byte_mix(200_003, seed=off)
+    data = oracle.encode_delta(np.cumsum(v.astype(np.uint64)).astype(np.uint32))
+    n = v.size
+    pinned = torch.full((n + 8,), 0x3C3C3C3C, dtype=torch.int32).pin_memory()
+    h = pinned.numpy().view(np.uint32)
+    out = h[off:off + n]
+    vbyte.decode_host(data, n, delta=True, prev=0, out=out)
+    assert vbyte.get_status() == 0
+    assert np.array_equal(out, oracle.decode_delta(data, prev=0))
+    assert np.all(h[:off] == 0x3C3C3C3C) and np.all(h[off + n:] == 0x3C3C3C3C)
+
+
 def test_two_streams_independent():
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     v1 = inputs.uniform_bits(200_000, seed=1)
