@@ -339,6 +339,7 @@ def run_gpu(args):
             "unit": "GB/s",
             "frac": round(achieved / peak_gbs, 4),
             "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
+            "frac_of_nominal_8000_gbs": round(achieved / 8000.0, 4),
             "traffic": traffic,
             "kernel": "sdecode_kernel<delta>" if all(s["delta"] for s in streams) else "sdecode_kernel",
             "algorithmic_bytes_per_launch": bytes_per_launch,
