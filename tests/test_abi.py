@@ -60,3 +60,32 @@ def test_host_delta_and_batched_encoders_match_oracle():
         b1, o1 = vbyte.encode_batched(ids, vo, delta, prev if delta else None)
         b2, o2 = oracle.encode_batched(ids, vo, delta, prev if delta else None)
         assert np.array_equal(b1, b2) and np.array_equal(o1, o2)
+
+
+def test_host_m1_encoder_matches_oracle():
+    rng = np.random.default_rng(4)
+    x = np.sort(rng.choice(1 << 31, 50_000, replace=False)).astype(np.uint32)
+    for prev in (0, 5, 2**32 - 1):
+        assert np.array_equal(vbyte.encode_delta_m1(x, prev=prev), oracle.encode_delta_m1(x, prev=prev))
+    assert vbyte.encode_delta_m1(np.zeros(0, np.uint32)).size == 0
+
+
+def test_argument_errors_before_any_device_work():
+    """Null or misaligned arguments are refused on the host (no CUDA call is
+    reached), so these run without a GPU."""
+    lib = vbyte.load()
+    P = ctypes.c_void_p
+    einval = 1
+    # a null input with bytes, a null output with values
+    assert lib.vbyte_decode(None, 16, P(16), 4, None) == einval
+    assert lib.vbyte_decode(P(16), 16, None, 4, None) == einval
+    assert lib.vbyte_decode_delta(None, 16, P(16), 4, 0, None) == einval
+    assert lib.vbyte_decode_delta_m1(None, 16, P(16), 4, 0, None) == einval
+    # an output that is not 4-byte aligned
+    assert lib.vbyte_decode(P(16), 16, P(18), 4, None) == einval
+    # the device encoder: misaligned input, null count word
+    assert lib.vbyte_encode_device(P(18), 4, P(64), P(128), None) == einval
+    assert lib.vbyte_encode_device(P(16), 4, P(64), None, None) == einval
+    assert lib.vbyte_encode_delta_m1_device(None, 4, 0, P(64), P(128), None) == einval
+    # plans and servers need their out-parameters
+    assert lib.vbyte_plan_create(None, P(16), 16, P(16), P(16), 4, P(16), 1, None, 0, 0, None) == einval
