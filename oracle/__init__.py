@@ -66,6 +66,19 @@ def _load():
     lib.oracle_decode_delta_m1.restype = S
     lib.oracle_validate.argtypes = [P, S, S]
     lib.oracle_validate.restype = U32
+    U64 = ctypes.c_uint64
+    lib.oracle_encode64_one.argtypes = [U64, P]
+    lib.oracle_encode64_one.restype = S
+    lib.oracle_encode64.argtypes = [P, S, P]
+    lib.oracle_encode64.restype = S
+    lib.oracle_encode_delta64.argtypes = [P, S, U64, P]
+    lib.oracle_encode_delta64.restype = S
+    lib.oracle_decode64.argtypes = [P, S, P, S]
+    lib.oracle_decode64.restype = S
+    lib.oracle_decode_delta64.argtypes = [P, S, P, S, U64]
+    lib.oracle_decode_delta64.restype = S
+    lib.oracle_validate64.argtypes = [P, S, S]
+    lib.oracle_validate64.restype = U32
     lib.oracle_decode_batched.argtypes = [P, P, P, S, ctypes.c_int, P, P]
     lib.oracle_decode_batched.restype = U32
     lib.oracle_encode_batched.argtypes = [P, P, S, ctypes.c_int, P, P, P]
@@ -155,6 +168,61 @@ def validate(data, n: int) -> int:
     """Status bits of the data-error contract for a stream expected to hold n values."""
     b = _u8(data)
     return int(_load().oracle_validate(_ptr(b), b.size, n))
+
+
+MASK64 = (1 << 64) - 1
+
+
+def encode64(values) -> np.ndarray:
+    """VByte-encode uint64 values (Sec. 1: the format read for 64-bit
+    integers, up to ten bytes each)."""
+    v = np.ascontiguousarray(values, dtype=np.uint64)
+    out = np.empty(10 * v.size, dtype=np.uint8)
+    nb = _load().oracle_encode64(_ptr(v), v.size, _ptr(out))
+    return out[:nb].copy()
+
+
+def encode_delta64(values, prev: int = 0) -> np.ndarray:
+    """Encode the gaps x_i - x_{i-1} (mod 2^64), x_0 = prev."""
+    v = np.ascontiguousarray(values, dtype=np.uint64)
+    out = np.empty(10 * v.size, dtype=np.uint8)
+    nb = _load().oracle_encode_delta64(_ptr(v), v.size, ctypes.c_uint64(prev & MASK64), _ptr(out))
+    return out[:nb].copy()
+
+
+def _decode64(fn, data, n, *extra):
+    b = _u8(data)
+    cap = b.size if n is None else max(n, 0)
+    out = np.empty(max(cap, 1), dtype=np.uint64)
+    cnt = fn(_ptr(b), b.size, _ptr(out), cap, *extra)
+    if cnt > cap:
+        out = np.empty(cnt, dtype=np.uint64)
+        cnt = fn(_ptr(b), b.size, _ptr(out), cnt, *extra)
+    return out[:cnt].copy()
+
+
+def decode64(data, n: int | None = None) -> np.ndarray:
+    """Algorithm 1 read for uint64 (ten steps, the tenth byte taken whole)."""
+    return _decode64(_load().oracle_decode64, data, n)
+
+
+def decode_delta64(data, n: int | None = None, prev: int = 0) -> np.ndarray:
+    """decode64 with the running sum from prev (uint64 wrap-around)."""
+    return _decode64(_load().oracle_decode_delta64, data, n, ctypes.c_uint64(prev & MASK64))
+
+
+def validate64(data, n: int) -> int:
+    """The data-error contract for uint64 streams: a run of ten or more bytes
+    with the high bit set, a final byte with it set, a terminator count other
+    than n."""
+    b = _u8(data)
+    return int(_load().oracle_validate64(_ptr(b), b.size, n))
+
+
+def encode64_one(v: int) -> bytes:
+    buf = (ctypes.c_uint8 * 10)()
+    k = _load().oracle_encode64_one(ctypes.c_uint64(v & MASK64), buf)
+    return bytes(buf[:k])
 
 
 def encode_batched(values, val_off, delta: bool, prev=None):

@@ -20,6 +20,9 @@
  *     without repeated values that Sec. 1 also names, which stores the first
  *     gap as is and every later one minus one (x_1 - x_0, x_2 - x_1 - 1, ...),
  *     undone by adding one more for every value after the first;
+ *   - 64-bit integers, which Sec. 1 says the format also covers: the same
+ *     rules read for uint64 (up to ten bytes, Algorithm 1 with ten steps,
+ *     the tenth byte taken without testing its high bit);
  *   - validation: a separate pass that states the data-error contract
  *     (a run of five or more bytes with the high bit set; a final byte with
  *     the high bit set; a terminator count that differs from the expected
@@ -169,6 +172,105 @@ uint32_t oracle_validate(const uint8_t *in, size_t nbytes, size_t n)
     for (size_t i = 0; i < nbytes; ++i) {
         if (in[i] & 128u) {
             if (++run >= 5) st |= ORACLE_ERR_MALFORMED_LONG;
+        } else {
+            run = 0;
+            ++terminators;
+        }
+    }
+    if (nbytes > 0 && (in[nbytes - 1] & 128u)) st |= ORACLE_ERR_TRUNCATED;
+    if (terminators != n) st |= ORACLE_ERR_COUNT_MISMATCH;
+    return st;
+}
+
+/* ---------------------------------------------------------------- 64-bit -- */
+
+/* Sec. 1 notes that the format applies to 64-bit integers as well.  The same
+ * rules, read for uint64: seven bits per byte from the least significant
+ * end, so a value takes 1 + [v >= 2^7] + ... + [v >= 2^63] bytes (at most
+ * ten); the decoder follows Algorithm 1 with ten steps instead of five, the
+ * tenth byte taken without testing its high bit and multiplied by 2^63
+ * modulo 2^64; a run of ten or more bytes with the high bit set is
+ * malformed. */
+size_t oracle_encode64_one(uint64_t v, uint8_t *out)
+{
+    size_t k = 0;
+    while (v >= 128u) {
+        out[k++] = (uint8_t)((v & 127u) | 128u);
+        v >>= 7;
+    }
+    out[k++] = (uint8_t)v;
+    return k;
+}
+
+size_t oracle_encode64(const uint64_t *in, size_t n, uint8_t *out)
+{
+    size_t w = 0;
+    for (size_t i = 0; i < n; ++i) w += oracle_encode64_one(in[i], out + w);
+    return w;
+}
+
+size_t oracle_encode_delta64(const uint64_t *in, size_t n, uint64_t prev, uint8_t *out)
+{
+    size_t w = 0;
+    for (size_t i = 0; i < n; ++i) {
+        w += oracle_encode64_one(in[i] - prev, out + w);
+        prev = in[i];
+    }
+    return w;
+}
+
+/* Algorithm 1 for uint64: read a byte; while its high bit is set and fewer
+ * than ten bytes of this integer were read, add its seven bits at the next
+ * position and read another; the last byte read goes in whole (the tenth:
+ * b * 2^63 modulo 2^64).  delta != 0: running sum from prev.  A partial
+ * integer at the end is dropped. */
+static size_t algorithm1_64(const uint8_t *in, size_t nbytes, uint64_t *y, size_t cap, int delta,
+                            uint64_t prev)
+{
+    size_t pos = 0, count = 0;
+    uint64_t p = prev;
+    while (pos < nbytes) {
+        uint64_t c = 0;
+        int k = 0;
+        int complete = 0;
+        while (pos < nbytes) {
+            const uint64_t b = in[pos++];
+            if (b < 128u || k == 9) {
+                c += b << (7 * k);
+                complete = 1;
+                break;
+            }
+            c += (b & 127u) << (7 * k);
+            ++k;
+        }
+        if (!complete) break;
+        if (delta) {
+            p += c;
+            c = p;
+        }
+        if (count < cap) y[count] = c;
+        ++count;
+    }
+    return count;
+}
+
+size_t oracle_decode64(const uint8_t *in, size_t nbytes, uint64_t *out, size_t cap)
+{
+    return algorithm1_64(in, nbytes, out, cap, 0, 0u);
+}
+
+size_t oracle_decode_delta64(const uint8_t *in, size_t nbytes, uint64_t *out, size_t cap, uint64_t prev)
+{
+    return algorithm1_64(in, nbytes, out, cap, 1, prev);
+}
+
+uint32_t oracle_validate64(const uint8_t *in, size_t nbytes, size_t n)
+{
+    uint32_t st = 0;
+    size_t run = 0, terminators = 0;
+    for (size_t i = 0; i < nbytes; ++i) {
+        if (in[i] & 128u) {
+            if (++run >= 10) st |= ORACLE_ERR_MALFORMED_LONG;
         } else {
             run = 0;
             ++terminators;

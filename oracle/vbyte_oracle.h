@@ -36,6 +36,14 @@ size_t oracle_decode_delta(const uint8_t *in, size_t nbytes, uint32_t *out,
                            size_t cap, uint32_t prev);
 uint32_t oracle_validate(const uint8_t *in, size_t nbytes, size_t n);
 
+size_t oracle_encode64_one(uint64_t v, uint8_t *out);
+size_t oracle_encode64(const uint64_t *in, size_t n, uint8_t *out);
+size_t oracle_encode_delta64(const uint64_t *in, size_t n, uint64_t prev, uint8_t *out);
+size_t oracle_decode64(const uint8_t *in, size_t nbytes, uint64_t *out, size_t cap);
+size_t oracle_decode_delta64(const uint8_t *in, size_t nbytes, uint64_t *out, size_t cap,
+                             uint64_t prev);
+uint32_t oracle_validate64(const uint8_t *in, size_t nbytes, size_t n);
+
 uint32_t oracle_decode_batched(const uint8_t *in, const uint64_t *byte_off,
                                const uint64_t *val_off, size_t num_lists,
                                int delta, const uint32_t *prev, uint32_t *out);

@@ -280,3 +280,102 @@ def test_batched_count_mismatch_per_list():
     vo = np.array([0, 2, 3], dtype=np.uint64)   # list 0 claims 2 values, holds 1
     _, st = oracle.decode_batched(enc, bo, vo, delta=False)
     assert st == oracle.ERR_COUNT_MISMATCH
+
+
+# ----------------------------------------------------------- 64-bit integers --
+# Sec. 1 notes that the format applies to 64-bit integers too.  The 64-bit
+# oracle is pinned to the same definition: seven bits per byte from the least
+# significant end, so up to ten bytes; Algorithm 1 with ten steps.
+
+MASK64 = (1 << 64) - 1
+
+
+def _length64(v):
+    """1 + [v >= 2^7] + [v >= 2^14] + ... + [v >= 2^63], with Python ints."""
+    return 1 + sum(v >= 1 << (7 * k) for k in range(1, 10))
+
+
+@pytest.mark.parametrize("k", range(10))
+def test64_powers_of_128(k):
+    v = 1 << (7 * k)
+    assert oracle.encode64_one(v) == b"\x80" * k + b"\x01"
+    assert oracle.decode64(b"\x80" * k + b"\x01").tolist() == [v]
+
+
+@pytest.mark.parametrize("k", range(1, 10))
+def test64_powers_of_128_minus_one(k):
+    v = (1 << (7 * k)) - 1
+    assert oracle.encode64_one(v) == b"\xff" * (k - 1) + b"\x7f"
+    assert oracle.decode64(b"\xff" * (k - 1) + b"\x7f").tolist() == [v]
+
+
+def test64_max():
+    """2^64 - 1: nine full groups, then the top bit alone, 0x01."""
+    assert oracle.encode64_one(MASK64) == b"\xff" * 9 + b"\x01"
+    assert oracle.decode64(b"\xff" * 9 + b"\x01").tolist() == [MASK64]
+
+
+def test64_group_sum_and_length_every_width():
+    """For values of every bit width 0..64, the bytes satisfy
+    v = sum (b_k mod 128) 2^(7k), the length closed form, and the
+    continuation bits, checked with Python integers."""
+    rng = np.random.default_rng(17)
+    vals = [0, 1, MASK64]
+    for bits in range(1, 65):
+        top = 1 << (bits - 1)
+        vals += [top, (top << 1) - 1] + [top | int(x) for x in rng.integers(0, top, 40, dtype=np.uint64)]
+    for v in vals:
+        bs = oracle.encode64_one(v)
+        assert len(bs) == _length64(v), v
+        assert sum((b & 127) << (7 * k) for k, b in enumerate(bs)) == v
+        assert all(b & 128 for b in bs[:-1]) and not bs[-1] & 128
+    arr = np.array(vals, dtype=np.uint64)
+    enc = oracle.encode64(arr)
+    assert enc.size == sum(_length64(v) for v in vals)
+    assert np.array_equal(oracle.decode64(enc), arr)
+
+
+def test64_agrees_with_32_bit_below_2_32():
+    """Below 2^32 the 64-bit form is the 32-bit one, byte for byte."""
+    v = inputs.uniform_bits(100_000, seed=5)
+    enc = oracle.encode(v)
+    assert np.array_equal(oracle.encode64(v.astype(np.uint64)), enc)
+    assert np.array_equal(oracle.decode64(enc), v.astype(np.uint64))
+
+
+def test64_tenth_byte_taken_whole():
+    """The tenth byte is the last of an integer whatever its high bit; only
+    its low bit survives the multiplication by 2^63 modulo 2^64."""
+    assert oracle.decode64(b"\x80" * 9 + b"\x7f").tolist() == [1 << 63]
+    assert oracle.decode64(b"\x80" * 9 + b"\xff\x05").tolist() == [1 << 63, 5]
+    assert oracle.validate64(b"\x80" * 9 + b"\xff\x05", 2) & oracle.ERR_MALFORMED_LONG
+    assert oracle.validate64(b"\x80" * 9 + b"\x01", 1) == 0
+    assert oracle.validate64(b"\x80" * 10 + b"\x01", 1) & oracle.ERR_MALFORMED_LONG
+    # five continuation bytes, malformed for uint32, are fine here
+    assert oracle.validate64(b"\x80" * 5 + b"\x01", 1) == 0
+    assert oracle.decode64(b"\x80" * 5 + b"\x01").tolist() == [1 << 35]
+
+
+def test64_truncated_and_count():
+    assert oracle.decode64(b"\x05\x80\x80").tolist() == [5]
+    assert oracle.validate64(b"\x05\x80", 1) == oracle.ERR_TRUNCATED
+    assert oracle.validate64(b"\x01\x02", 3) == oracle.ERR_COUNT_MISMATCH
+    assert oracle.decode64(b"").tolist() == [] and oracle.validate64(b"", 0) == 0
+
+
+def test64_delta_wraps_modulo_2_64():
+    """Differential coding on uint64: the decoded values are numpy's uint64
+    cumulative sum of the stored gaps from prev, wrapping modulo 2^64."""
+    rng = np.random.default_rng(9)
+    x = rng.integers(0, 1 << 63, 50_000, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, 50_000, dtype=np.uint64)
+    for prev in (0, MASK64, 1 << 40):
+        enc = oracle.encode_delta64(x, prev=prev)
+        gaps = oracle.decode64(enc)
+        with np.errstate(over="ignore"):
+            assert np.array_equal(gaps, x - np.concatenate([[np.uint64(prev)], x[:-1]]))
+            assert np.array_equal(np.cumsum(np.concatenate([[np.uint64(prev)], gaps]))[1:], x)
+        assert np.array_equal(oracle.decode_delta64(enc, x.size, prev=prev), x)
+    ids = np.cumsum(inputs.geometric_gaps(100_000, seed=2).astype(np.uint64)) + np.uint64(1 << 40)
+    enc = oracle.encode_delta64(ids)
+    assert enc.size == sum(_length64(int(g)) for g in np.diff(np.concatenate([[0], ids])).tolist())
+    assert np.array_equal(oracle.decode_delta64(enc, ids.size), ids)
