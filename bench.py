@@ -98,11 +98,19 @@ KERNEL_SOURCES = ["paper_1503_07387_gb300/csrc/vbyte_stream.cu", "paper_1503_073
                   "paper_1503_07387_gb300/csrc/vbyte_internal.h", "include/vbyte.h"]
 
 
+def _code_only(src: str) -> str:
+    """The source with its comments removed and its whitespace collapsed, so
+    that editing a comment does not invalidate a profile of unchanged code."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
         h.update(os.path.basename(rel).encode())
-        h.update(open(os.path.join(ROOT, rel), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, rel)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -23,8 +23,9 @@
  *     stream).  Device work is queued on it and the call returns without
  *     synchronising, except where an entry point says otherwise.
  *   - The library keeps one small workspace per (device, stream): a status
- *     word, a tile counter and the look-back descriptors of the single-pass
- *     scan (16 bytes per 4 KiB of input).  It grows on demand with
+ *     word, tile and chunk counters, and the per-tile descriptors through
+ *     which the CTAs pass counts and running sums to one another (16 bytes
+ *     per 4 KiB of input).  It grows on demand with
  *     cudaMallocAsync on that stream; a call made while the stream is being
  *     captured into a CUDA graph never allocates and returns VBYTE_ENOMEM if
  *     the workspace is too small (run the same call once before capture).
@@ -62,8 +63,8 @@ extern "C" {
 /* The number of terminator bytes (high bit clear) differs from the expected
  * count n (or from val_off[j+1]-val_off[j] for list j). */
 #define VBYTE_ERR_COUNT_MISMATCH 4u
-/* A cross-tile look-back wait gave up after its time limit (about two
- * seconds); the outputs of that call are unspecified. */
+/* A wait on another tile's count or running sum gave up after its time
+ * limit (about two seconds); the outputs of that call are unspecified. */
 #define VBYTE_ERR_TIMEOUT 8u
 /* Batched calls: the offset arrays break their contract (not non-decreasing,
  * or not running from 0 to nbytes and from 0 to n). */
@@ -315,7 +316,7 @@ int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out,
  * or vbyte_decode_delta (delta != 0, from prev) and calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *
- * Scratch: the look-back descriptors live in one file-scope __device__ array
+ * Scratch: the per-tile descriptors live in one file-scope __device__ array
  * in the library, shared by every call on a device.  The first call on each
  * device (with that device current) looks up that array's address with
  * cudaGetSymbolAddress and the device's SM count; make that first call
