@@ -66,6 +66,10 @@ def _load():
     lib.oracle_decode_delta_m1.restype = S
     lib.oracle_validate.argtypes = [P, S, S]
     lib.oracle_validate.restype = U32
+    lib.oracle_encode_delta4.argtypes = [P, S, P, P]
+    lib.oracle_encode_delta4.restype = S
+    lib.oracle_decode_delta4.argtypes = [P, S, P, S, P]
+    lib.oracle_decode_delta4.restype = S
     U64 = ctypes.c_uint64
     lib.oracle_encode64_one.argtypes = [U64, P]
     lib.oracle_encode64_one.restype = S
@@ -168,6 +172,39 @@ def validate(data, n: int) -> int:
     """Status bits of the data-error contract for a stream expected to hold n values."""
     b = _u8(data)
     return int(_load().oracle_validate(_ptr(b), b.size, n))
+
+
+def _prev4(prev4):
+    if prev4 is None:
+        return None
+    p = np.ascontiguousarray(prev4, dtype=np.uint32)
+    if p.size != 4:
+        raise ValueError("prev4 holds the four values before the list")
+    return p
+
+
+def encode_delta4(values, prev4=None) -> np.ndarray:
+    """The blocked differences of Sec. 1: x_i - x_{i-4} (mod 2^32), the four
+    values before the list being prev4 (zeros: the paper's x_1..x_4 as is)."""
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    p = _prev4(prev4)
+    out = np.empty(5 * v.size, dtype=np.uint8)
+    nb = _load().oracle_encode_delta4(_ptr(v), v.size, None if p is None else _ptr(p), _ptr(out))
+    return out[:nb].copy()
+
+
+def decode_delta4(data, n: int | None = None, prev4=None) -> np.ndarray:
+    """Algorithm 1, then x_i = g_i + x_{i-4} (mod 2^32)."""
+    b = _u8(data)
+    p = _prev4(prev4)
+    cap = b.size if n is None else max(n, 0)
+    out = np.empty(max(cap, 1), dtype=np.uint32)
+    pp = None if p is None else _ptr(p)
+    cnt = _load().oracle_decode_delta4(_ptr(b), b.size, _ptr(out), cap, pp)
+    if cnt > cap:
+        out = np.empty(cnt, dtype=np.uint32)
+        cnt = _load().oracle_decode_delta4(_ptr(b), b.size, _ptr(out), cnt, pp)
+    return out[:cnt].copy()
 
 
 MASK64 = (1 << 64) - 1

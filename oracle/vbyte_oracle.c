@@ -20,6 +20,9 @@
  *     without repeated values that Sec. 1 also names, which stores the first
  *     gap as is and every later one minus one (x_1 - x_0, x_2 - x_1 - 1, ...),
  *     undone by adding one more for every value after the first;
+ *     The blocked variant Sec. 1 names as well (x_1..x_4, then x_i - x_{i-4})
+ *     is undone by adding, to each decoded difference, the value four
+ *     places before it;
  *   - 64-bit integers, which Sec. 1 says the format also covers: the same
  *     rules read for uint64 (up to ten bytes, Algorithm 1 with ten steps,
  *     the tenth byte taken without testing its high bit);
@@ -180,6 +183,39 @@ uint32_t oracle_validate(const uint8_t *in, size_t nbytes, size_t n)
     if (nbytes > 0 && (in[nbytes - 1] & 128u)) st |= ORACLE_ERR_TRUNCATED;
     if (terminators != n) st |= ORACLE_ERR_COUNT_MISMATCH;
     return st;
+}
+
+/* ------------------------------------------------ blocked differences -- */
+
+/* Sec. 1 "Differential coding" also names differences taken across blocks
+ * of four for speed: x_1, x_2, x_3, x_4, x_5 - x_1, x_6 - x_2, ...  Written
+ * with a seed: value i (from 0) is stored as x_i - x_{i-4} modulo 2^32,
+ * where x_{-4}, x_{-3}, x_{-2}, x_{-1} are prev4[0..3] (all zero when prev4
+ * is NULL, which gives the paper's list). */
+size_t oracle_encode_delta4(const uint32_t *in, size_t n, const uint32_t *prev4, uint8_t *out)
+{
+    size_t w = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const uint32_t before = i >= 4 ? in[i - 4] : (prev4 ? prev4[i] : 0u);
+        w += oracle_encode_one(in[i] - before, out + w);
+    }
+    return w;
+}
+
+/* Algorithm 1 gives the stored differences g_i; then x_i = g_i + x_{i-4}
+ * modulo 2^32, in order, with the same seed.  Returns Algorithm 1's count;
+ * values beyond cap are not stored (and not needed: x_i depends only on
+ * earlier values). */
+size_t oracle_decode_delta4(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
+                            const uint32_t *prev4)
+{
+    const size_t count = algorithm1(in, nbytes, out, cap, 0, 0u);
+    const size_t m = count < cap ? count : cap;
+    for (size_t i = 0; i < m; ++i) {
+        const uint32_t before = i >= 4 ? out[i - 4] : (prev4 ? prev4[i] : 0u);
+        out[i] = out[i] + before;
+    }
+    return count;
 }
 
 /* ---------------------------------------------------------------- 64-bit -- */

@@ -36,6 +36,10 @@ size_t oracle_decode_delta(const uint8_t *in, size_t nbytes, uint32_t *out,
                            size_t cap, uint32_t prev);
 uint32_t oracle_validate(const uint8_t *in, size_t nbytes, size_t n);
 
+size_t oracle_encode_delta4(const uint32_t *in, size_t n, const uint32_t *prev4, uint8_t *out);
+size_t oracle_decode_delta4(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
+                            const uint32_t *prev4);
+
 size_t oracle_encode64_one(uint64_t v, uint8_t *out);
 size_t oracle_encode64(const uint64_t *in, size_t n, uint8_t *out);
 size_t oracle_encode_delta64(const uint64_t *in, size_t n, uint64_t prev, uint8_t *out);

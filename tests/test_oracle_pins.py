@@ -379,3 +379,53 @@ def test64_delta_wraps_modulo_2_64():
     enc = oracle.encode_delta64(ids)
     assert enc.size == sum(_length64(int(g)) for g in np.diff(np.concatenate([[0], ids])).tolist())
     assert np.array_equal(oracle.decode_delta64(enc, ids.size), ids)
+
+
+# ------------------------------------------------------ blocked differences --
+# Sec. 1: x_1, x_2, x_3, x_4, x_5 - x_1, x_6 - x_2, x_7 - x_3, x_8 - x_4, ...
+
+def test_delta4_paper_form():
+    """The stored integers are the paper's list for a small example."""
+    x = np.array([3, 10, 20, 21, 40, 41, 60, 100, 107], dtype=np.uint32)
+    g = oracle.decode(oracle.encode_delta4(x))
+    assert g.tolist() == [3, 10, 20, 21, 40 - 3, 41 - 10, 60 - 20, 100 - 21, 107 - 40]
+    assert oracle.decode_delta4(oracle.encode_delta4(x)).tolist() == x.tolist()
+
+
+def test_delta4_lanes_are_numpy_cumsums():
+    """Each residue class mod 4 of the decoded list is numpy's cumulative sum
+    (mod 2^32) of that class's stored integers, from its seed."""
+    rng = np.random.default_rng(21)
+    g = rng.integers(0, 1 << 32, 40_003, dtype=np.uint64).astype(np.uint32)
+    data = oracle.encode(g)
+    for prev4 in (None, [5, 0xFFFFFFFF, 7, 1 << 31]):
+        x = oracle.decode_delta4(data, g.size, prev4=prev4)
+        seeds = [0, 0, 0, 0] if prev4 is None else prev4
+        for r in range(4):
+            want = (np.cumsum(g[r::4].astype(np.uint64)) + seeds[r]) & MASK32
+            assert np.array_equal(x[r::4], want.astype(np.uint32)), r
+
+
+def test_delta4_round_trip_and_small_gaps():
+    """Four interleaved sorted lists: the stored integers are each list's own
+    gaps, and the round trip gives the lists back."""
+    rng = np.random.default_rng(8)
+    lanes = [np.cumsum(inputs.geometric_gaps(10_000, seed=s).astype(np.uint64)) for s in range(4)]
+    x = np.stack(lanes, axis=1).reshape(-1).astype(np.uint32)
+    data = oracle.encode_delta4(x)
+    g = oracle.decode(data)
+    assert np.array_equal(g, np.concatenate([x[:4], x[4:] - x[:-4]]))
+    assert np.array_equal(oracle.decode_delta4(data, x.size), x)
+    for prev4 in ([1, 2, 3, 4], rng.integers(0, 1 << 32, 4, dtype=np.uint64).astype(np.uint32)):
+        assert np.array_equal(oracle.decode_delta4(oracle.encode_delta4(x, prev4), x.size, prev4), x)
+
+
+def test_delta4_short_lists_and_wrap():
+    for n in range(0, 9):
+        x = (np.arange(n, dtype=np.uint64) * 0x9E3779B9 & MASK32).astype(np.uint32)
+        data = oracle.encode_delta4(x, prev4=[MASK32] * 4)
+        assert np.array_equal(oracle.decode_delta4(data, n, prev4=[MASK32] * 4), x)
+        g = oracle.decode(data)
+        before = np.concatenate([np.full(4, MASK32, dtype=np.uint64), x.astype(np.uint64)])[:n]
+        want = (x.astype(np.uint64) + np.uint64(1 << 32) - before) & np.uint64(MASK32)
+        assert np.array_equal(g, want.astype(np.uint32))
