@@ -294,6 +294,14 @@ def run_gpu(args):
     if not args.no_encode:
         encode = run_encode(args, streams, stream, measured_peaks())
 
+    # ---- 64-bit integers
+    decode64 = None
+    if not args.no_decode64:
+        try:
+            decode64 = run_decode64(args, stream, measured_peaks())
+        except Exception as e:   # an auxiliary leg: report it, keep the headline line
+            decode64 = {"error": f"{type(e).__name__}: {e}"}
+
     # ---- batched lists: one tuned, graph-replayed launch vs one call per list
     batched = serving = None
     if ws == 1 and not args.no_batched:
@@ -363,6 +371,7 @@ def run_gpu(args):
         },
         "gpu_launches": len(streams) * args.steps,
         "encode": encode,
+        "decode64": decode64,
         "batched": batched,
         "serving": serving,
         "status": status,
@@ -410,6 +419,58 @@ def run_encode(args, streams, stream, peaks):
             "bit_exact_with_input": bool(exact), "status": int(vbyte.get_status()),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes_per_step": algo}}
+
+
+def run_decode64(args, stream, peaks):
+    """64-bit VByte decoding (the format read for uint64): 2^26 sorted uint64
+    document ids from 1 + Geometric(0.1) gaps above 2^40 (differential, almost
+    all one-byte codes) and 2^26 values of every bit width 0..64 (plain, code
+    lengths 1..10), checked bit for bit against the values the streams were
+    built from and timed with CUDA events over the three launches of each
+    call: Gints/s and the HBM roofline (input bytes + 8n per call)."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    n = 1 << 26
+    ids = np.cumsum(inputs.geometric_gaps(n, seed=0).astype(np.uint64)) + np.uint64(1 << 40)
+    vals = inputs.uniform_bits64(n, seed=1)
+    cases = [{"label": "geometric_ids_delta", "x": ids, "delta": True, "host": vbyte.encode_delta64(ids)},
+             {"label": "uniform_bits64_plain", "x": vals, "delta": False, "host": vbyte.encode64(vals)}]
+    for c in cases:
+        c["d_in"] = torch.from_numpy(c["host"]).cuda()
+        c["out"] = torch.empty(n, dtype=torch.int64, device="cuda")
+
+    def call(c):
+        if c["delta"]:
+            vbyte.decode_delta64(c["d_in"], n, out=c["out"], stream=stream)
+        else:
+            vbyte.decode64(c["d_in"], n, out=c["out"], stream=stream)
+
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    reps = max(5, min(args.steps, 200))
+    res = []
+    for c in cases:
+        for _ in range(3):
+            call(c)
+        torch.cuda.synchronize()
+        exact = torch.equal(c["out"], torch.from_numpy(c["x"].view(np.int64)).cuda())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call(c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        algo = int(c["host"].size) + 8 * n
+        achieved = algo / (ms * 1e-3) / 1e9
+        res.append({"label": c["label"], "n": n, "nbytes": int(c["host"].size), "ms": round(ms, 5),
+                    "value": round(n / (ms * 1e-3) / 1e9, 3), "unit": "Gints/s", "bit_exact": bool(exact),
+                    "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(achieved / peak, 4), "algorithmic_bytes_per_call": algo}})
+    status = int(vbyte.get_status())
+    for c in cases:
+        del c["d_in"], c["out"]
+    return {"form": "vbyte_decode_delta64 / vbyte_decode64 (count, scan and decode launches per call)",
+            "status": status, "streams": res}
 
 
 def run_batched(args, peaks):
@@ -640,6 +701,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-encode", action="store_true")
+    ap.add_argument("--no-decode64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000, 50000])
     ap.add_argument("--serve-seconds", type=float, default=1.0)

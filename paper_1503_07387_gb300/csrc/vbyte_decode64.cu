@@ -1,0 +1,413 @@
+// 64-bit VByte decoding (vbyte_decode64, vbyte_decode_delta64).
+//
+// Operation (arXiv 1503.07387): Sec. 1 notes that the VByte format covers
+// 64-bit integers as well as the 32-bit ones the paper works with.  Read for
+// uint64: seven data bits per byte, least significant group first, the high
+// bit set on every byte of an integer but the last, so up to ten bytes; an
+// integer ends at a byte whose high bit is clear, and Algorithm 1 (Sec. 2)
+// run for ten steps rebuilds it, the tenth byte multiplied by 2^63 modulo
+// 2^64.  In delta mode the integers are gaps and the output is their running
+// sum from prev, modulo 2^64 (Sec. 1, "Differential coding").
+//
+// Design: three launches and no waits between CTAs.
+//   count64:  per 4 KiB tile of the input, the number of integers that end
+//             in it and, in delta mode, their sum; also the data-error
+//             checks (a run of ten or more high-bit bytes; a last byte with
+//             the high bit set);
+//   scan64:   one CTA turns the per-tile counts and sums into the values
+//             before each tile and prev plus the sum of every integer before
+//             it, and checks the total count against n;
+//   decode64: per tile, every integer that ends in it, assembled from its own
+//             bytes (at most nine before its terminator; the 16 bytes staged
+//             ahead of the tile cover them), placed by a block scan of the
+//             per-thread counts into shared memory, prefix-summed there in
+//             delta mode, and written out with coalesced 8-byte stores.
+// Tiles start at the input address rounded down to 16 bytes, so every
+// staged chunk is one aligned 16-byte load; bytes of a chunk outside the
+// input are staged as zero and never counted.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "vbyte.h"
+#include "vbyte64.h"
+#include "vbyte_internal.h"
+
+namespace vbk {
+namespace d64 {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kTile = 4096;                 // input bytes per tile
+constexpr int kSlice = kTile / kThreads;    // bytes per thread
+constexpr int kHalo = 16;                   // bytes staged before the tile
+constexpr int kMaxLen = 10;                 // bytes of the longest uint64 code
+constexpr int kScanThreads = 1024;
+constexpr size_t kHead = 256;               // workspace: status word, then the tile arrays
+static_assert(kSlice == 16, "one 16-byte chunk per thread");
+static_assert(kHalo >= kMaxLen - 1, "an integer's earlier bytes lie in the halo");
+
+struct Params {
+    const uint8_t *base;   // the input rounded down to 16 bytes
+    int64_t lo, hi;        // the input is [lo, hi) from base (lo < 16)
+    uint64_t ntiles;
+    uint64_t *out;
+    uint64_t n;
+    uint64_t prev;
+    uint64_t *tcnt;        // per tile: integers ending in it; after scan64, integers before it
+    uint64_t *tsum;        // per tile (delta): their sum; after scan64, prev + the sum before it
+    uint32_t *status;
+};
+
+struct CountShared {
+    alignas(16) uint8_t bytes[kHalo + kTile];
+    unsigned long long wsum[kWarps];
+    uint32_t wcnt[kWarps];
+};
+
+struct DecodeShared {
+    alignas(16) uint8_t bytes[kHalo + kTile];
+    alignas(16) unsigned long long vals[kTile];   // the tile's integers, in order
+    unsigned long long wsum[kWarps];
+    uint32_t wcnt[kWarps];
+};
+
+// Zero the bytes of the chunk at q0 that lie outside [lo, hi).
+__device__ __forceinline__ uint4 clip_chunk(uint4 v, int64_t q0, int64_t lo, int64_t hi)
+{
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t q = q0 + 4 * k + j;
+            if (q < lo || q >= hi) w[k] &= ~(0xFFu << (8 * j));
+        }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Stage tile t and the 16 bytes before it: chunk c in [-1, kTile/16) goes to
+// bytes[kHalo + 16c].  A chunk is loaded only if it holds an input byte; it
+// is then one aligned 16-byte load that stays inside the input's 16-byte
+// blocks.
+__device__ __forceinline__ void stage(const Params &p, uint64_t t, uint8_t *bytes)
+{
+    const int64_t t0 = static_cast<int64_t>(t) * kTile;
+    for (int c = static_cast<int>(threadIdx.x) - 1; c < kTile / 16; c += kThreads) {
+        const int64_t q0 = t0 + 16ll * c;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (q0 + 16 > p.lo && q0 < p.hi) {   // then q0 >= 0: q0 is a multiple of 16 above -16
+            v = __ldg(reinterpret_cast<const uint4 *>(p.base + q0));
+            if (q0 < p.lo || q0 + 16 > p.hi) v = clip_chunk(v, q0, p.lo, p.hi);
+        }
+        *reinterpret_cast<uint4 *>(bytes + kHalo + 16 * c) = v;
+    }
+}
+
+// The integers that end in this thread's slice, tile bytes [16 tid, 16 tid +
+// 16), at tile positions in [a, b), in order: f(v) for each.  Each is
+// assembled from the high-bit bytes before its terminator, the first of them
+// possibly in the previous slice (or the halo).  Returns true if the slice
+// holds a byte that makes a run of ten or more high-bit bytes.
+template <bool kValues, class F>
+__device__ __forceinline__ bool walk(const uint8_t *bytes, int tid, int a, int b, F &&f)
+{
+    const uint8_t *s = bytes + kHalo + kSlice * tid;
+    const uint4 q = *reinterpret_cast<const uint4 *>(s);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    // the high-bit bytes just before the slice (at most nine): the start of an
+    // integer that ends here; s[-1] holds its highest group of them
+    int r = 0;
+    uint64_t acc = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxLen; ++k) {
+        const uint32_t c = s[-k];
+        if (r == k - 1 && (c & 0x80u)) {
+            r = k;
+            if (kValues) acc = (acc << 7) | (c & 0x7Fu);
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kSlice; ++j) {
+        const uint32_t c = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+        if (c & 0x80u) {
+            if (kValues && r < kMaxLen) acc |= static_cast<uint64_t>(c & 0x7Fu) << (7 * r);   // shift <= 63
+            ++r;
+            bad |= (r >= kMaxLen);
+        } else {
+            if (kValues && r < kMaxLen) acc |= static_cast<uint64_t>(c) << (7 * r);
+            const int pos = kSlice * tid + j;
+            if (pos >= a && pos < b) f(acc);
+            acc = 0;
+            r = 0;
+        }
+    }
+    return bad;
+}
+
+// Bytes with the high bit clear at tile positions [a, b) of this thread's slice.
+__device__ __forceinline__ uint32_t slice_count(const uint8_t *bytes, int tid, int a, int b)
+{
+    const uint4 q = *reinterpret_cast<const uint4 *>(bytes + kHalo + kSlice * tid);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    const int s0 = kSlice * tid;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t m = ~w[k] & 0x80808080u;
+        if (s0 < a || s0 + kSlice > b) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int pos = s0 + 4 * k + j;
+                if (pos < a || pos >= b) m &= ~(0x80u << (8 * j));
+            }
+        }
+        cnt += __popc(m);
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ uint32_t warp_sum32(uint32_t x)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, d);
+    return x;
+}
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t x)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, d);
+    return x;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_incl(T x, int lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d) x += y;
+    }
+    return x;
+}
+
+// Exclusive block scan over kThreads threads (wt: kWarps words of shared
+// memory, free since the last barrier); *total gets the block's sum.
+template <class T>
+__device__ __forceinline__ T block_excl(T x, T *wt, T *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T inc = warp_incl(x, lane);
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    T before = 0, all = 0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) {
+        const T v = wt[k];
+        if (k < warp) before += v;
+        all += v;
+    }
+    *total = all;
+    return before + inc - x;
+}
+
+// Tile positions [a, b) of tile t that hold input bytes.
+__device__ __forceinline__ void tile_range(const Params &p, uint64_t t, int *a, int *b)
+{
+    const int64_t t0 = static_cast<int64_t>(t) * kTile;
+    *a = static_cast<int>(p.lo > t0 ? p.lo - t0 : 0);
+    *b = static_cast<int>(p.hi - t0 < kTile ? p.hi - t0 : kTile);
+}
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kThreads) count64_kernel(Params p)
+{
+    __shared__ CountShared S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+        stage(p, t, S.bytes);
+        __syncthreads();
+        int a, b;
+        tile_range(p, t, &a, &b);
+        uint32_t cnt = 0;
+        uint64_t sum = 0;
+        const bool bad = walk<kDelta>(S.bytes, tid, a, b, [&](uint64_t v) {
+            ++cnt;
+            if (kDelta) sum += v;
+        });
+        if (bad) atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
+        if (t + 1 == p.ntiles && b - 1 >= kSlice * tid && b - 1 < kSlice * (tid + 1) &&
+            (S.bytes[kHalo + b - 1] & 0x80u))
+            atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+        cnt = warp_sum32(cnt);
+        if (kDelta) sum = warp_sum64(sum);
+        if (lane == 0) {
+            S.wcnt[warp] = cnt;
+            S.wsum[warp] = sum;
+        }
+        __syncthreads();   // also: every walk of this tile is done before the next stage
+        if (tid == 0) {
+            uint64_t c = 0, s = 0;
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) {
+                c += S.wcnt[k];
+                s += S.wsum[k];
+            }
+            p.tcnt[t] = c;
+            if (kDelta) p.tsum[t] = s;
+        }
+    }
+}
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kScanThreads) scan64_kernel(Params p)
+{
+    __shared__ unsigned long long wc[kScanThreads / 32], ws[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t T = p.ntiles;
+    const uint64_t per = (T + kScanThreads - 1) / kScanThreads;
+    const uint64_t i0 = std::min<uint64_t>(T, per * tid), i1 = std::min<uint64_t>(T, i0 + per);
+    uint64_t c = 0, s = 0;
+    for (uint64_t i = i0; i < i1; ++i) {
+        c += p.tcnt[i];
+        if (kDelta) s += p.tsum[i];
+    }
+    const uint64_t ci = warp_incl<uint64_t>(c, lane);
+    const uint64_t si = kDelta ? warp_incl<uint64_t>(s, lane) : 0;
+    if (lane == 31) {
+        wc[warp] = ci;
+        ws[warp] = si;
+    }
+    __syncthreads();
+    uint64_t cb = 0, sb = 0, call = 0;
+    for (int k = 0; k < kScanThreads / 32; ++k) {
+        if (k < warp) {
+            cb += wc[k];
+            sb += ws[k];
+        }
+        call += wc[k];
+    }
+    uint64_t ce = cb + ci - c, se = p.prev + sb + si - s;
+    for (uint64_t i = i0; i < i1; ++i) {
+        const uint64_t x = p.tcnt[i];
+        p.tcnt[i] = ce;
+        ce += x;
+        if (kDelta) {
+            const uint64_t y = p.tsum[i];
+            p.tsum[i] = se;
+            se += y;
+        }
+    }
+    if (tid == 0 && call != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+}
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kThreads) decode64_kernel(Params p)
+{
+    __shared__ DecodeShared S;
+    const int tid = threadIdx.x;
+    for (uint64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+        stage(p, t, S.bytes);
+        __syncthreads();
+        int a, b;
+        tile_range(p, t, &a, &b);
+        uint32_t C = 0;
+        uint32_t rank = block_excl<uint32_t>(slice_count(S.bytes, tid, a, b), S.wcnt, &C);
+        walk<true>(S.bytes, tid, a, b, [&](uint64_t v) { S.vals[rank++] = v; });
+        __syncthreads();
+        if (kDelta) {
+            // running sums of the tile's integers from prev + everything before it
+            const uint32_t j0 = kSlice * tid, j1 = min(j0 + kSlice, C);
+            uint64_t run = 0;
+            for (uint32_t j = j0; j < j1; ++j) run += S.vals[j];
+            unsigned long long tot;
+            uint64_t x = p.tsum[t] + block_excl<unsigned long long>(run, S.wsum, &tot);
+            for (uint32_t j = j0; j < j1; ++j) {
+                x += S.vals[j];
+                S.vals[j] = x;
+            }
+            __syncthreads();
+        }
+        const uint64_t r0 = p.tcnt[t];
+        for (uint32_t j = tid; j < C; j += kThreads) {
+            const uint64_t g = r0 + j;
+            if (g < p.n) p.out[g] = S.vals[j];
+        }
+        __syncthreads();   // the next stage and scan reuse S
+    }
+}
+
+namespace {
+
+int occupancy_grid(const void *kernel, int smem, uint64_t ntiles, int *grid)
+{
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem) != cudaSuccess)
+        return VBYTE_ECUDA;
+    *grid = static_cast<int>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(sms) * std::max(occ, 1)));
+    return VBYTE_OK;
+}
+
+template <bool kDelta>
+int enqueue(const Params &p, cudaStream_t s)
+{
+    int gc = 0, gd = 0;
+    int rc = occupancy_grid(reinterpret_cast<const void *>(count64_kernel<kDelta>), 0, p.ntiles, &gc);
+    if (rc == VBYTE_OK) rc = occupancy_grid(reinterpret_cast<const void *>(decode64_kernel<kDelta>), 0, p.ntiles, &gd);
+    if (rc != VBYTE_OK) return rc;
+    count64_kernel<kDelta><<<gc, kThreads, 0, s>>>(p);
+    scan64_kernel<kDelta><<<1, kScanThreads, 0, s>>>(p);
+    decode64_kernel<kDelta><<<gd, kThreads, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
+int launch(const uint8_t *in, size_t nbytes, uint64_t *out, size_t n, bool delta, uint64_t prev, cudaStream_t s)
+{
+    if (nbytes == 0 && n == 0) return VBYTE_OK;
+    if ((nbytes && !in) || (n && !out)) return VBYTE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(out) & 7u) return VBYTE_EINVAL;
+    const uintptr_t ia = reinterpret_cast<uintptr_t>(in);
+    const uint64_t lo = ia & 15u;
+    const uint64_t ntiles = (lo + nbytes + kTile - 1) / kTile;
+    uint8_t *ws = nullptr;
+    const int rc = stream_workspace(s, kHead + 16 * ntiles, &ws);
+    if (rc != VBYTE_OK) return rc;
+    uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+    if (nbytes == 0) return set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s);   // n > 0 from no bytes
+    Params p = {};
+    p.base = reinterpret_cast<const uint8_t *>(ia - lo);
+    p.lo = static_cast<int64_t>(lo);
+    p.hi = static_cast<int64_t>(lo + nbytes);
+    p.ntiles = ntiles;
+    p.out = out;
+    p.n = n;
+    p.prev = prev;
+    p.tcnt = reinterpret_cast<uint64_t *>(ws + kHead);
+    p.tsum = p.tcnt + ntiles;
+    p.status = status;
+    return delta ? enqueue<true>(p, s) : enqueue<false>(p, s);
+}
+
+}  // namespace
+}  // namespace d64
+}  // namespace vbk
+
+extern "C" {
+
+int vbyte_decode64(const uint8_t *d_in, size_t nbytes, uint64_t *d_out, size_t n, void *stream)
+{
+    return vbk::d64::launch(d_in, nbytes, d_out, n, false, 0u, static_cast<cudaStream_t>(stream));
+}
+
+int vbyte_decode_delta64(const uint8_t *d_in, size_t nbytes, uint64_t *d_out, size_t n, uint64_t prev,
+                         void *stream)
+{
+    return vbk::d64::launch(d_in, nbytes, d_out, n, true, prev, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

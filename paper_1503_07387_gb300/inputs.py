@@ -70,6 +70,18 @@ def full_range(n: int = 1 << 28, seed: int = 0) -> np.ndarray:
     return rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
 
 
+def uniform_bits64(n: int = 1 << 26, seed: int = 0) -> np.ndarray:
+    """uint64 values of every bit width 0..64, equally often (code lengths
+    1..10 of the 64-bit form)."""
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 65, size=n).astype(np.uint64)
+    top = rng.integers(0, 1 << 63, size=n, dtype=np.uint64) * np.uint64(2) \
+        + rng.integers(0, 2, size=n, dtype=np.uint64)
+    v = top >> (np.uint64(64) - np.maximum(bits, np.uint64(1)))
+    v[bits == 0] = 0
+    return v
+
+
 def posting_lists(num_lists: int = 100_000, universe: int = 50_000_000,
                   cap: int = 10_000_000, seed: int = 0, min_len: int = 1):
     """Rank-Zipf(s=1) posting lists.

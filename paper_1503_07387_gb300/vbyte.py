@@ -34,6 +34,7 @@ ERR_TIMEOUT = 8
 ERR_BAD_OFFSETS = 16
 
 HEADER = os.path.join(_build.INCLUDE, "vbyte.h")
+HEADERS = [HEADER, os.path.join(_build.INCLUDE, "vbyte64.h")]
 
 _lib = None
 
@@ -77,6 +78,11 @@ def _signatures(lib):
         "vbyte_get_status": ([P, P], I),
         "vbyte_strerror": ([I], ctypes.c_char_p),
         "vbyte_workspace_size": ([S], S),
+        "vbyte_max_encoded_size64": ([S], S),
+        "vbyte_encode64": ([P, S, P], S),
+        "vbyte_encode_delta64": ([P, S, ctypes.c_uint64, P], S),
+        "vbyte_decode64": ([P, S, P, S, P], I),
+        "vbyte_decode_delta64": ([P, S, P, S, ctypes.c_uint64, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -100,8 +106,8 @@ def load(build: bool = True):
 
 
 def declared_symbols() -> list[str]:
-    """Function names declared in include/vbyte.h."""
-    text = open(HEADER).read()
+    """Function names declared in the public headers (vbyte.h, vbyte64.h)."""
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(vbyte_[a-z0-9_]+)\s*\(", text)))
 
@@ -477,6 +483,59 @@ def decode_noalloc(data, n: int, delta: bool = False, prev: int = 0, out=None, s
                                      ctypes.c_void_p(out.data_ptr()), n, int(delta),
                                      ctypes.c_uint32(prev & 0xFFFFFFFF), sp, _stream_handle(stream))
     _check(rc, "vbyte_decode_noalloc")
+    return out
+
+
+# ------------------------------------------------------- 64-bit integers --
+
+MASK64 = (1 << 64) - 1
+
+
+def encode64(values) -> np.ndarray:
+    """Host encoding of uint64 values (up to ten bytes each)."""
+    v = np.ascontiguousarray(values, dtype=np.uint64)
+    out = np.empty(max(10 * v.size, 1), dtype=np.uint8)
+    nb = load().vbyte_encode64(_np_ptr(v), v.size, _np_ptr(out))
+    return out[:nb]
+
+
+def encode_delta64(values, prev: int = 0) -> np.ndarray:
+    """Host encoding of the uint64 gaps x_i - x_{i-1} (mod 2^64), x_0 = prev."""
+    v = np.ascontiguousarray(values, dtype=np.uint64)
+    out = np.empty(max(10 * v.size, 1), dtype=np.uint8)
+    nb = load().vbyte_encode_delta64(_np_ptr(v), v.size, ctypes.c_uint64(prev & MASK64), _np_ptr(out))
+    return out[:nb]
+
+
+def _device_args64(data, n, out):
+    import torch
+    if not isinstance(data, torch.Tensor) or data.dtype != torch.uint8 or not data.is_cuda \
+            or not data.is_contiguous():
+        raise TypeError("data must be a contiguous CUDA uint8 tensor")
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=data.device)
+    elif out.dtype not in (torch.int64, torch.uint64) or not out.is_contiguous() or out.numel() < n:
+        raise ValueError("out must be a contiguous 64-bit CUDA tensor with at least n elements")
+    return out
+
+
+def decode64(data, n: int, out=None, stream=None):
+    """Decode uint64 VByte integers into n 64-bit slots (int64 tensor by
+    default; view its bits as uint64)."""
+    out = _device_args64(data, n, out)
+    rc = load().vbyte_decode64(ctypes.c_void_p(data.data_ptr()), data.numel(),
+                               ctypes.c_void_p(out.data_ptr()), n, _stream_handle(stream))
+    _check(rc, "vbyte_decode64")
+    return out
+
+
+def decode_delta64(data, n: int, prev: int = 0, out=None, stream=None):
+    """Decode uint64 gaps and return their prefix sums from prev (mod 2^64)."""
+    out = _device_args64(data, n, out)
+    rc = load().vbyte_decode_delta64(ctypes.c_void_p(data.data_ptr()), data.numel(),
+                                     ctypes.c_void_p(out.data_ptr()), n,
+                                     ctypes.c_uint64(prev & MASK64), _stream_handle(stream))
+    _check(rc, "vbyte_decode_delta64")
     return out
 
 

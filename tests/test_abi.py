@@ -89,3 +89,32 @@ def test_argument_errors_before_any_device_work():
     assert lib.vbyte_encode_delta_m1_device(None, 4, 0, P(64), P(128), None) == einval
     # plans and servers need their out-parameters
     assert lib.vbyte_plan_create(None, P(16), 16, P(16), P(16), 4, P(16), 1, None, 0, 0, None) == einval
+    # 64-bit decoding: null pointers, an output that is not 8-byte aligned
+    assert lib.vbyte_decode64(None, 16, P(16), 4, None) == einval
+    assert lib.vbyte_decode64(P(16), 16, None, 4, None) == einval
+    assert lib.vbyte_decode64(P(16), 16, P(20), 4, None) == einval
+    assert lib.vbyte_decode_delta64(P(16), 16, P(12), 4, 0, None) == einval
+    # nothing to do: no bytes and no values
+    assert lib.vbyte_decode64(None, 0, None, 0, None) == 0
+
+
+def _all_widths64(n, seed):
+    """uint64 values of every bit width 0..64, equally often."""
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 65, n).astype(np.uint64)
+    hi = rng.integers(0, 1 << 63, n, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        v = np.where(bits == 0, np.uint64(0), hi >> (np.uint64(64) - np.maximum(bits, np.uint64(1))))
+    return v.astype(np.uint64)
+
+
+def test_host_encoder64_matches_oracle():
+    v = _all_widths64(100_000, 2)
+    assert np.array_equal(vbyte.encode64(v), oracle.encode64(v))
+    edges = [0, 1, (1 << 64) - 1] + [(1 << (7 * k)) + d for k in range(1, 10) for d in (-1, 0)]
+    e = np.array(edges, dtype=np.uint64)
+    assert np.array_equal(vbyte.encode64(e), oracle.encode64(e))
+    assert vbyte.encode64(np.zeros(0, np.uint64)).size == 0
+    assert vbyte.load().vbyte_max_encoded_size64(7) == 70
+    for prev in (0, 12345, (1 << 64) - 1):
+        assert np.array_equal(vbyte.encode_delta64(v, prev=prev), oracle.encode_delta64(v, prev=prev))
