@@ -350,6 +350,30 @@ const char *vbyte_strerror(int code);
  * graph capture); the library allocates it itself on first use. */
 size_t vbyte_workspace_size(size_t nbytes);
 
+/* Give `stream` (on the current device) a caller-owned workspace in place of
+ * the one the library would allocate.  d_ws: device memory, 256-byte
+ * aligned, `bytes` long, bytes >= vbyte_workspace_size(0).  From then on the
+ * calls on that stream use it and never allocate a workspace: a call that
+ * needs more than `bytes` (vbyte_workspace_size of its input) returns
+ * VBYTE_ENOMEM and queues nothing.  The first 4 bytes become the stream's
+ * status word; the bits recorded so far carry over (a 4-byte copy queued on
+ * `stream`), and a workspace the library had allocated for the stream is
+ * freed, queued on `stream`.  The buffer serves the stream until it is
+ * replaced, handed back (d_ws = NULL: the library allocates again, the
+ * status bits carry over) or dropped by vbyte_release_stream; the library
+ * never frees it.  The staging buffers of vbyte_decode_host stay the
+ * library's.  Returns VBYTE_EINVAL for a misaligned or too small buffer or
+ * while `stream` is being captured, VBYTE_ENOMEM if handing back cannot
+ * allocate, VBYTE_ECUDA if a queued copy fails. */
+int vbyte_set_workspace(void *stream, void *d_ws, size_t bytes);
+
+/* Forget `stream` (current device): free the workspace and the host-call
+ * staging buffers the library allocated for it (queued on `stream`) and
+ * drop a caller-owned workspace without freeing it.  Call it before
+ * destroying the stream; status bits not yet read are lost.  Returns
+ * VBYTE_OK, also for a stream the library has not seen. */
+int vbyte_release_stream(void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,7 @@ constexpr size_t kWsHead = 256;
 struct Workspace {
     uint8_t *ptr = nullptr;
     size_t cap = 0;
+    bool caller = false;   // the caller's buffer (vbyte_set_workspace): never grown or freed here
 };
 
 struct HostBuffers {
@@ -136,7 +137,7 @@ int get_workspace(cudaStream_t s, size_t need, Workspace **out)
     std::lock_guard<std::mutex> lk(g_mu);
     Workspace &w = g_ws[{dev, reinterpret_cast<uintptr_t>(s)}];
     if (w.cap < need) {
-        if (capturing(s)) return VBYTE_ENOMEM;
+        if (w.caller || capturing(s)) return VBYTE_ENOMEM;
         size_t cap = std::max<size_t>(need, std::max<size_t>(2 * w.cap, size_t(1) << 20));
         void *np = nullptr;
         if (cudaMallocAsync(&np, cap, s) != cudaSuccess) {
@@ -198,7 +199,7 @@ void release_workspace(cudaStream_t s)
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_ws.find({dev, reinterpret_cast<uintptr_t>(s)});
     if (it != g_ws.end()) {
-        if (it->second.ptr) cudaFreeAsync(it->second.ptr, s);
+        if (it->second.ptr && !it->second.caller) cudaFreeAsync(it->second.ptr, s);
         g_ws.erase(it);
     }
     auto ih = g_hb.find({dev, reinterpret_cast<uintptr_t>(s)});
@@ -267,6 +268,50 @@ int launch_decode_noalloc(const uint8_t *in, size_t nbytes, uint32_t *out, size_
     if (status == nullptr) status = reinterpret_cast<uint32_t *>(scratch);
     if (nbytes == 0) return set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s);   // n > 0 from no bytes
     return enqueue_stream(in, nbytes, out, n, delta, prev, scratch, status, s);
+}
+
+// Make ptr (caller-owned, bytes long) the workspace of (current device, s),
+// or with ptr == nullptr hand the stream back to library allocations; the
+// status word carries over either way.
+int set_workspace(cudaStream_t s, uint8_t *ptr, size_t bytes)
+{
+    if (ptr && ((reinterpret_cast<uintptr_t>(ptr) & 255u) || bytes < workspace_bound(0))) return VBYTE_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VBYTE_ECUDA;
+    if (capturing(s)) return VBYTE_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace &w = g_ws[{dev, reinterpret_cast<uintptr_t>(s)}];
+    if (!ptr) {
+        if (!w.caller) return VBYTE_OK;   // already the library's
+        const size_t cap = size_t(1) << 20;
+        void *np = nullptr;
+        if (cudaMallocAsync(&np, cap, s) != cudaSuccess) {
+            cudaGetLastError();
+            return VBYTE_ENOMEM;
+        }
+        if (cudaMemcpyAsync(np, w.ptr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return VBYTE_ECUDA;
+        w.ptr = static_cast<uint8_t *>(np);
+        w.cap = cap;
+        w.caller = false;
+        return VBYTE_OK;
+    }
+    if (ptr == w.ptr) {
+        w.cap = bytes;   // the same buffer again, perhaps with a new length
+        w.caller = true;
+        return VBYTE_OK;
+    }
+    if (w.ptr) {
+        if (cudaMemcpyAsync(ptr, w.ptr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return VBYTE_ECUDA;
+        if (!w.caller) cudaFreeAsync(w.ptr, s);
+    } else if (cudaMemsetAsync(ptr, 0, sizeof(uint32_t), s) != cudaSuccess) {
+        return VBYTE_ECUDA;
+    }
+    w.ptr = ptr;
+    w.cap = bytes;
+    w.caller = true;
+    return VBYTE_OK;
 }
 
 int reserve_workspace(cudaStream_t s, size_t nbytes)
@@ -385,5 +430,16 @@ const char *vbyte_strerror(int code)
 }
 
 size_t vbyte_workspace_size(size_t nbytes) { return vbk::workspace_bound(nbytes); }
+
+int vbyte_set_workspace(void *stream, void *d_ws, size_t bytes)
+{
+    return vbk::set_workspace(static_cast<cudaStream_t>(stream), static_cast<uint8_t *>(d_ws), bytes);
+}
+
+int vbyte_release_stream(void *stream)
+{
+    vbk::release_workspace(static_cast<cudaStream_t>(stream));
+    return VBYTE_OK;
+}
 
 }  // extern "C"

@@ -78,6 +78,8 @@ def _signatures(lib):
         "vbyte_get_status": ([P, P], I),
         "vbyte_strerror": ([I], ctypes.c_char_p),
         "vbyte_workspace_size": ([S], S),
+        "vbyte_set_workspace": ([P, P, S], I),
+        "vbyte_release_stream": ([P], I),
         "vbyte_max_encoded_size64": ([S], S),
         "vbyte_encode64": ([P, S, P], S),
         "vbyte_encode_delta64": ([P, S, ctypes.c_uint64, P], S),
@@ -549,3 +551,23 @@ def get_status(stream=None) -> int:
 
 def workspace_size(nbytes: int) -> int:
     return int(load().vbyte_workspace_size(nbytes))
+
+
+def set_workspace(buf, stream=None):
+    """vbyte_set_workspace: make the CUDA uint8 tensor `buf` (256-byte aligned,
+    at least workspace_size(0) bytes) the stream's workspace, or with
+    buf=None hand the stream back to library allocations.  The caller keeps
+    `buf` alive while the stream uses it."""
+    import torch
+    if buf is None:
+        _check(load().vbyte_set_workspace(_stream_handle(stream), None, 0), "vbyte_set_workspace")
+        return
+    if not isinstance(buf, torch.Tensor) or buf.dtype != torch.uint8 or not buf.is_cuda or not buf.is_contiguous():
+        raise TypeError("buf must be a contiguous CUDA uint8 tensor")
+    _check(load().vbyte_set_workspace(_stream_handle(stream), ctypes.c_void_p(buf.data_ptr()), buf.numel()),
+           "vbyte_set_workspace")
+
+
+def release_stream(stream=None):
+    """vbyte_release_stream: free what the library holds for the stream."""
+    _check(load().vbyte_release_stream(_stream_handle(stream)), "vbyte_release_stream")

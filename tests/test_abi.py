@@ -96,6 +96,9 @@ def test_argument_errors_before_any_device_work():
     assert lib.vbyte_decode_delta64(P(16), 16, P(12), 4, 0, None) == einval
     # nothing to do: no bytes and no values
     assert lib.vbyte_decode64(None, 0, None, 0, None) == 0
+    # a caller workspace must be 256-byte aligned and hold at least the head
+    assert lib.vbyte_set_workspace(None, P(256 + 16), 1 << 20) == einval
+    assert lib.vbyte_set_workspace(None, P(1 << 20), vbyte.workspace_size(0) - 1) == einval
 
 
 def _all_widths64(n, seed):
