@@ -1,0 +1,91 @@
+"""Host-side pieces of bench.py, checked on the CPU: the kernel-source hash
+that ties the committed ncu traffic figure to the code it was taken on, the
+lookup of that figure, the clock-record parsing, and the prefix sizing of
+the reference arm."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_code_only_ignores_comments_and_spacing():
+    a = "int f(int x) {  // add one\n    return x + 1; /* the\n successor */ }\n"
+    b = "/* header */\nint f(int x)\n{\n    return x + 1;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b) == "int f(int x) { return x + 1; }"
+    assert bench._code_only(a) != bench._code_only(a.replace("x + 1", "x + 2"))
+
+
+def test_committed_profile_names_a_hash_and_a_traffic_figure():
+    """The committed summary carries both lines the bench reads; its traffic
+    is reported only for the sources it names."""
+    import re
+    text = open(bench.PROFILE_FILE).read()
+    m = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
+    assert m and re.search(r"dram bytes per launch \(full workload\):\s*[0-9.eE+]+", text)
+    assert bench.profiled_traffic(m.group(1)) > 0
+    assert bench.profiled_traffic("0" * 16) is None
+    assert len(bench.kernel_source_hash()) == 16
+
+
+def test_profiled_traffic_missing_file(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "PROFILE_FILE", str(tmp_path / "absent.md"))
+    assert bench.profiled_traffic(bench.kernel_source_hash()) is None
+    p = tmp_path / "p.md"
+    p.write_text("kernel source hash: `0123456789abcdef`\ndram bytes per launch (full workload): 1.5e6\n")
+    monkeypatch.setattr(bench, "PROFILE_FILE", str(p))
+    assert bench.profiled_traffic("0123456789abcdef") == 1.5e6
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+class _FakeThread:
+    def join(self, timeout=None):
+        pass
+
+
+def test_clock_sampler_parses_rows_inside_the_timed_region():
+    s = bench.ClockSampler(0)
+    s.proc, s.thread = _FakeProc(), _FakeThread()
+    s.t_start, s.t_end = 100.0, 101.0
+    row = "0, {sm}, 2070, 900.5, 0x{r}, Not Active, Not Active, Not Active, {cap}"
+    s.rows = [(99.0, row.format(sm=300, r=0, cap="Not Active")),     # before: ignored
+              (100.2, row.format(sm=2070, r=0, cap="Not Active")),
+              (100.5, row.format(sm=2040, r=4, cap="Active")),
+              (100.9, row.format(sm=2055, r=0, cap="Not Active")),
+              (105.0, row.format(sm=500, r=0, cap="Not Active"))]    # after: ignored
+    rec = s.stop()
+    assert rec["sm_mhz"] == 2055 and rec["sm_max_mhz"] == 2070
+    assert rec["reasons"] == ["sw_power_cap"] and rec["samples"] == 3
+    assert rec["window"] == "timed region"
+
+
+def test_clock_sampler_without_nvidia_smi():
+    s = bench.ClockSampler(0)
+    assert s.stop() is None
+
+
+def test_prefix_bytes_is_the_end_of_the_mth_integer():
+    v = np.array([1, 300, 70000, 5, 1 << 31], dtype=np.uint32)
+    data = oracle.encode(v)
+    ends = np.cumsum([len(oracle.encode_one(int(x))) for x in v])
+    for m in range(1, v.size + 1):
+        assert bench._prefix_bytes(data, m) == ends[m - 1]
+    assert bench._prefix_bytes(data, 0) == 0
+
+
+def test_whole_job_rate_is_weak_scaling():
+    assert bench.whole_job_rate(10**9, 1, 1.0) == pytest.approx(1.0)
+    assert bench.whole_job_rate(10**9, 4, 2.0) == pytest.approx(2.0)
