@@ -2,6 +2,7 @@
 the public header declares, and its host encoder agrees byte for byte with
 the oracle's (no GPU needed: the encoder is host code)."""
 import ctypes
+import os
 import subprocess
 
 import numpy as np
@@ -121,3 +122,41 @@ def test_host_encoder64_matches_oracle():
     assert vbyte.load().vbyte_max_encoded_size64(7) == 70
     for prev in (0, 12345, (1 << 64) - 1):
         assert np.array_equal(vbyte.encode_delta64(v, prev=prev), oracle.encode_delta64(v, prev=prev))
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include <stdint.h>
+#include "vbyte.h"
+#include "vbyte64.h"
+int main(void)
+{
+    const uint32_t v[3] = {1u, 300u, 0xFFFFFFFFu};
+    uint8_t out[15];
+    const uint64_t w[2] = {1u, 0xFFFFFFFFFFFFFFFFull};
+    uint8_t o64[20];
+    size_t nb = vbyte_encode(v, 3, out);
+    size_t nb64 = vbyte_encode64(w, 2, o64);
+    for (size_t i = 0; i < nb; ++i) printf("%02x", out[i]);
+    printf(" ");
+    for (size_t i = 0; i < nb64; ++i) printf("%02x", o64[i]);
+    printf(" %d\n", vbyte_decode(NULL, 16, NULL, 4, NULL));
+    return 0;
+}
+"""
+
+
+def test_plain_c_consumer(tmp_path):
+    """The public headers compile as C99 with warnings as errors, and a C
+    program links against libvbyte.so and calls its host entry points."""
+    vbyte.load()
+    src = tmp_path / "consumer.c"
+    src.write_text(C_CONSUMER)
+    exe = tmp_path / "consumer"
+    libdir = os.path.dirname(_build.LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", f"-I{_build.INCLUDE}", str(src),
+                    f"-L{libdir}", "-lvbyte", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out[0] == bytes(oracle.encode(np.array([1, 300, 0xFFFFFFFF], np.uint32))).hex()
+    assert out[1] == bytes(oracle.encode64(np.array([1, (1 << 64) - 1], np.uint64))).hex()
+    assert out[2] == "1"   # VBYTE_EINVAL, before any CUDA call
