@@ -1,0 +1,40 @@
+/*
+ * libvbyte -- fault injection for tests of the bounded waits.
+ *
+ * The paper has no counterpart: its decoder is one sequential loop.  The GPU
+ * decoders pass tile counts and running sums between CTAs through published
+ * words, and every wait for such a word is bounded by the global timer; when
+ * a bound runs out the launch records VBYTE_ERR_TIMEOUT in the status word,
+ * writes nothing outside [0, n) and returns.  This call makes that happen on
+ * purpose, with no GPU fault: a chosen tile's count is simply never
+ * published, so the wait for it runs out.  Not for production use.
+ */
+#ifndef VBYTE_DEBUG_H
+#define VBYTE_DEBUG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Process-wide, for the single-stream and batched decode launches queued
+ * after the call (vbyte_decode*, vbyte_decode_noalloc, the batched calls and
+ * plans created afterwards; a plan keeps the setting it was captured with):
+ *   skip_tile      index of the 4 KiB input tile (tile 0 starts at the input
+ *                  rounded down to 16 bytes) whose count descriptor is never
+ *                  published; < 0 for none (the default);
+ *   wait_limit_ns  bound of every wait between CTAs, in nanoseconds; 0 for
+ *                  the default of two seconds.
+ * Returns VBYTE_OK, or VBYTE_EINVAL for a limit above the default.  The
+ * output of a launch that timed out is unspecified within [0, n); read and
+ * clear the status word (vbyte_get_status) before the next call on that
+ * stream, since a recorded timeout makes every later wait give up at once. */
+int vbyte_debug_inject(long long skip_tile, uint64_t wait_limit_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBYTE_DEBUG_H */

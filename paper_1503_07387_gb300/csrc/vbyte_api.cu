@@ -6,11 +6,13 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
 
 #include "vbyte.h"
+#include "vbyte_debug.h"
 #include "vbyte_device.cuh"
 #include "vbyte_internal.h"
 
@@ -97,6 +99,13 @@ int enqueue_head_ranges(const uint8_t *in, size_t nbytes, const uint64_t *bo, co
 }
 
 __global__ void set_status_kernel(uint32_t *status, uint32_t bits) { atomicOr(status, bits); }
+
+// ---- fault injection (vbyte_debug.h)
+
+std::atomic<uint64_t> g_skip_tile{~0ull};
+std::atomic<uint64_t> g_wait_ns{kWaitLimitNs};
+
+FaultCfg fault_cfg() { return FaultCfg{g_skip_tile.load(), g_wait_ns.load()}; }
 
 // ---- per-stream workspaces
 
@@ -430,6 +439,14 @@ const char *vbyte_strerror(int code)
 }
 
 size_t vbyte_workspace_size(size_t nbytes) { return vbk::workspace_bound(nbytes); }
+
+int vbyte_debug_inject(long long skip_tile, uint64_t wait_limit_ns)
+{
+    if (wait_limit_ns > vbk::kWaitLimitNs) return VBYTE_EINVAL;
+    vbk::g_skip_tile.store(skip_tile < 0 ? ~0ull : static_cast<uint64_t>(skip_tile));
+    vbk::g_wait_ns.store(wait_limit_ns ? wait_limit_ns : vbk::kWaitLimitNs);
+    return VBYTE_OK;
+}
 
 int vbyte_set_workspace(void *stream, void *d_ws, size_t bytes)
 {

@@ -69,9 +69,10 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v)
 }
 
 // One thread waits until *p has one of the bits of `mask` set, bounded by
-// the global timer; on expiry, or once another wait of the launch has
-// expired, the status word has VBYTE_ERR_TIMEOUT and 0 is returned.
-__device__ __forceinline__ uint64_t wait_bits(const uint64_t *p, uint64_t mask, uint32_t *status)
+// the global timer (limit_ns); on expiry, or once another wait of the launch
+// has expired, the status word has VBYTE_ERR_TIMEOUT and 0 is returned.
+__device__ __forceinline__ uint64_t wait_bits(const uint64_t *p, uint64_t mask, uint32_t *status,
+                                              uint64_t limit_ns = kWaitLimitNs)
 {
     uint64_t t0 = 0;
     for (int spin = 0;; ++spin) {
@@ -79,7 +80,7 @@ __device__ __forceinline__ uint64_t wait_bits(const uint64_t *p, uint64_t mask, 
         if (v & mask) return v;
         const uint64_t now = global_ns();
         if (t0 == 0) t0 = now;
-        if (now - t0 > kWaitLimitNs) {
+        if (now - t0 > limit_ns) {
             atomicOr(status, VBYTE_ERR_TIMEOUT);
             return 0u;
         }
@@ -91,7 +92,10 @@ __device__ __forceinline__ uint64_t wait_bits(const uint64_t *p, uint64_t mask, 
 }
 
 // The same for bit 0 (a published word).
-__device__ __forceinline__ uint64_t wait_word(const uint64_t *p, uint32_t *status) { return wait_bits(p, 1u, status); }
+__device__ __forceinline__ uint64_t wait_word(const uint64_t *p, uint32_t *status, uint64_t limit_ns = kWaitLimitNs)
+{
+    return wait_bits(p, 1u, status, limit_ns);
+}
 
 // Bit i of the result is 1 iff byte i of w has its high bit clear (a
 // terminator).  The multiply moves bits 7, 15, 23, 31 to bits 28..31; the

@@ -34,6 +34,14 @@ struct LaunchCfg {
 };
 
 int check_batch(const BatchArgs &a);
+// Fault injection for tests of the bounded waits (vbyte_debug.h): the tile
+// whose count descriptor later decode launches leave unpublished (~0: none)
+// and the bound of every wait in them (ns).
+struct FaultCfg {
+    uint64_t skip_tile;
+    uint64_t wait_ns;
+};
+FaultCfg fault_cfg();
 // The per-stream workspace of s (current device) with at least need bytes;
 // its first 4 bytes are the stream's status word.
 int stream_workspace(cudaStream_t s, size_t need, uint8_t **ptr);

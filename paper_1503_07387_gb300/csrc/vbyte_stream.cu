@@ -107,6 +107,9 @@ struct Params {
     const uint32_t *prevs;     // per-list x_0 (nullptr: 0)
     uint64_t L;
     const uint64_t *hr;        // per tile: [first, end) of the lists whose head may own a terminator in it
+    // bounded waits and fault injection (tests of the timeout path)
+    uint64_t wait_ns;          // bound of every wait
+    uint64_t skip_tile;        // this tile's count is never published (~0: none)
 };
 
 struct Shared {
@@ -228,7 +231,7 @@ __device__ __forceinline__ unsigned int count_publish(const Params &p, uint64_t 
     const uint32_t ts = kDelta ? __reduce_add_sync(~0u, lane < kWarps ? S.csum[lane] : 0u) : 0u;
     unsigned int old = 0;
     if (lane == 0) {
-        st_relaxed_u64(p.tdesc + t, desc_word(tc, 0u, ts));
+        if (t != p.skip_tile) st_relaxed_u64(p.tdesc + t, desc_word(tc, 0u, ts));
         old = atomicAdd(p.cdone + t / kChunk, 1u);
     }
     return old;
@@ -270,7 +273,7 @@ __device__ void chunk_scan(const Params &p, uint64_t c, Shared &S)
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
         if (tb + i < c1) {
-            if (!(d[i] & 1u)) d[i] = wait_word(p.tdesc + tb + i, p.status);
+            if (!(d[i] & 1u)) d[i] = wait_word(p.tdesc + tb + i, p.status, p.wait_ns);
             Seg e;
             e.f = kSeg ? desc_flag(d[i]) : 0u;
             e.s = word_hi(d[i]);
@@ -324,8 +327,8 @@ __device__ void chunk_scan(const Params &p, uint64_t c, Shared &S)
         uint64_t pc = 0;
         uint32_t ps = p.prev;
         if (c > 0) {
-            pc = wait_word(p.cnext + 2 * (c - 1), p.status) >> 1;
-            ps = word_hi(wait_word(p.cnext + 2 * (c - 1) + 1, p.status));
+            pc = wait_word(p.cnext + 2 * (c - 1), p.status, p.wait_ns) >> 1;
+            ps = word_hi(wait_word(p.cnext + 2 * (c - 1) + 1, p.status, p.wait_ns));
         }
         st_relaxed_u64(p.cnext + 2 * c, ((pc + call) << 1) | 1u);
         st_relaxed_u64(p.cnext + 2 * c + 1, (static_cast<uint64_t>(seg_apply(ps, wall)) << 32) | 1u);
@@ -349,9 +352,9 @@ __device__ __forceinline__ void tile_prefix(const Params &p, uint64_t t, Shared 
         cn1 = S.pcn[b].y;
     }
     if (!(tp & cn0 & cn1 & 1u)) {   // not yet published when staged
-        if (!(tp & 1u)) tp = wait_word(p.tpre + t, p.status);
-        if (!(cn0 & 1u)) cn0 = wait_word(p.cnext + 2 * (c - 1), p.status);
-        if (!(cn1 & 1u)) cn1 = wait_word(p.cnext + 2 * (c - 1) + 1, p.status);
+        if (!(tp & 1u)) tp = wait_word(p.tpre + t, p.status, p.wait_ns);
+        if (!(cn0 & 1u)) cn0 = wait_word(p.cnext + 2 * (c - 1), p.status, p.wait_ns);
+        if (!(cn1 & 1u)) cn1 = wait_word(p.cnext + 2 * (c - 1) + 1, p.status, p.wait_ns);
     }
     const uint32_t rel = static_cast<uint32_t>(tp >> 1) & 0x7FFFFFu;
     const uint32_t s = word_hi(tp);
@@ -783,7 +786,7 @@ __device__ __forceinline__ unsigned int count_publish_seg(const Params &p, uint6
     const uint32_t f = __shfl_sync(~0u, ws.f, 31), sm = __shfl_sync(~0u, ws.s, 31);
     unsigned int old = 0;
     if (lane == 0) {
-        st_relaxed_u64(p.tdesc + t, desc_word(tc, f, sm));
+        if (t != p.skip_tile) st_relaxed_u64(p.tdesc + t, desc_word(tc, f, sm));
         old = atomicAdd(p.cdone + t / kChunk, 1u);
     }
     return old;
@@ -1170,6 +1173,9 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
     p.status = status;
     p.prev = prev;
     p.lead = std::min<uint64_t>(sd::kChunk + sd::kSlack, ntiles);
+    const FaultCfg fc = fault_cfg();
+    p.wait_ns = fc.wait_ns;
+    p.skip_tile = fc.skip_tile;
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * di.occ[delta]);
     if (!sd::tickets_fit(ntiles, p.lead, grid)) return VBYTE_EINVAL;
     if (rank)
@@ -1242,6 +1248,9 @@ int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cuda
     p.prevs = a.prevs;
     p.L = a.L;
     p.hr = hr;
+    const FaultCfg fc = fault_cfg();
+    p.wait_ns = fc.wait_ns;
+    p.skip_tile = fc.skip_tile;
     const int occ = di.occ_seg[a.delta];
     const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
     const uint64_t grid = std::min<uint64_t>(ntiles + p.lead, static_cast<uint64_t>(di.sms) * per_sm);

@@ -34,7 +34,7 @@ ERR_TIMEOUT = 8
 ERR_BAD_OFFSETS = 16
 
 HEADER = os.path.join(_build.INCLUDE, "vbyte.h")
-HEADERS = [HEADER, os.path.join(_build.INCLUDE, "vbyte64.h")]
+HEADERS = [HEADER, os.path.join(_build.INCLUDE, "vbyte64.h"), os.path.join(_build.INCLUDE, "vbyte_debug.h")]
 
 _lib = None
 
@@ -80,6 +80,7 @@ def _signatures(lib):
         "vbyte_workspace_size": ([S], S),
         "vbyte_set_workspace": ([P, P, S], I),
         "vbyte_release_stream": ([P], I),
+        "vbyte_debug_inject": ([ctypes.c_longlong, ctypes.c_uint64], I),
         "vbyte_max_encoded_size64": ([S], S),
         "vbyte_encode64": ([P, S, P], S),
         "vbyte_encode_delta64": ([P, S, ctypes.c_uint64, P], S),
@@ -539,6 +540,13 @@ def decode_delta64(data, n: int, prev: int = 0, out=None, stream=None):
                                      ctypes.c_uint64(prev & MASK64), _stream_handle(stream))
     _check(rc, "vbyte_decode_delta64")
     return out
+
+
+def debug_inject(skip_tile: int = -1, wait_limit_ns: int = 0):
+    """vbyte_debug_inject: make later decode launches leave tile skip_tile's
+    count unpublished and bound their waits by wait_limit_ns (tests of the
+    timeout path; skip_tile < 0 and 0 restore the defaults)."""
+    _check(load().vbyte_debug_inject(int(skip_tile), int(wait_limit_ns)), "vbyte_debug_inject")
 
 
 def get_status(stream=None) -> int:

@@ -129,6 +129,7 @@ C_CONSUMER = r"""
 #include <stdint.h>
 #include "vbyte.h"
 #include "vbyte64.h"
+#include "vbyte_debug.h"
 int main(void)
 {
     const uint32_t v[3] = {1u, 300u, 0xFFFFFFFFu};
@@ -140,7 +141,8 @@ int main(void)
     for (size_t i = 0; i < nb; ++i) printf("%02x", out[i]);
     printf(" ");
     for (size_t i = 0; i < nb64; ++i) printf("%02x", o64[i]);
-    printf(" %d\n", vbyte_decode(NULL, 16, NULL, 4, NULL));
+    printf(" %d", vbyte_decode(NULL, 16, NULL, 4, NULL));
+    printf(" %d\n", vbyte_debug_inject(-1, 3000000000ull));
     return 0;
 }
 """
@@ -160,3 +162,4 @@ def test_plain_c_consumer(tmp_path):
     assert out[0] == bytes(oracle.encode(np.array([1, 300, 0xFFFFFFFF], np.uint32))).hex()
     assert out[1] == bytes(oracle.encode64(np.array([1, (1 << 64) - 1], np.uint64))).hex()
     assert out[2] == "1"   # VBYTE_EINVAL, before any CUDA call
+    assert out[3] == "1"   # a wait bound above the default is refused
