@@ -1,27 +1,38 @@
 """Benchmark: VByte decoding throughput on GB300 (Gints/s and % of HBM roofline).
 
-Default workload (one "step" = one pass of the whole hot path over one batch):
-differential decoding of two single streams of 2^26 uint32 each --
-  stream A: gaps 1 + Geometric(0.1) (first gap 0), almost all one-byte codes;
-  stream B: gaps uniform in [1, 300], a dense mix of one- and two-byte codes --
-VByte-encoded on the host, resident in HBM, decoded and prefix-summed back to
-document ids (uint32 wrap-around).  Inputs plus outputs exceed the 129 MB L2,
-so no flush is needed between steps.  A smaller workload (--workload
-plain_uniform_bits_1e6, about 6.7 MB) is timed with L2 flushed before every
-step, its value taken from the launches' own events, and a warm-L2 figure
-beside it.
+One "step" is one pass of the whole hot path over one batch of synthetic
+input.  The default (headline) workload is the roofline-stress configuration:
+two single streams of 2^28 uint32 each, resident in HBM --
+  * one- or two-byte codes by a fair coin (the branch-misprediction case of
+    the paper's Sec. 2), about 0.375 GiB compressed;
+  * uniform full-range uint32 (mostly five-byte codes), about 1.23 GiB --
+each decoded plainly and differentially (the same bytes read as gaps and
+prefix-summed back with uint32 wrap-around): four launches per step.  Inputs
+plus outputs exceed the 129 MB L2, so no flush is needed between steps.
+
+The same JSON line carries a block per other configuration, each with its own
+roofline and single-core oracle baseline: 10^6 plain values of every code
+length (about 6.7 MB, timed with L2 flushed before every step and warm beside
+it), the two differential 2^26 streams (geometric and uniform [1, 300] gaps),
+and every stream of the headline separately; then batched decoding of 100,000
+rank-Zipf posting lists (a tuned plan replayed from a CUDA graph against one
+call per list, with an all-cores oracle baseline), the serving loop at
+Poisson query rates, the device encoder and the 64-bit decoder.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload differential_2x2^26 | ...]
+                    [--workload roofline_stress_2^28 | ...]
 
 Under torchrun (N > 1) every rank decodes its own replica of the workload
 (the path shards into independent streams; no data-path collective); rank 0
-prints one JSON line with the whole-job throughput.  ``--impl reference`` times
-the CPU oracle (Algorithm 1, one core) on the same workload instead.
+prints one JSON line with the whole-job throughput.  ``--impl reference``
+times the CPU oracle (Algorithm 1, one core) on the same workload instead.
+``--profile-case NAME`` runs one small stream a few times (for ncu) and prints
+nothing else.
 """
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -29,7 +40,6 @@ import re
 import statistics
 import subprocess
 import sys
-import tempfile
 import threading
 import time
 
@@ -42,32 +52,71 @@ from paper_1503_07387_gb300 import inputs  # noqa: E402
 
 METRIC = "Gints/s decoded + % of HBM roofline"
 UNIT = "Gints/s"
-PROFILE_FILE = os.path.join(ROOT, "profiles", "decode_delta_differential_2x2^26.md")
+PROFILES = os.path.join(ROOT, "profiles")
 L2_FLUSH_BYTES = 256 << 20   # about twice the GB300's 129 MB L2
+NOMINAL_HBM_GBS = 8000.0
 
 
 # ------------------------------------------------------------------ workloads --
+#
+# A workload is a list of streams (label, values-to-encode generator, delta).
+# For differential streams the values are the gaps; streams with the same
+# `src` share their bytes (plain and differential readings of one stream).
 
-def workload(name: str):
-    """Returns a list of (label, values_to_encode, delta) streams."""
-    if name == "differential_2x2^26":
-        return [("geometric_gaps", inputs.geometric_gaps(1 << 26, seed=0), True),
-                ("uniform_gaps_1_300", inputs.uniform_gaps(1 << 26, seed=1), True)]
-    if name == "plain_uniform_bits_1e6":
-        return [("uniform_bits", inputs.uniform_bits(1_000_000, seed=0), False)]
-    if name == "plain_one_two_2^28":
-        return [("one_two_byte_mix", inputs.one_two_byte_mix(1 << 28, seed=0), False)]
-    if name == "delta_one_two_2^28":
-        return [("one_two_byte_mix", inputs.one_two_byte_mix(1 << 28, seed=0), True)]
-    if name == "plain_full_range_2^28":
-        return [("full_range", inputs.full_range(1 << 28, seed=0), False)]
-    if name == "delta_full_range_2^28":
-        return [("full_range", inputs.full_range(1 << 28, seed=0), True)]
-    raise SystemExit(f"unknown workload {name}")
+def _src(name: str):
+    gens = {
+        "uniform_bits_1e6": lambda: inputs.uniform_bits(1_000_000, seed=0),
+        "geometric_gaps_2^26": lambda: inputs.geometric_gaps(1 << 26, seed=0),
+        "uniform_gaps_1_300_2^26": lambda: inputs.uniform_gaps(1 << 26, seed=1),
+        "one_two_byte_mix_2^28": lambda: inputs.one_two_byte_mix(1 << 28, seed=0),
+        "full_range_2^28": lambda: inputs.full_range(1 << 28, seed=0),
+    }
+    return gens[name]()
 
 
-WORKLOADS = ["differential_2x2^26", "plain_uniform_bits_1e6", "plain_one_two_2^28",
-             "delta_one_two_2^28", "plain_full_range_2^28", "delta_full_range_2^28"]
+WORKLOADS = {
+    # config 5: the roofline stress streams, plain and differential (the headline)
+    "roofline_stress_2^28": [("one_two_byte_mix_plain", "one_two_byte_mix_2^28", False),
+                             ("one_two_byte_mix_delta", "one_two_byte_mix_2^28", True),
+                             ("full_range_plain", "full_range_2^28", False),
+                             ("full_range_delta", "full_range_2^28", True)],
+    # config 1: plain decode of 10^6 values of every code length
+    "plain_uniform_bits_1e6": [("uniform_bits", "uniform_bits_1e6", False)],
+    # config 2: differential decode of two 2^26 document-id streams
+    "differential_2x2^26": [("geometric_gaps", "geometric_gaps_2^26", True),
+                            ("uniform_gaps_1_300", "uniform_gaps_1_300_2^26", True)],
+    # single streams of config 5, for experiments and profiles
+    "plain_one_two_2^28": [("one_two_byte_mix_plain", "one_two_byte_mix_2^28", False)],
+    "delta_one_two_2^28": [("one_two_byte_mix_delta", "one_two_byte_mix_2^28", True)],
+    "plain_full_range_2^28": [("full_range_plain", "full_range_2^28", False)],
+    "delta_full_range_2^28": [("full_range_delta", "full_range_2^28", True)],
+}
+HEADLINE = "roofline_stress_2^28"
+BLOCKS = ["plain_uniform_bits_1e6", "differential_2x2^26"]   # reported beside the headline
+
+# Small cases for ncu captures (one stream, larger than L2, a few launches).
+PROFILE_CASES = {
+    "one_two_plain_2^26": ("one_two_byte_mix", 1 << 26, False),
+    "one_two_delta_2^26": ("one_two_byte_mix", 1 << 26, True),
+    "full_range_plain_2^26": ("full_range", 1 << 26, False),
+    "full_range_delta_2^26": ("full_range", 1 << 26, True),
+    "geometric_delta_2^26": ("geometric_gaps", 1 << 26, True),
+    "uniform300_delta_2^26": ("uniform_gaps", 1 << 26, True),
+}
+
+
+def encode_workload(name: str, encoder):
+    """[(label, n, delta, bytes)] with bytes shared between streams of one source."""
+    cache = {}
+    out = []
+    for label, src, delta in WORKLOADS[name]:
+        if src not in cache:
+            v = _src(src)
+            cache[src] = (int(v.size), encoder(v))
+            del v
+        n, b = cache[src]
+        out.append((label, n, delta, b, src))
+    return out
 
 
 # --------------------------------------------------------------- environment --
@@ -99,7 +148,7 @@ def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
 
 # the translation unit of the decode kernels and every header it includes
 KERNEL_SOURCES = ["paper_1503_07387_gb300/csrc/vbyte_stream.cu", "paper_1503_07387_gb300/csrc/vbyte_device.cuh",
-                  "paper_1503_07387_gb300/csrc/vbyte_internal.h", "include/vbyte.h"]
+                  "paper_1503_07387_gb300/csrc/vbyte_internal.h"]
 
 
 def _code_only(src: str) -> str:
@@ -118,17 +167,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the kernel source that is built now (else None)."""
-    try:
-        text = open(PROFILE_FILE).read()
-    except OSError:
-        return None
-    m_hash = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
-    m_traffic = re.search(r"dram bytes per launch \(full workload\):\s*([0-9.eE+]+)", text)
-    if m_hash and m_traffic and m_hash.group(1) == src_hash:
-        return float(m_traffic.group(1))
+def profiled_traffic(src_hash: str, label: str, profiles_dir: str = PROFILES):
+    """DRAM bytes per launch of stream `label` at its full size, from a
+    committed ncu summary taken on the kernel source that is built now (else
+    None).  A summary names its source hash once and has lines
+    ``dram bytes per launch (full workload) [label]: X``."""
+    for path in sorted(glob.glob(os.path.join(profiles_dir, "*.md"))):
+        text = open(path).read()
+        m_hash = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
+        if not m_hash or m_hash.group(1) != src_hash:
+            continue
+        m = re.search(r"dram bytes per launch \(full workload\) \[" + re.escape(label) + r"\]:\s*([0-9.eE+]+)",
+                      text)
+        if m:
+            return float(m.group(1))
     return None
 
 
@@ -137,6 +189,13 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         return None
+
+
+def hbm_peak():
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        return float(peaks["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "of fallback (6.8 TB/s)"
 
 
 class ClockSampler:
@@ -157,7 +216,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", f"-lms", str(self.period)],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -208,6 +267,124 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- GPU arm --
 
+def _gpu_streams(name: str):
+    """Encode (the library's host encoder) and move a workload to the device."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    dev = {}
+    streams = []
+    for label, n, delta, b, src in encode_workload(name, vbyte.encode):
+        if src not in dev:
+            dev[src] = torch.from_numpy(b).cuda()
+        streams.append(dict(label=label, n=n, delta=delta, host=b, d_in=dev[src],
+                            d_out=torch.empty(n, dtype=torch.uint32, device="cuda")))
+    torch.cuda.synchronize()
+    return streams
+
+
+def _launch(vbyte, s, stream):
+    if s["delta"]:
+        vbyte.decode_delta(s["d_in"], s["n"], out=s["d_out"], stream=stream)
+    else:
+        vbyte.decode(s["d_in"], s["n"], out=s["d_out"], stream=stream)
+
+
+def time_streams(streams, steps: int, warmup: int, stream, ws: int = 1, sampler=None):
+    """W untimed steps, then K timed steps bracketed by a barrier and a device
+    synchronisation on both sides, every launch with its own CUDA events on
+    the launching stream.  A workload smaller than 256 MiB is timed with L2
+    flushed before every step (a write larger than L2, outside the launches'
+    events) and its time is the sum of the launches' event times; a warm-L2
+    figure is taken beside it."""
+    import torch
+    import torch.distributed as dist
+    from paper_1503_07387_gb300 import vbyte
+
+    def step(events=None):
+        for i, s in enumerate(streams):
+            if events is not None:
+                events[i][0].record(stream)
+            _launch(vbyte, s, stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if vbyte.get_status() != 0:
+        raise SystemExit("data error during warm-up")
+    algo = sum(int(s["host"].size) + 4 * s["n"] for s in streams)
+    l2_resident = algo < L2_FLUSH_BYTES
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda") if l2_resident else None
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in streams]
+          for _ in range(steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler is not None:
+        sampler.mark("start")
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        step(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if sampler is not None:
+        sampler.mark("end")
+    if ws > 1:
+        dist.barrier()
+    launch_ms = [[e[0].elapsed_time(e[1]) for e in row] for row in ev]
+    elapsed = t0.elapsed_time(t1)
+    warm = None
+    if flush is not None:
+        elapsed = sum(x for row in launch_ms for x in row)   # the flushes are not decoding
+        del flush
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        for _ in range(steps):
+            step()
+        w1.record(stream)
+        torch.cuda.synchronize()
+        warm = w0.elapsed_time(w1)
+    status = vbyte.get_status()
+    return dict(elapsed_ms=elapsed, launch_ms=launch_ms, warm_ms=warm, status=status, l2_resident=l2_resident)
+
+
+def roofline_of(streams, launch_ms, peak, peak_source, src_hash, kernel):
+    """The dominant kernel's roofline over a step: algorithmic bytes (input
+    read once + 4 bytes per value written) per launch over its CUDA-event
+    duration, averaged over the step's launches."""
+    nl = len(launch_ms)
+    per_stream_ms = [sum(row[i] for row in launch_ms) / nl for i in range(len(streams))]
+    algo = [int(s["host"].size) + 4 * s["n"] for s in streams]
+    bytes_per_launch = sum(algo) / len(streams)
+    avg_ms = sum(per_stream_ms) / len(streams)
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    tr = [profiled_traffic(src_hash, s["label"]) for s in streams]
+    traffic = sum(tr) / len(tr) if all(t is not None for t in tr) else None
+    rows = []
+    for s, ms, a, t in zip(streams, per_stream_ms, algo, tr):
+        gbs = a / (ms * 1e-3) / 1e9
+        rows.append({"label": s["label"], "n": s["n"], "nbytes": int(s["host"].size),
+                     "mode": "differential" if s["delta"] else "plain", "avg_launch_ms": round(ms, 5),
+                     "gints_per_s": round(s["n"] / (ms * 1e-3) / 1e9, 3), "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / peak, 4), "frac_of_nominal_8000_gbs": round(gbs / NOMINAL_HBM_GBS, 4),
+                     "traffic": t})
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_source,
+            "frac_of_nominal_8000_gbs": round(achieved / NOMINAL_HBM_GBS, 4), "traffic": traffic,
+            "kernel": kernel, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": round(avg_ms, 5), "kernel_source_hash": src_hash, "streams": rows}
+
+
+def kernel_name(vbyte, streams):
+    passes = {vbyte.chosen_passes(int(s["host"].size), s["n"], s["delta"]) for s in streams}
+    names = {1: "onepass_kernel (single pass, decoupled look-back)", 2: "sdecode_kernel (count then decode)"}
+    return " + ".join(names[p] for p in sorted(passes))
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -218,139 +395,68 @@ def run_gpu(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     vbyte.load()
-
-    streams = []
-    for label, vals, delta in workload(args.workload):
-        # values are the integers to code; for differential streams they are the gaps
-        data = vbyte.encode(vals)
-        streams.append(dict(label=label, n=int(vals.size), delta=delta, host=data,
-                            d_in=torch.from_numpy(data).cuda(),
-                            d_out=torch.empty(vals.size, dtype=torch.uint32, device="cuda")))
-        del vals
-    torch.cuda.synchronize()
-    total_vals = sum(s["n"] for s in streams)
-    algo_bytes = sum(s["host"].size + 4 * s["n"] for s in streams)
+    if args.passes:
+        vbyte.debug_force_passes(args.passes)
     stream = torch.cuda.current_stream()
+    peak, peak_source = hbm_peak()
+    src_hash = kernel_source_hash()
 
-    def step(events=None):
-        for i, s in enumerate(streams):
-            if events is not None:
-                events[i][0].record(stream)
-            if s["delta"]:
-                vbyte.decode_delta(s["d_in"], s["n"], out=s["d_out"], stream=stream)
-            else:
-                vbyte.decode(s["d_in"], s["n"], out=s["d_out"], stream=stream)
-            if events is not None:
-                events[i][1].record(stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if vbyte.get_status() != 0:
-        raise SystemExit("data error during warm-up")
-    # A workload whose inputs and outputs fit in L2 is timed with L2 flushed
-    # before every step (a write larger than L2, outside the launches' events).
-    l2_resident = algo_bytes < L2_FLUSH_BYTES
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda") if l2_resident else None
-
+    streams = _gpu_streams(args.workload)
+    total_vals = sum(s["n"] for s in streams)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.5)
-    per_launch = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-                   for _ in streams] for _ in range(args.steps)]
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.mark("start")
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for k in range(args.steps):
-        if flush is not None:
-            flush.fill_(k & 0xFF)
-        step(per_launch[k])
-    t1.record(stream)
-    torch.cuda.synchronize()
-    sampler.mark("end")
-    if ws > 1:
-        dist.barrier()
+    t = time_streams(streams, args.steps, args.warmup, stream, ws, sampler)
     clocks = sampler.stop()
-    elapsed_ms = t0.elapsed_time(t1)
-    launch_ms = [[ev[0].elapsed_time(ev[1]) for ev in row] for row in per_launch]
+    elapsed_ms = max_over_ranks(t["elapsed_ms"], ws, "cuda")
+    roof = roofline_of(streams, t["launch_ms"], peak, peak_source, src_hash, kernel_name(vbyte, streams))
     warm = None
-    if flush is not None:
-        elapsed_ms = sum(x for row in launch_ms for x in row)   # the flushes are not decoding
-        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        w0.record(stream)
-        for _ in range(args.steps):
-            step()
-        w1.record(stream)
-        torch.cuda.synchronize()
-        warm_ms = w0.elapsed_time(w1)
-        warm = {"value": round(whole_job_rate(total_vals * args.steps, 1, warm_ms * 1e-3), 3), "unit": UNIT,
-                "ms_per_step": round(warm_ms / args.steps, 5),
+    if t["warm_ms"] is not None:
+        warm = {"value": round(whole_job_rate(total_vals * args.steps, 1, t["warm_ms"] * 1e-3), 3), "unit": UNIT,
+                "ms_per_step": round(t["warm_ms"] / args.steps, 5),
                 "note": "the same steps back to back with L2 warm (inputs and outputs resident)"}
-        del flush
-    status = vbyte.get_status()
-
-    elapsed_ms = max_over_ranks(elapsed_ms, ws, "cuda")
+    status = t["status"]
 
     # ---- end to end through the public host-buffer call (copies inside)
-    pinned_in = [torch.from_numpy(s["host"]).pin_memory() for s in streams]
-    pinned_out = [torch.empty(s["n"], dtype=torch.int32).pin_memory() for s in streams]
-    h_in = [p.numpy() for p in pinned_in]
-    h_out = [p.numpy().view(np.uint32) for p in pinned_out]
-    e2e_steps = max(3, min(args.steps, 20))
-    for i, s in enumerate(streams):
-        vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
-    if ws > 1:
-        dist.barrier()
-    te = time.perf_counter()
-    for _ in range(e2e_steps):
-        for i, s in enumerate(streams):
-            vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
-    e2e_s = time.perf_counter() - te
-    e2e_s = max_over_ranks(e2e_s, ws, "cuda")
-    status |= vbyte.get_status()
-
-    # ---- the device encoder on the same streams (the step before the path)
-    encode = None
-    if not args.no_encode:
-        encode = run_encode(args, streams, stream, measured_peaks())
-
-    # ---- 64-bit integers
-    decode64 = None
-    if not args.no_decode64:
-        try:
-            decode64 = run_decode64(args, stream, measured_peaks())
-        except Exception as e:   # an auxiliary leg: report it, keep the headline line
-            decode64 = {"error": f"{type(e).__name__}: {e}"}
-
-    # ---- batched lists: one tuned, graph-replayed launch vs one call per list
-    batched = serving = None
-    if ws == 1 and not args.no_batched:
-        batched, pool = run_batched(args, measured_peaks())
-        if not args.no_serving:
-            serving = run_serving(args, pool)
-        del pool
+    e2e = run_e2e(args, streams, stream, ws)
+    status |= e2e.pop("status")
 
     # ---- CPU baseline (rank 0, N = 1 only): the oracle as it stands
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(streams, budget_s=args.cpu_seconds)
 
+    for s in streams:
+        del s["d_in"], s["d_out"]
+    del streams
+    torch.cuda.empty_cache()
+
+    # ---- the other single-stream configurations, each with its own roofline
+    blocks = {}
+    if ws == 1 and not args.no_blocks:
+        for name in [b for b in BLOCKS if b != args.workload]:
+            blocks[name] = run_block(args, name, stream, peak, peak_source, src_hash)
+
+    encode = decode64 = batched = serving = None
+    if ws == 1:
+        if not args.no_encode:
+            encode = run_encode(args, stream, peak)
+        if not args.no_decode64:
+            try:
+                decode64 = run_decode64(args, stream, peak)
+            except Exception as e:   # an auxiliary leg: report it, keep the headline line
+                decode64 = {"error": f"{type(e).__name__}: {e}"}
+        if not args.no_batched:
+            batched, pool = run_batched(args, peak)
+            if not args.no_serving:
+                serving = run_serving(args, pool)
+            del pool
+
     if rank != 0:
         dist.destroy_process_group()
         return
-    peaks = measured_peaks()
-    peak_gbs = peaks["hbm_gbs"] if peaks else 6800.0
-    launches = [x for row in launch_ms for x in row]
-    avg_launch_ms = sum(launches) / len(launches)
-    bytes_per_launch = algo_bytes / len(streams)
-    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
-    src_hash = kernel_source_hash()
-    traffic = profiled_traffic(src_hash)
     value = whole_job_rate(total_vals * args.steps, ws, elapsed_ms * 1e-3)
+    wl = WORKLOADS[args.workload]
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -366,68 +472,113 @@ def run_gpu(args):
         "data": "synthetic (seeded generators shaped like the paper's posting lists)",
         "config": {
             "workload": args.workload,
-            "streams": [{"label": s["label"], "n": s["n"], "nbytes": int(s["host"].size),
-                         "mode": "differential" if s["delta"] else "plain"} for s in streams],
+            "streams": [{"label": lab, "source": src, "mode": "differential" if d else "plain"}
+                        for lab, src, d in wl],
             "values_per_step": total_vals,
             "l2": ("L2 flushed before every step (a 256 MiB write outside the launches' events); "
                    "value from the launches' event times" if warm is not None else
                    "inputs and outputs larger than the 129 MB L2; no flush"),
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "kernel_choice": "forced" if args.passes else "library default",
         },
-        "roofline": {
-            "bound": "hbm",
-            "achieved": round(achieved, 1),
-            "peak": peak_gbs,
-            "unit": "GB/s",
-            "frac": round(achieved / peak_gbs, 4),
-            "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
-            "frac_of_nominal_8000_gbs": round(achieved / 8000.0, 4),
-            "traffic": traffic,
-            "kernel": "sdecode_kernel<delta>" if all(s["delta"] for s in streams) else "sdecode_kernel",
-            "algorithmic_bytes_per_launch": bytes_per_launch,
-            "avg_launch_ms": round(avg_launch_ms, 5),
-            "kernel_source_hash": src_hash,
-        },
-        "e2e": {
-            "value": round(whole_job_rate(total_vals * e2e_steps, ws, e2e_s), 3),
-            "unit": UNIT,
-            "h2d_bytes_per_step": int(sum(s["host"].size for s in streams)),
-            "d2h_bytes_per_step": int(4 * total_vals),
-            "api": "vbyte_decode_host (pinned host buffers, copies inside the call)",
-        },
-        "gpu_launches": len(streams) * args.steps,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": len(wl) * args.steps,
         "warm": warm,
-        "encode": encode,
-        "decode64": decode64,
-        "batched": batched,
-        "serving": serving,
         "status": status,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "host_cores": os.cpu_count(),
+        "configs": blocks,
+        "batched": batched,
+        "serving": serving,
+        "encode": encode,
+        "decode64": decode64,
     }
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
 
 
-def run_encode(args, streams, stream, peaks):
-    """Device encoding of the decoded streams (differential streams from their
-    document ids), checked byte for byte against the encoded input and timed
-    with CUDA events: Gints/s and the HBM roofline (4n read + bytes written)."""
+def run_e2e(args, streams, stream, ws):
+    """The same metric through vbyte_decode_host: every step copies the inputs
+    from page-locked host memory and the decoded values back, inside the call."""
     import torch
     from paper_1503_07387_gb300 import vbyte
-    bufs = [torch.empty(5 * s["n"], dtype=torch.uint8, device="cuda") for s in streams]
-    nbs = [torch.empty(1, dtype=torch.int64, device="cuda") for _ in streams]
+    import torch.distributed as dist
+    pinned = {}
+    h_in, h_out = [], []
+    for s in streams:
+        key = id(s["host"])
+        if key not in pinned:
+            pinned[key] = torch.from_numpy(s["host"]).pin_memory()
+        h_in.append(pinned[key].numpy())
+        h_out.append(torch.empty(s["n"], dtype=torch.int32).pin_memory().numpy().view(np.uint32))
+    e2e_steps = max(3, min(args.steps, args.e2e_steps))
+    for i, s in enumerate(streams):
+        vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
+    if ws > 1:
+        dist.barrier()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, s in enumerate(streams):
+            vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
+    e2e_s = max_over_ranks(time.perf_counter() - te, ws, "cuda")
+    status = vbyte.get_status()
+    total = sum(s["n"] for s in streams)
+    return {"value": round(whole_job_rate(total * e2e_steps, ws, e2e_s), 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(s["host"].size for s in streams)),
+            "d2h_bytes_per_step": int(4 * total), "steps": e2e_steps,
+            "api": "vbyte_decode_host (pinned host buffers, copies inside the call)", "status": status}
+
+
+def run_block(args, name, stream, peak, peak_source, src_hash):
+    """One more configuration: its own timing, roofline and oracle baseline."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    streams = _gpu_streams(name)
+    steps = max(5, min(args.steps, 200))
+    t = time_streams(streams, steps, 3, stream)
+    total = sum(s["n"] for s in streams)
+    res = {"value": round(whole_job_rate(total * steps, 1, t["elapsed_ms"] * 1e-3), 3), "unit": UNIT,
+           "steps": steps, "ms_per_step": round(t["elapsed_ms"] / steps, 5), "status": t["status"],
+           "l2": "flushed before every step; value from the launches' event times" if t["l2_resident"]
+           else "inputs and outputs larger than L2; no flush",
+           "roofline": roofline_of(streams, t["launch_ms"], peak, peak_source, src_hash, kernel_name(vbyte, streams))}
+    if t["warm_ms"] is not None:
+        res["warm"] = {"value": round(whole_job_rate(total * steps, 1, t["warm_ms"] * 1e-3), 3), "unit": UNIT}
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(streams, budget_s=max(1.0, args.cpu_seconds / 4))
+    for s in streams:
+        del s["d_in"], s["d_out"]
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_encode(args, stream, peak):
+    """Device encoding of the two differential 2^26 streams' document ids,
+    checked byte for byte against the host encoder and timed with CUDA events:
+    Gints/s and the HBM roofline (4n read + bytes written)."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    cases = []
+    for gen, seed in (("geometric_gaps", 0), ("uniform_gaps", 1)):
+        g = getattr(inputs, gen)(1 << 26, seed=seed)
+        x = np.cumsum(g.astype(np.uint64)).astype(np.uint32)
+        want = vbyte.encode_delta(x, prev=0)
+        cases.append(dict(n=x.size, want=torch.from_numpy(want).cuda(), nb=int(want.size),
+                          x=torch.from_numpy(x.view(np.int32)).cuda(),
+                          buf=torch.empty(5 * x.size, dtype=torch.uint8, device="cuda"),
+                          d_nb=torch.empty(1, dtype=torch.int64, device="cuda")))
 
     def step():
-        for s, b, nb in zip(streams, bufs, nbs):
-            vbyte.encode_device(s["d_out"], delta=s["delta"], out=b, nbytes=nb, stream=stream)
+        for c in cases:
+            vbyte.encode_device(c["x"], delta=True, out=c["buf"], nbytes=c["d_nb"], stream=stream)
 
     for _ in range(3):
         step()
     torch.cuda.synchronize()
-    exact = all(int(nb.item()) == s["host"].size and torch.equal(b[:s["host"].size], s["d_in"])
-                for s, b, nb in zip(streams, bufs, nbs))
+    exact = all(int(c["d_nb"].item()) == c["nb"] and torch.equal(c["buf"][:c["nb"]], c["want"]) for c in cases)
     reps = max(5, min(args.steps, 200))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -436,25 +587,24 @@ def run_encode(args, streams, stream, peaks):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    n = sum(s["n"] for s in streams)
-    algo = sum(4 * s["n"] + s["host"].size for s in streams)
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    n = sum(c["n"] for c in cases)
+    algo = sum(4 * c["n"] + c["nb"] for c in cases)
     achieved = algo / (ms * 1e-3) / 1e9
-    del bufs
+    del cases
     return {"value": round(n / (ms * 1e-3) / 1e9, 3), "unit": "Gints/s", "ms_per_step": round(ms, 5),
-            "form": "vbyte_encode_device / vbyte_encode_delta_device, one launch per stream",
-            "bit_exact_with_input": bool(exact), "status": int(vbyte.get_status()),
+            "form": "vbyte_encode_delta_device, one launch per stream (2 x 2^26 document ids)",
+            "bit_exact_with_host_encoder": bool(exact), "status": int(vbyte.get_status()),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes_per_step": algo}}
 
 
-def run_decode64(args, stream, peaks):
+def run_decode64(args, stream, peak):
     """64-bit VByte decoding (the format read for uint64): 2^26 sorted uint64
     document ids from 1 + Geometric(0.1) gaps above 2^40 (differential, almost
     all one-byte codes) and 2^26 values of every bit width 0..64 (plain, code
     lengths 1..10), checked bit for bit against the values the streams were
-    built from and timed with CUDA events over the three launches of each
-    call: Gints/s and the HBM roofline (input bytes + 8n per call)."""
+    built from and timed with CUDA events: Gints/s and the HBM roofline
+    (input bytes + 8n per call)."""
     import torch
     from paper_1503_07387_gb300 import vbyte
     n = 1 << 26
@@ -472,7 +622,6 @@ def run_decode64(args, stream, peaks):
         else:
             vbyte.decode64(c["d_in"], n, out=c["out"], stream=stream)
 
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
     reps = max(5, min(args.steps, 200))
     res = []
     for c in cases:
@@ -496,16 +645,17 @@ def run_decode64(args, stream, peaks):
     status = int(vbyte.get_status())
     for c in cases:
         del c["d_in"], c["out"]
-    return {"form": "vbyte_decode_delta64 / vbyte_decode64 (count, scan and decode launches per call)",
-            "status": status, "streams": res}
+    return {"form": "vbyte_decode_delta64 / vbyte_decode64", "status": status, "streams": res}
 
 
-def run_batched(args, peaks):
+def run_batched(args, peak):
     """Batched differential decoding of 100,000 rank-Zipf posting lists (about
     1.2e8 values): a tuned plan replayed from a CUDA graph against one
-    vbyte_decode_delta call per list, both bit-exact and timed with CUDA
-    events on the same stream."""
+    vbyte_decode_delta call per list, both checked against the oracle's
+    per-list decoding and timed with CUDA events on the same stream; the
+    oracle itself timed on all host cores."""
     import torch
+    import oracle
     from paper_1503_07387_gb300 import vbyte
     ids, vo = inputs.posting_lists()
     L = vo.size - 1
@@ -513,10 +663,12 @@ def run_batched(args, peaks):
     hb, hbo = vbyte.encode_batched(ids, vo, True, prev)
     n = int(vo[-1])
     del ids
+    want, _ = oracle.decode_batched(hb, hbo, vo, True, prev, threads=os.cpu_count() or 1)
     d = torch.from_numpy(hb).cuda()
     dbo = torch.from_numpy(hbo.view(np.int64)).cuda()
     dvo = torch.from_numpy(vo.view(np.int64)).cuda()
     dp = torch.from_numpy(prev.view(np.int32)).cuda()
+    dwant = torch.from_numpy(want.view(np.int32)).cuda()
     out_b = torch.empty(n, dtype=torch.uint32, device="cuda")
     out_e = torch.empty(n, dtype=torch.uint32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -548,10 +700,19 @@ def run_batched(args, peaks):
     torch.cuda.synchronize()
     each_ms = e0.elapsed_time(e1) / reps
     st_e = vbyte.get_status(stream)
-    same = bool(torch.equal(out_b.view(torch.int32), out_e.view(torch.int32)))
+    exact_b = bool(torch.equal(out_b.view(torch.int32), dwant))
+    exact_e = bool(torch.equal(out_e.view(torch.int32), dwant))
     med = ms[len(ms) // 2]
     algo = hb.size + 4 * n + 16 * (L + 1)
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    # the oracle on every host core, lists split between threads
+    cores = os.cpu_count() or 1
+    reps_c, tc = 0, time.perf_counter()
+    while True:
+        oracle.decode_batched(hb, hbo, vo, True, prev, threads=cores)
+        reps_c += 1
+        if time.perf_counter() - tc >= args.cpu_seconds / 4:
+            break
+    cpu_s = (time.perf_counter() - tc) / reps_c
     res = {
         "workload": "100,000 rank-Zipf posting lists, universe 5e7, differential, per-list prev",
         "lists": L, "values": n, "nbytes": int(hb.size),
@@ -565,10 +726,13 @@ def run_batched(args, peaks):
         "per_list": {"value": round(n / (each_ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms": round(each_ms, 3),
                      "form": "vbyte_decode_each (one vbyte_decode_delta per list)"},
         "speedup": round(each_ms / med, 2),
-        "bit_exact_between_forms": same,
+        "bit_exact_vs_oracle": {"batched": exact_b, "per_list": exact_e},
         "status": st_b | st_e,
+        "cpu_baseline": {"value": round(n / cpu_s / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"the whole batch, {reps_c} pass(es), lists split over {cores} threads"},
     }
     plan.close()
+    del dwant
     pool = dict(d=d, bo=hbo, vo=vo, prev=prev, lens=np.diff(vo).astype(np.int64))
     return res, pool
 
@@ -577,22 +741,22 @@ def run_serving(args, pool):
     """Open-loop Poisson query streams against the resident 100,000-list pool:
     each query names 2..8 lists drawn proportionally to length; continuous
     batching (gather + one batched launch per batch) against the same loop
-    decoding every list with its own call.  Latency runs from a query's
-    scheduled arrival to the scheduler seeing its batch complete."""
+    decoding every list with its own call.  Per rate, at least
+    args.serve_seconds of arrivals or args.serve_queries queries, whichever is
+    fewer, after an untimed warm-up.  Latency runs from a query's scheduled
+    arrival to the scheduler seeing its batch complete."""
     import torch
     from paper_1503_07387_gb300 import vbyte
-    # a query's output is about 27 MB (lists drawn in proportion to length):
-    # 8 GiB holds four full batches of 64 queries in flight
     free, _ = torch.cuda.mem_get_info()
     arena = int(min(free * 0.25, 8 << 30)) // 4096 * 4096
     cfg = dict(arena_bytes=arena, staging_bytes=512 << 20, max_inflight=4, max_batch_queries=64,
                max_batch_lists=512)
     rows = []
     for rate in args.serve_rates:
-        nq = int(min(max(rate * args.serve_seconds, 200), 40000))
+        nq = int(max(200, min(rate * args.serve_seconds, args.serve_queries)))
         arr, qoff, ql = inputs.query_stream(pool["lens"], nq, float(rate), seed=40)
         vals = int(sum(int(pool["lens"][ql[qoff[i]:qoff[i + 1]]].sum()) for i in range(nq)))
-        row = {"rate_qps": rate, "queries": nq, "values": vals}
+        row = {"rate_qps": rate, "queries": nq, "seconds_of_arrivals": round(float(arr[-1]), 2), "values": vals}
         for form, per_list in (("batched", False), ("per_list", True)):
             srv = vbyte.Server(pool["d"], pool["bo"], pool["vo"], True, pool["prev"], per_list=per_list, **cfg)
             w = min(nq, max(100, int(rate * 0.2)))   # untimed warm-up: 0.2 s at the same rate
@@ -617,25 +781,59 @@ def run_serving(args, pool):
 
 
 def cpu_baseline(streams, budget_s=10.0):
-    """The oracle (scalar Algorithm 1, one core) over the same streams, repeated
-    until about budget_s seconds of CPU work."""
+    """The oracle (scalar Algorithm 1, one core) over bounded prefixes of the
+    same streams: each stream gets an equal share of about budget_s seconds."""
     import oracle
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        for s in streams:
-            if s["delta"]:
-                oracle.decode_delta(s["host"], s["n"])
-            else:
-                oracle.decode(s["host"], s["n"])
-        reps += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    total = reps * sum(s["n"] for s in streams)
-    return {"value": round(total / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full pass(es) over every stream of the workload "
-                      f"({total} values, {dt:.1f} s, single thread)"}
+    per = budget_s / len(streams)
+    done, spent = 0, 0.0
+    parts = []
+    for s in streams:
+        # calibrate on a small prefix, then time a prefix worth `per` seconds
+        m0 = min(s["n"], 1 << 18)
+        t0 = time.perf_counter()
+        _oracle_prefix(oracle, s, m0)
+        rate = m0 / max(time.perf_counter() - t0, 1e-6)
+        m = max(1, min(s["n"], int(rate * per)))
+        t0 = time.perf_counter()
+        _oracle_prefix(oracle, s, m)
+        dt = time.perf_counter() - t0
+        done += m
+        spent += dt
+        parts.append(f"{s['label']}: first {m} of {s['n']} values")
+    return {"value": round(done / spent / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "; ".join(parts) + f" ({spent:.1f} s, single thread)"}
+
+
+def _oracle_prefix(oracle, s, m):
+    nb = _prefix_bytes(s["host"], m)
+    if s["delta"]:
+        oracle.decode_delta(s["host"][:nb], m)
+    else:
+        oracle.decode(s["host"][:nb], m)
+
+
+# --------------------------------------------------------------- profile case --
+
+def run_profile_case(args):
+    """One small stream decoded a few times (the command ncu captures)."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    gen, n, delta = PROFILE_CASES[args.profile_case]
+    v = getattr(inputs, gen)(n, seed=0)
+    b = vbyte.encode(v)
+    if args.passes:
+        vbyte.debug_force_passes(args.passes)
+    d = torch.from_numpy(b).cuda()
+    out = torch.empty(n, dtype=torch.uint32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        (vbyte.decode_delta if delta else vbyte.decode)(d, n, out=out)
+    torch.cuda.synchronize()
+    st = vbyte.get_status()
+    print(json.dumps({"profile_case": args.profile_case, "n": n, "nbytes": int(b.size), "delta": delta,
+                      "launches": args.warmup + args.steps, "status": st,
+                      "kernel_source_hash": kernel_source_hash()}))
+    if st:
+        raise SystemExit(1)
 
 
 # --------------------------------------------------------------- reference arm --
@@ -649,25 +847,23 @@ def _prefix_bytes(data: np.ndarray, m: int) -> int:
 
 
 def run_reference(args):
-    """The CPU oracle (scalar Algorithm 1, one core) on the same workload.  Each
-    step decodes a bounded prefix of every stream, sized so that the whole
-    --steps/--warmup run stays within about args.ref_seconds."""
+    """The CPU oracle (scalar Algorithm 1, one core) on the same workload,
+    encoded by the oracle's own encoder.  Each step decodes a bounded prefix
+    of every stream, sized so that the whole --steps/--warmup run stays
+    within about args.ref_seconds."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    from paper_1503_07387_gb300 import vbyte
     oracle.build()
-    streams = []
-    for label, vals, delta in workload(args.workload):
-        streams.append(dict(label=label, n=int(vals.size), delta=delta, host=vbyte.encode(vals)))
+    streams = [dict(label=lab, n=n, delta=d, host=b) for lab, n, d, b, _ in
+               encode_workload(args.workload, oracle.encode)]
     # calibrate the oracle's speed on the first 2^20 values of each stream
     t0 = time.perf_counter()
     cal = 0
     for s in streams:
         m = min(s["n"], 1 << 20)
-        nb = _prefix_bytes(s["host"], m)
-        (oracle.decode_delta if s["delta"] else oracle.decode)(s["host"][:nb], m)
+        _oracle_prefix(oracle, s, m)
         cal += m
     rate = cal / max(time.perf_counter() - t0, 1e-6)
     per_step = args.ref_seconds / (args.steps + args.warmup)
@@ -690,7 +886,7 @@ def run_reference(args):
     total = args.steps * per
     value = total / dt / 1e9
     sample = (f"each step decodes the first {frac:.4f} of every stream ({per} values), "
-              f"single thread")
+              f"single thread; bytes from the oracle's encoder")
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -719,23 +915,31 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=WORKLOADS, default="differential_2x2^26")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE)
+    ap.add_argument("--passes", type=int, choices=[0, 1, 2], default=0,
+                    help="single-stream kernel: 1 single pass, 2 count then decode, 0 the library's choice")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-blocks", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-encode", action="store_true")
     ap.add_argument("--no-decode64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000, 50000])
-    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-queries", type=int, default=100_000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -107,6 +107,19 @@ std::atomic<uint64_t> g_wait_ns{kWaitLimitNs};
 
 FaultCfg fault_cfg() { return FaultCfg{g_skip_tile.load(), g_wait_ns.load()}; }
 
+std::atomic<int> g_passes{0};
+int forced_passes() { return g_passes.load(); }
+
+// Count then decode unless a test forced the other kernel.
+int choose_passes(size_t nbytes, size_t n, bool delta)
+{
+    (void)nbytes;
+    (void)n;
+    (void)delta;
+    const int f = forced_passes();
+    return f ? f : 2;
+}
+
 // ---- per-stream workspaces
 
 // One workspace per (device, stream), grown on demand with cudaMallocAsync
@@ -439,6 +452,18 @@ const char *vbyte_strerror(int code)
 }
 
 size_t vbyte_workspace_size(size_t nbytes) { return vbk::workspace_bound(nbytes); }
+
+int vbyte_debug_force_passes(int passes)
+{
+    if (passes < 0 || passes > 2) return VBYTE_EINVAL;
+    vbk::g_passes.store(passes);
+    return VBYTE_OK;
+}
+
+int vbyte_debug_passes_for(size_t nbytes, size_t n, int delta)
+{
+    return vbk::choose_passes(nbytes, n, delta != 0);
+}
 
 int vbyte_debug_inject(long long skip_tile, uint64_t wait_limit_ns)
 {

@@ -110,6 +110,9 @@ struct Params {
     // bounded waits and fault injection (tests of the timeout path)
     uint64_t wait_ns;          // bound of every wait
     uint64_t skip_tile;        // this tile's count is never published (~0: none)
+    // single pass only
+    uint64_t *lagg;            // per tile: its own count and sum
+    uint64_t *linc;            // per tile: inclusive count, running x after it
 };
 
 struct Shared {
@@ -376,8 +379,20 @@ struct RegA {
     bool on;   // warp-uniform: nothing is in the value buffer
 };
 
-template <bool kDelta, bool kKeep>
-__device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared &S, const uint8_t *bytes, RegA &ra)
+// A decoded tile in shared memory: per warp, its staged values and its value
+// count and (delta) sum.
+struct TileView {
+    uint32_t (*vals)[kWarpValBuf];
+    uint32_t *dcnt, *dsum;
+};
+
+// kCheck: also check the data-error contract (the single-pass kernel has no
+// count pass to do it).  kCopy (with kKeep): a one-byte warp copies its staged
+// bytes, with 16 before and after, into its value buffer (bytes 16..527 are
+// the warp's), so that the copy-out can run after the byte buffer is reused.
+template <bool kDelta, bool kKeep, bool kCheck = false, bool kCopy = false>
+__device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, const TileView &V, const uint8_t *bytes,
+                                             RegA &ra)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
@@ -387,13 +402,19 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared
     const uint4 w0 = *reinterpret_cast<const uint4 *>(bytes + kHalo + tid * kBPT);
     const uint32_t wp0 = reinterpret_cast<const uint32_t *>(bytes)[(kHalo + tid * kBPT) / 4 - 1];
     const bool mineA = interior && !((w0.x | w0.y | w0.z | w0.w) & 0x80808080u) && !(wp0 & 0x80000000u);
-    uint32_t *vals = S.vals[warp];
+    uint32_t *vals = V.vals[warp];
     uint32_t wc, ws = 0;
     if (kKeep && __all_sync(~0u, mineA)) {
         // one-byte integers only: written from the bytes at the copy-out
         if (kDelta) ws = __reduce_add_sync(~0u, byte_sum4(w0));
         ra.on = true;
         wc = kWarpBytes;
+        if (kCopy) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(bytes + kHalo + warp * kWarpBytes - 16);
+            uint4 *dst = reinterpret_cast<uint4 *>(vals);
+            dst[lane] = src[lane];
+            if (lane < 2) dst[32 + lane] = src[32 + lane];
+        }
     } else if (__all_sync(~0u, mineA)) {
         // one-byte integers only: lane l holds warp ranks 16l .. 16l+15
         uint4 q[4] = {bytes_as_values(w0.x), bytes_as_values(w0.y), bytes_as_values(w0.z),
@@ -423,6 +444,12 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared
         const uint32_t cnt = __popc(m.tc);
         const uint32_t c20 = ~m.t20 & 0xFFFFFu;
         const bool notB = (c20 & (c20 << 1) & 0xFFFF8u) != 0;
+        if (kCheck) {
+            if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
+                atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
+            if (t == p.ntiles - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((m.tl >> (hi - 1 - va)) & 1u))
+                atomicOr(p.status, VBYTE_ERR_TRUNCATED);
+        }
         const uint32_t inc = warp_incl_scan(cnt, lane);
         wc = __shfl_sync(~0u, inc, 31);
         uint32_t *dst = vals + 4 + inc - cnt;
@@ -481,8 +508,8 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, Shared
         }
     }
     if (lane == 0) {
-        S.dcnt[warp] = wc;
-        S.dsum[warp] = ws;
+        V.dcnt[warp] = wc;
+        V.dsum[warp] = ws;
     }
 }
 
@@ -620,24 +647,26 @@ __device__ __forceinline__ void emit_bytes_a(uint32_t *oq, const uint8_t *wb, ui
 }
 
 // After the middle barrier: this warp's values to the output, coalesced;
-// with kRank each value also gets its global rank (gaps minus one).
+// with kRank each value also gets its global rank (gaps minus one).  R0, S0:
+// the values before the tile and the running x before it; wb: the warp's
+// first staged byte (one-byte warps, ra.on).
 template <bool kDelta, bool kRank>
-__device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const RegA &ra, const uint8_t *bytes)
+__device__ __forceinline__ void decode_emit(const Params &p, const TileView &V, unsigned long long R0, uint32_t S0,
+                                            const RegA &ra, const uint8_t *wb)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
     const long long n = static_cast<long long>(p.n);
     // the warps before this one: their value counts and sums
-    const uint32_t wbase = __reduce_add_sync(~0u, lane < warp ? S.dcnt[lane] : 0u);
-    const uint32_t wsb = kDelta ? __reduce_add_sync(~0u, lane < warp ? S.dsum[lane] : 0u) : 0u;
-    const uint32_t wc = S.dcnt[warp];
-    const long long G0 = static_cast<long long>(S.R0 + wbase);   // global rank of warp rank 0
-    const uint32_t add = kDelta ? S.S0 + wsb : 0u;
+    const uint32_t wbase = __reduce_add_sync(~0u, lane < warp ? V.dcnt[lane] : 0u);
+    const uint32_t wsb = kDelta ? __reduce_add_sync(~0u, lane < warp ? V.dsum[lane] : 0u) : 0u;
+    const uint32_t wc = V.dcnt[warp];
+    const long long G0 = static_cast<long long>(R0 + wbase);   // global rank of warp rank 0
+    const uint32_t add = kDelta ? S0 + wsb : 0u;
     const int sh = static_cast<int>((out_word + static_cast<uint32_t>(G0)) & 3u);
-    uint32_t *vals = S.vals[warp];
+    uint32_t *vals = V.vals[warp];
     uint32_t *const oq = p.out + (G0 - sh);   // 16-byte aligned; quad q at oq + 4q
     if (ra.on) {   // warp-uniform
-        const uint8_t *wb = bytes + kHalo + warp * kWarpBytes;
         if (G0 + kWarpBytes <= n) {
             const uint32_t rb = static_cast<uint32_t>(G0);
             switch (sh) {
@@ -649,7 +678,9 @@ __device__ __forceinline__ void decode_emit(const Params &p, Shared &S, const Re
             return;
         }
         // near the end of the output: through the buffer, with the checks
+        // (wb may lie inside the buffer: every lane reads before any writes)
         const uint4 w = *reinterpret_cast<const uint4 *>(wb + lane * kBPT);
+        __syncwarp();
         uint4 q[4] = {bytes_as_values(w.x), bytes_as_values(w.y), bytes_as_values(w.z), bytes_as_values(w.w)};
         if (kDelta) {
             const uint32_t mine = byte_sum4(w);
@@ -1007,14 +1038,14 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
                 if (kDelta && dheads) {
                     decode_stage_seg<kDelta>(p, t, S, S.dbytes[b], dha, dhe);
                 } else {
-                    decode_stage<kDelta, false>(p, t, S, S.dbytes[b], ra);
+                    decode_stage<kDelta, false>(p, t, TileView{S.vals, S.dcnt, S.dsum}, S.dbytes[b], ra);
                     if (lane == 0) {
                         S.dflag[warp] = 0u;
                         S.dhf[warp] = 0xFFFFFFFFu;
                     }
                 }
             } else {
-                decode_stage<kDelta, true>(p, t, S, S.dbytes[b], ra);
+                decode_stage<kDelta, true>(p, t, TileView{S.vals, S.dcnt, S.dsum}, S.dbytes[b], ra);
             }
         }
         __syncthreads();   // count partials, decode partials and the prefix are in place
@@ -1032,7 +1063,8 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
                 decode_emit_seg<kDelta>(p, S);
                 if (dheads) check_heads(p, t, S, S.dbytes[b], dha, dhe, S.R0);
             } else {
-                decode_emit<kDelta, kRank>(p, S, ra, S.dbytes[b]);
+                decode_emit<kDelta, kRank>(p, TileView{S.vals, S.dcnt, S.dsum}, S.R0, S.S0, ra,
+                                           S.dbytes[b] + kHalo + warp * kWarpBytes);
             }
         }
         // did this count complete its chunk?  (read after the emission, so the
@@ -1047,6 +1079,179 @@ __global__ void __launch_bounds__(kThreads, kSeg ? 4 : 5) sdecode_kernel(const P
     }
     __syncthreads();
     if (S.scan_c >= 0) chunk_scan<kSeg>(p, static_cast<uint64_t>(S.scan_c), S);
+    cp_async_wait_all();
+}
+
+
+// ---- single pass: decoupled look-back, two tiles in flight per CTA
+//
+// Ticket k is tile k.  In each iteration a CTA stages (decodes into shared
+// memory) the tile whose bytes it holds and publishes that tile's own value
+// count and sum; then it resolves the prefix of the tile it staged in the
+// previous iteration by looking back over earlier tiles' words -- one
+// iteration after that tile's own words went out, so the tiles before it
+// have usually published by then -- and writes that tile out.  The input is
+// read from HBM once and every value is assembled once.  Every wait is on a
+// tile with a smaller ticket, which a running CTA holds (its own words go out
+// before its CTA waits on anything); each wait is bounded.
+//
+// Words (bit 0 = written; one 64-bit relaxed access each):
+//   lagg[t]      sum << 32 | count << 1 | 1     tile t's own values (count <= 4096)
+//   linc[2t]     count << 1 | 1                 values up to and including tile t
+//   linc[2t+1]   x << 32 | 1                    running x after tile t
+
+struct Shared1 {
+    alignas(16) uint8_t bytes[2][kByteBuf];             // staged tiles: the one decoded now, the next
+    alignas(16) uint32_t vals[2][kWarps][kWarpValBuf];  // staged values: this tile's, the previous one's
+    uint32_t dcnt[2][kWarps], dsum[2][kWarps];          // per-warp totals of both
+    unsigned long long R0[2];                           // values before the previous tile
+    uint32_t S0[2];                                     // running x before it
+    uint32_t tcur, tnext;                               // first tickets
+};
+static_assert(offsetof(Shared1, bytes) % 16 == 0 && offsetof(Shared1, vals) % 16 == 0, "Shared1 alignment");
+
+// Warp 0: the values before tile t and the running x before it, from the
+// words of earlier tiles, 32 at a time (lane i reads tile jb - i); then
+// tile t's inclusive words.  Tiles before the stream act as one inclusive
+// word with no values and x = prev.  After a timeout R0 = n (nothing is
+// written) and tile t publishes nothing.
+__device__ __forceinline__ void lookback(const Params &p, uint32_t t, uint32_t own_c, uint32_t own_s,
+                                         unsigned long long *R0, uint32_t *S0)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t cacc = 0;
+    uint32_t sacc = 0;
+    long long jb = static_cast<long long>(t) - 1;
+    uint64_t t0 = 0;
+    bool ok = true;
+    for (int spin = 0;; ++spin) {
+        const long long j = jb - lane;
+        int kind = 0;   // 0: nothing published yet, 1: own words, 2: inclusive words
+        uint64_t c = 0;
+        uint32_t sv = 0;
+        if (j < 0) {
+            kind = 2;
+            sv = p.prev;
+        } else {
+            const uint64_t ic = ld_relaxed_u64(p.linc + 2 * j);
+            const uint64_t ix = ld_relaxed_u64(p.linc + 2 * j + 1);
+            const uint64_t a = ld_relaxed_u64(p.lagg + j);
+            if (ic & ix & 1u) {
+                kind = 2;
+                c = ic >> 1;
+                sv = word_hi(ix);
+            } else if (a & 1u) {
+                kind = 1;
+                c = desc_count(a);
+                sv = word_hi(a);
+            }
+        }
+        const uint32_t inc = __ballot_sync(~0u, kind == 2);
+        const uint32_t upto = inc ? (inc ^ (inc - 1u)) : ~0u;   // lanes up to the nearest inclusive word
+        if (__ballot_sync(~0u, kind == 0) & upto) {             // a word we need is not out yet
+            int stop = 0;
+            if (lane == 0) {
+                const uint64_t now = global_ns();
+                if (t0 == 0) t0 = now;
+                if (now - t0 > p.wait_ns) {
+                    atomicOr(p.status, VBYTE_ERR_TIMEOUT);
+                    stop = 1;
+                } else if (spin > 4) {
+                    if (*reinterpret_cast<volatile uint32_t *>(p.status) & VBYTE_ERR_TIMEOUT) stop = 1;
+                    __nanosleep(100);
+                }
+            }
+            if (__shfl_sync(~0u, stop, 0)) {
+                ok = false;
+                break;
+            }
+            continue;
+        }
+        const bool mine = (upto >> lane) & 1u;
+        sacc += __reduce_add_sync(~0u, mine ? sv : 0u);
+        cacc += __reduce_add_sync(~0u, (mine && kind == 1) ? static_cast<uint32_t>(c) : 0u);
+        if (inc) {
+            const int k = __ffs(inc) - 1;
+            const uint32_t lo = __shfl_sync(~0u, static_cast<uint32_t>(c), k);
+            const uint32_t hi = __shfl_sync(~0u, static_cast<uint32_t>(c >> 32), k);
+            cacc += (static_cast<uint64_t>(hi) << 32) | lo;
+            break;
+        }
+        jb -= 32;
+        spin = 0;
+        t0 = 0;
+    }
+    if (lane == 0) {
+        if (ok) {
+            *R0 = cacc;
+            *S0 = sacc;
+            if (t != p.skip_tile) {
+                st_relaxed_u64(p.linc + 2 * static_cast<uint64_t>(t) + 1,
+                               (static_cast<uint64_t>(sacc + own_s) << 32) | 1u);
+                st_relaxed_u64(p.linc + 2 * static_cast<uint64_t>(t), ((cacc + own_c) << 1) | 1u);
+            }
+            if (t == p.ntiles - 1 && cacc + own_c != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        } else {
+            *R0 = p.n;
+            *S0 = 0u;
+        }
+    }
+}
+
+template <bool kDelta, bool kRank>
+__global__ void __launch_bounds__(kThreads, 5) onepass_kernel(const Params p)
+{
+    __shared__ Shared1 S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t ntiles = static_cast<uint32_t>(p.ntiles);   // tickets fit 32 bits (checked by the host)
+    if (tid < 2) *reinterpret_cast<uint4 *>(S.bytes[tid] + kHalo + kTile) = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        S.tcur = atomicAdd(p.ctr, 1u);
+        S.tnext = atomicAdd(p.ctr, 1u);
+    }
+    __syncthreads();
+    uint32_t cur = S.tcur, prev = 0xFFFFFFFFu;
+    if (cur < ntiles) issue_stage(p, cur, tid, S.bytes[0]);
+    cp_async_commit();
+    RegA rp;
+    rp.on = false;
+    int b = 0;
+    for (;;) {
+        cp_async_wait_all();
+        __syncthreads();   // cur's bytes are in S.bytes[b]; the previous iteration is over
+        const uint32_t nx = S.tnext;
+        const bool hc = cur < ntiles, hp = prev < ntiles;
+        if (!hc && !hp) break;   // CTA-uniform
+        uint32_t nnx = 0xFFFFFFFFu;
+        if (tid == 0 && nx < ntiles) nnx = atomicAdd(p.ctr, 1u);
+        if (nx < ntiles) issue_stage(p, nx, tid, S.bytes[b ^ 1]);
+        cp_async_commit();
+        const TileView vc{S.vals[b], S.dcnt[b], S.dsum[b]};
+        const TileView vp{S.vals[b ^ 1], S.dcnt[b ^ 1], S.dsum[b ^ 1]};
+        RegA rc;
+        rc.on = false;
+        if (hc) decode_stage<kDelta, true, true, true>(p, cur, vc, S.bytes[b], rc);
+        __syncthreads();   // cur's per-warp totals are in place
+        if (hc && warp == kWarps - 1) {
+            const uint32_t tc = __reduce_add_sync(~0u, lane < kWarps ? vc.dcnt[lane] : 0u);
+            const uint32_t ts = kDelta ? __reduce_add_sync(~0u, lane < kWarps ? vc.dsum[lane] : 0u) : 0u;
+            if (lane == 0 && cur != p.skip_tile) st_relaxed_u64(p.lagg + cur, desc_word(tc, 0u, ts));
+        }
+        if (hp && warp == 0) {
+            const uint32_t pc = __reduce_add_sync(~0u, lane < kWarps ? vp.dcnt[lane] : 0u);
+            const uint32_t ps = kDelta ? __reduce_add_sync(~0u, lane < kWarps ? vp.dsum[lane] : 0u) : 0u;
+            lookback(p, prev, pc, ps, &S.R0[b ^ 1], &S.S0[b ^ 1]);
+        }
+        __syncthreads();   // prev's prefix is in place
+        if (hp)
+            decode_emit<kDelta, kRank>(p, vp, S.R0[b ^ 1], S.S0[b ^ 1], rp,
+                                       reinterpret_cast<const uint8_t *>(vp.vals[warp]) + 16);
+        if (tid == 0) S.tnext = nnx;
+        prev = cur;
+        rp = rc;
+        cur = nx;
+        b ^= 1;
+    }
     cp_async_wait_all();
 }
 
@@ -1077,6 +1282,24 @@ Layout layout(uint64_t ntiles)
     return L;
 }
 
+// Workspace of a single-pass launch: status head, ticket counter, per tile its
+// own word and two inclusive words; all but the head cleared before each
+// launch.
+struct Layout1 {
+    size_t ctr, lagg, linc, total, clear;
+};
+
+Layout1 layout1(uint64_t ntiles)
+{
+    Layout1 L;
+    L.ctr = 256;
+    L.lagg = L.ctr + 16;
+    L.linc = (L.lagg + 8 * ntiles + 15) / 16 * 16;
+    L.total = L.linc + 16 * ntiles;
+    L.clear = L.total - L.ctr;
+    return L;
+}
+
 // Tiles [t_in_lo, t_in_hi) lie wholly inside [in, in + nbytes).
 void inside_range(Params &p, uintptr_t in, size_t nbytes)
 {
@@ -1101,6 +1324,7 @@ struct Dev {
     int sms = 0;
     int occ[2] = {0, 0};       // single stream: plain, delta
     int occ_seg[2] = {0, 0};   // batched lists: plain, delta
+    int occ1[2] = {0, 0};      // single pass: plain, delta
 };
 std::mutex g_mu;
 std::map<int, Dev> g_dev;
@@ -1117,8 +1341,11 @@ int dev_info(Dev *out)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], sdecode_kernel<true, false>, kThreads, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_seg[0], sdecode_kernel<false, true>, kThreads, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_seg[1], sdecode_kernel<true, true>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ1[0], onepass_kernel<false, false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ1[1], onepass_kernel<true, false>, kThreads, 0);
         for (int &o : d.occ) o = std::max(o, 1);
         for (int &o : d.occ_seg) o = std::max(o, 1);
+        for (int &o : d.occ1) o = std::max(o, 1);
     }
     *out = d;
     return VBYTE_OK;
@@ -1131,6 +1358,12 @@ size_t stream_workspace_bytes(const uint8_t *in, size_t nbytes)
     return sd::layout(sd::tiles_for(reinterpret_cast<uintptr_t>(in), nbytes)).total;
 }
 
+size_t stream_workspace_bytes_any(const uint8_t *in, size_t nbytes)
+{
+    const uint64_t ntiles = sd::tiles_for(reinterpret_cast<uintptr_t>(in), nbytes);
+    return std::max(sd::layout(ntiles).total, sd::layout1(ntiles).total);
+}
+
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
                   cudaStream_t s, bool rank)
 {
@@ -1138,17 +1371,57 @@ int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     if ((nbytes && !in) || (n && !out)) return VBYTE_EINVAL;
     if (reinterpret_cast<uintptr_t>(out) & 3u) return VBYTE_EINVAL;
     uint8_t *ws = nullptr;
-    const int rc = stream_workspace(s, stream_workspace_bytes(in, nbytes), &ws);
+    const int rc = stream_workspace(s, stream_workspace_bytes_any(in, nbytes), &ws);
     if (rc != VBYTE_OK) return rc;
     uint32_t *status = reinterpret_cast<uint32_t *>(ws);
     if (nbytes == 0) return set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s);   // n > 0 from no bytes
-    return enqueue_stream(in, nbytes, out, n, delta, prev, ws, status, s, rank);
+    return enqueue_stream(in, nbytes, out, n, delta, prev, ws, status, s, rank, choose_passes(nbytes, n, delta));
+}
+
+// The single-pass kernel (decoupled look-back).
+int enqueue_onepass(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
+                    uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(in);
+    const uint64_t ntiles = sd::tiles_for(a, nbytes);
+    const sd::Layout1 L = sd::layout1(ntiles);
+    if (reinterpret_cast<uintptr_t>(ws) & 15u) return VBYTE_EINVAL;
+    sd::Dev di;
+    const int rc = sd::dev_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    if (cudaMemsetAsync(ws + L.ctr, 0, L.clear, s) != cudaSuccess) return VBYTE_ECUDA;
+    sd::Params p = {};
+    p.in = in;
+    p.nbytes = nbytes;
+    p.out = out;
+    p.n = n;
+    p.ntiles = ntiles;
+    p.base = a & ~static_cast<uintptr_t>(15);
+    sd::inside_range(p, a, nbytes);
+    p.ctr = reinterpret_cast<unsigned int *>(ws + L.ctr);
+    p.lagg = reinterpret_cast<uint64_t *>(ws + L.lagg);
+    p.linc = reinterpret_cast<uint64_t *>(ws + L.linc);
+    p.status = status;
+    p.prev = prev;
+    const FaultCfg fc = fault_cfg();
+    p.wait_ns = fc.wait_ns;
+    p.skip_tile = fc.skip_tile;
+    const uint64_t grid = std::min<uint64_t>(ntiles, static_cast<uint64_t>(di.sms) * di.occ1[delta]);
+    if (ntiles + 3 * grid >= (1ull << 32)) return VBYTE_EINVAL;
+    if (rank)
+        sd::onepass_kernel<true, true><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    else if (delta)
+        sd::onepass_kernel<true, false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    else
+        sd::onepass_kernel<false, false><<<static_cast<unsigned>(grid), sd::kThreads, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
 int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                   uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank)
+                   uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank, int passes)
 {
     if (rank && !delta) return VBYTE_EINVAL;
+    if (passes == 1) return enqueue_onepass(in, nbytes, out, n, delta, prev, ws, status, s, rank);
     const uintptr_t a = reinterpret_cast<uintptr_t>(in);
     const uint64_t ntiles = sd::tiles_for(a, nbytes);
     const sd::Layout L = sd::layout(ntiles);

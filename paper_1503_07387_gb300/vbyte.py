@@ -81,6 +81,8 @@ def _signatures(lib):
         "vbyte_set_workspace": ([P, P, S], I),
         "vbyte_release_stream": ([P], I),
         "vbyte_debug_inject": ([ctypes.c_longlong, ctypes.c_uint64], I),
+        "vbyte_debug_force_passes": ([I], I),
+        "vbyte_debug_passes_for": ([S, S, I], I),
         "vbyte_max_encoded_size64": ([S], S),
         "vbyte_encode64": ([P, S, P], S),
         "vbyte_encode_delta64": ([P, S, ctypes.c_uint64, P], S),
@@ -547,6 +549,17 @@ def debug_inject(skip_tile: int = -1, wait_limit_ns: int = 0):
     count unpublished and bound their waits by wait_limit_ns (tests of the
     timeout path; skip_tile < 0 and 0 restore the defaults)."""
     _check(load().vbyte_debug_inject(int(skip_tile), int(wait_limit_ns)), "vbyte_debug_inject")
+
+
+def debug_force_passes(passes: int = 0):
+    """vbyte_debug_force_passes: 1 = single-pass kernel, 2 = count then
+    decode, 0 = the library's choice."""
+    _check(load().vbyte_debug_force_passes(int(passes)), "vbyte_debug_force_passes")
+
+
+def chosen_passes(nbytes: int, n: int, delta: bool) -> int:
+    """The single-stream kernel (1 or 2 passes) a call on this input would use."""
+    return int(load().vbyte_debug_passes_for(nbytes, n, int(delta)))
 
 
 def get_status(stream=None) -> int:

@@ -22,25 +22,27 @@ def test_code_only_ignores_comments_and_spacing():
     assert bench._code_only(a) != bench._code_only(a.replace("x + 1", "x + 2"))
 
 
-def test_committed_profile_names_a_hash_and_a_traffic_figure():
-    """The committed summary carries both lines the bench reads; its traffic
-    is reported only for the sources it names."""
-    import re
-    text = open(bench.PROFILE_FILE).read()
-    m = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", text)
-    assert m and re.search(r"dram bytes per launch \(full workload\):\s*[0-9.eE+]+", text)
-    assert bench.profiled_traffic(m.group(1)) > 0
-    assert bench.profiled_traffic("0" * 16) is None
+def test_profiled_traffic_lookup(tmp_path):
+    """A summary's traffic figure is reported only for the kernel source hash
+    it names, per stream label."""
+    p = tmp_path / "p.md"
+    p.write_text("kernel source hash: `0123456789abcdef`\n"
+                 "dram bytes per launch (full workload) [full_range_delta]: 1.5e6\n"
+                 "dram bytes per launch (full workload) [one_two_byte_mix_plain]: 2.5e6\n")
+    assert bench.profiled_traffic("0123456789abcdef", "full_range_delta", str(tmp_path)) == 1.5e6
+    assert bench.profiled_traffic("0123456789abcdef", "one_two_byte_mix_plain", str(tmp_path)) == 2.5e6
+    assert bench.profiled_traffic("0123456789abcdef", "geometric_gaps", str(tmp_path)) is None
+    assert bench.profiled_traffic("f" * 16, "full_range_delta", str(tmp_path)) is None
+    assert bench.profiled_traffic("0123456789abcdef", "x", str(tmp_path / "absent")) is None
     assert len(bench.kernel_source_hash()) == 16
 
 
-def test_profiled_traffic_missing_file(monkeypatch, tmp_path):
-    monkeypatch.setattr(bench, "PROFILE_FILE", str(tmp_path / "absent.md"))
-    assert bench.profiled_traffic(bench.kernel_source_hash()) is None
-    p = tmp_path / "p.md"
-    p.write_text("kernel source hash: `0123456789abcdef`\ndram bytes per launch (full workload): 1.5e6\n")
-    monkeypatch.setattr(bench, "PROFILE_FILE", str(p))
-    assert bench.profiled_traffic("0123456789abcdef") == 1.5e6
+def test_workloads_share_bytes_between_readings():
+    """The headline's plain and differential streams read the same bytes."""
+    wl = bench.WORKLOADS[bench.HEADLINE]
+    assert len(wl) == 4 and {d for _, _, d in wl} == {False, True}
+    assert len({src for _, src, _ in wl}) == 2
+    assert set(bench.BLOCKS) <= set(bench.WORKLOADS)
 
 
 class _FakeProc:

@@ -11,6 +11,15 @@ from paper_1503_07387_gb300 import inputs, vbyte
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(autouse=True, params=[1, 2], ids=["onepass", "twopass"])
+def kernel(request):
+    """Every test runs on both single-stream kernels: the single pass with a
+    decoupled look-back and count-then-decode."""
+    vbyte.debug_force_passes(request.param)
+    yield request.param
+    vbyte.debug_force_passes(0)
+
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("CUDA not available", allow_module_level=True)
 

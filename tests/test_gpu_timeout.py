@@ -1,7 +1,8 @@
 """The bounded waits between CTAs, made to run out on purpose.
 
 A decode launch passes tile counts and running sums between CTAs through
-published words.  With vbyte_debug_inject one tile's count is never
+published words (either kernel: count-then-decode or the single pass with a
+decoupled look-back).  With vbyte_debug_inject one tile's words are never
 published and every wait is bounded by 50 ms: the launch must then return
 (no hang, no trap), record VBYTE_ERR_TIMEOUT in the status word, and write
 nothing outside [0, n).  Afterwards, with the defaults restored, the same
@@ -24,6 +25,7 @@ PAD = 64
 def injected():
     yield vbyte.debug_inject
     vbyte.debug_inject(-1, 0)
+    vbyte.debug_force_passes(0)
 
 
 def _padded(n):
@@ -38,10 +40,12 @@ def _canaries_intact(buf):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("passes", [1, 2])
 @pytest.mark.parametrize("n,skip", [(30_000_000, 2048 + 100),   # four chunks; a tile of the second goes missing
                                     (100_000, 3)])              # one chunk
-def test_single_stream_wait_runs_out(injected, n, skip):
+def test_single_stream_wait_runs_out(injected, n, skip, passes):
     import torch
+    vbyte.debug_force_passes(passes)
     g = inputs.geometric_gaps(n, seed=3)
     b = oracle.encode(g)
     d = torch.from_numpy(b).cuda()
