@@ -782,7 +782,8 @@ def run_serving(args, pool):
 
 def cpu_baseline(streams, budget_s=10.0):
     """The oracle (scalar Algorithm 1, one core) over bounded prefixes of the
-    same streams: each stream gets an equal share of about budget_s seconds."""
+    same streams: each stream gets an equal share of about budget_s seconds
+    (the prefix's byte length is found before the clock starts)."""
     import oracle
     per = budget_s / len(streams)
     done, spent = 0, 0.0
@@ -790,12 +791,14 @@ def cpu_baseline(streams, budget_s=10.0):
     for s in streams:
         # calibrate on a small prefix, then time a prefix worth `per` seconds
         m0 = min(s["n"], 1 << 18)
+        nb0 = _prefix_bytes(s["host"], m0)
         t0 = time.perf_counter()
-        _oracle_prefix(oracle, s, m0)
+        _oracle_prefix(oracle, s, m0, nb0)
         rate = m0 / max(time.perf_counter() - t0, 1e-6)
         m = max(1, min(s["n"], int(rate * per)))
+        nb = _prefix_bytes(s["host"], m)
         t0 = time.perf_counter()
-        _oracle_prefix(oracle, s, m)
+        _oracle_prefix(oracle, s, m, nb)
         dt = time.perf_counter() - t0
         done += m
         spent += dt
@@ -804,8 +807,7 @@ def cpu_baseline(streams, budget_s=10.0):
             "sample": "; ".join(parts) + f" ({spent:.1f} s, single thread)"}
 
 
-def _oracle_prefix(oracle, s, m):
-    nb = _prefix_bytes(s["host"], m)
+def _oracle_prefix(oracle, s, m, nb):
     if s["delta"]:
         oracle.decode_delta(s["host"][:nb], m)
     else:
@@ -839,10 +841,11 @@ def run_profile_case(args):
 # --------------------------------------------------------------- reference arm --
 
 def _prefix_bytes(data: np.ndarray, m: int) -> int:
-    """Byte length of the first m integers of a well-formed stream."""
+    """Byte length of the first m integers of a well-formed stream (at most
+    five bytes each, so only the first 5m bytes are scanned)."""
     if m <= 0:
         return 0
-    ends = np.flatnonzero(data < 128)
+    ends = np.flatnonzero(data[:5 * m] < 128)
     return int(ends[m - 1]) + 1
 
 
@@ -859,13 +862,12 @@ def run_reference(args):
     streams = [dict(label=lab, n=n, delta=d, host=b) for lab, n, d, b, _ in
                encode_workload(args.workload, oracle.encode)]
     # calibrate the oracle's speed on the first 2^20 values of each stream
+    cal = [(s, min(s["n"], 1 << 20)) for s in streams]
+    cal = [(s, m, _prefix_bytes(s["host"], m)) for s, m in cal]
     t0 = time.perf_counter()
-    cal = 0
-    for s in streams:
-        m = min(s["n"], 1 << 20)
-        _oracle_prefix(oracle, s, m)
-        cal += m
-    rate = cal / max(time.perf_counter() - t0, 1e-6)
+    for s, m, nb in cal:
+        _oracle_prefix(oracle, s, m, nb)
+    rate = sum(m for _, m, _ in cal) / max(time.perf_counter() - t0, 1e-6)
     per_step = args.ref_seconds / (args.steps + args.warmup)
     frac = min(1.0, per_step * rate / sum(s["n"] for s in streams))
     for s in streams:

@@ -36,14 +36,15 @@ int vbyte_debug_inject(long long skip_tile, uint64_t wait_limit_ns);
 /* Which single-stream kernel vbyte_decode, vbyte_decode_delta and
  * vbyte_decode_delta_m1 use from now on (process-wide): 1 = single pass (each
  * tile resolves its output position and running sum by looking back over
- * earlier tiles' published counts and sums), 2 = count then decode (a count
- * pass runs a fixed number of tiles ahead of the decode pass), 0 = the
- * library's choice (the default).  Both give identical results; this exists
- * so that tests can check each and benchmarks can compare them.  Returns
- * VBYTE_OK, or VBYTE_EINVAL for another value. */
+ * earlier tiles' published counts and sums), 2 = count then decode in one
+ * launch (a count pass runs a fixed number of tiles ahead of the decode
+ * pass), 3 = split (separate count, scan and decode launches; no CTA waits
+ * on another), 0 = the library's choice (the default).  All give identical
+ * results; this exists so that tests can check each and benchmarks can
+ * compare them.  Returns VBYTE_OK, or VBYTE_EINVAL for another value. */
 int vbyte_debug_force_passes(int passes);
 
-/* The kernel (1 or 2 passes, as above) that a single-stream call on an
+/* The kernel (1, 2 or 3, as above) that a single-stream call on an
  * nbytes-byte input holding n values would use now. */
 int vbyte_debug_passes_for(size_t nbytes, size_t n, int delta);
 

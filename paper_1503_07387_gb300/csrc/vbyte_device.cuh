@@ -204,6 +204,31 @@ __device__ __forceinline__ void assemble_all(const uint32_t *sw, int tid, uint32
     }
 }
 
+// The same from registers: wp is the word before the slice, w the slice.  The
+// word pair holding a terminator's four preceding bytes and itself is picked
+// by selects (no shared-memory loads, so no bank conflicts between lanes
+// whose slices lie 16 bytes apart).
+template <typename F>
+__device__ __forceinline__ void assemble_regs(uint32_t wp, uint4 w, uint32_t tl, uint32_t t20, uint32_t tc, F emit)
+{
+    uint32_t m = tl & tc;
+    int prevo = 27 - __clz(t20 & 0xFu);   // last terminator before my bytes (-5: none)
+    uint32_t all = tl;                     // every terminator, for the code lengths
+    while (m) {
+        const int o = __ffs(m) - 1;
+        m &= m - 1u;
+        const uint32_t below = all & ((1u << o) - 1u);   // terminators of the slice before o
+        const int po = below ? 31 - __clz(below) : prevo;
+        const int L = min(o - po, 5);
+        const int k = o >> 2;
+        const uint32_t A = (k & 2) ? ((k & 1) ? w.z : w.y) : ((k & 1) ? w.x : wp);
+        const uint32_t B = (k & 2) ? ((k & 1) ? w.w : w.z) : ((k & 1) ? w.y : w.x);
+        const uint32_t lo4 = __funnelshift_r(A, B, 8 * (o & 3));
+        const uint32_t x = prmt(B, 0u, 0x4440u | static_cast<uint32_t>(o & 3));
+        emit(assemble(lo4, x, L));
+    }
+}
+
 // Bit j set iff byte va + j lies inside [lo, hi).
 __device__ __forceinline__ uint32_t slice_valid(uintptr_t va, uintptr_t lo, uintptr_t hi)
 {

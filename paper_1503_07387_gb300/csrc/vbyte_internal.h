@@ -42,7 +42,7 @@ struct FaultCfg {
     uint64_t wait_ns;
 };
 FaultCfg fault_cfg();
-// 0: the library's choice of kernel; 1 or 2: that many passes (tests).
+// 0: the library's choice of kernel; 1, 2 or 3: that kernel (tests).
 int forced_passes();
 // The per-stream workspace of s (current device) with at least need bytes;
 // its first 4 bytes are the stream's status word.
@@ -57,14 +57,22 @@ size_t workspace_bound(size_t nbytes);
 // (stream_workspace_bytes) and data errors OR-ed into *status.  rank (delta
 // only): the gaps-minus-one variant, every value plus its rank.
 // passes: 2 = count-then-decode (the workspace layout of
-// stream_workspace_bytes), 1 = single pass with a decoupled look-back (needs
+// stream_workspace_bytes), 1 = single pass with a decoupled look-back, 3 = the
+// split count / scan / decode launches (1 and 3 need
 // stream_workspace_bytes_any).
 int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
                    uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank = false, int passes = 2);
-// Workspace bytes for a single-stream call with either kernel.
+// Workspace bytes for a single-stream call with any of the kernels.
 size_t stream_workspace_bytes_any(const uint8_t *in, size_t nbytes);
+// The split decoder (vbyte_split.cu): count, scan and decode launches with no
+// wait between CTAs; its workspace for an input at `in`, and for any
+// alignment.
+size_t split_workspace_bytes(const uint8_t *in, size_t nbytes);
+size_t split_workspace_bound(size_t nbytes);
+int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
+                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank);
 // The kernel vbyte_decode* use for an input of nbytes holding n values:
-// 1 (single pass) or 2 (count-then-decode).
+// 1 (single pass), 2 (count-then-decode) or 3 (split).
 int choose_passes(size_t nbytes, size_t n, bool delta);
 // The single-stream call with the per-stream workspace.
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,

@@ -50,6 +50,7 @@
 
 #include "vbyte.h"
 #include "vbyte_device.cuh"
+#include "vbyte_emit.cuh"
 #include "vbyte_internal.h"
 
 namespace vbk {
@@ -510,139 +511,6 @@ __device__ __forceinline__ void decode_stage(const Params &p, uint64_t t, const 
     if (lane == 0) {
         V.dcnt[warp] = wc;
         V.dsum[warp] = ws;
-    }
-}
-
-// Output quad q of a warp holds its ranks 4q - SH .. 4q - SH + 3, staged at
-// vals[4q + 4 - SH ..]: the tail of U = vals[4q..] and the head of
-// V = vals[4q+4..].
-template <int SH>
-__device__ __forceinline__ uint4 staged_quad(const uint32_t *vals, int q)
-{
-    const uint4 V = *reinterpret_cast<const uint4 *>(vals + 4 * q + 4);
-    if (SH == 0) return V;
-    const uint4 U = *reinterpret_cast<const uint4 *>(vals + 4 * q);
-    if (SH == 1) return make_uint4(U.w, V.x, V.y, V.z);
-    if (SH == 2) return make_uint4(U.z, U.w, V.x, V.y);
-    return make_uint4(U.y, U.z, U.w, V.x);
-}
-
-// A warp's staged values to the output, SH = (output word of rank 0) mod 4.
-// Output quad q holds ranks 4q - SH .. 4q - SH + 3, staged at
-// vals[4q + 4 - SH ..]; quads [qa, qb) are whole (inside the warp's ranks and
-// below `room`, the ranks the output still holds); the ranks outside them
-// are written one per lane.  `add` goes to every rank; with kRank the rank
-// itself too, counted from rb (the gaps-minus-one variant).
-template <int SH, bool kRank>
-__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, uint32_t rb,
-                                            long long room, int lane)
-{
-    constexpr int qa = SH ? 1 : 0;
-    const int lim = room < wc ? (room > 0 ? static_cast<int>(room) : 0) : wc;   // ranks [0, lim) are written
-    const int qb = (lim + SH) >> 2;
-#pragma unroll 2
-    for (int q = qa + lane; q < qb; q += kLanes) {
-        uint4 e = staged_quad<SH>(vals, q);
-        const uint32_t a0 = add + (kRank ? rb + static_cast<uint32_t>(4 * q - SH) : 0u);
-        e.x += a0;
-        e.y += a0 + (kRank ? 1u : 0u);
-        e.z += a0 + (kRank ? 2u : 0u);
-        e.w += a0 + (kRank ? 3u : 0u);
-        st_quad(oq + 4 * q, e);
-    }
-    const bool whole = qb > qa;
-    const int hb = whole ? min(4 * qa - SH, lim) : lim;   // ranks [0, hb)
-    const int tb = whole ? 4 * qb - SH : lim;             // ranks [tb, lim)
-    for (int r = lane; r < hb; r += kLanes)
-        oq[SH + r] = vals[4 + r] + add + (kRank ? rb + static_cast<uint32_t>(r) : 0u);
-    for (int r = tb + lane; r < lim; r += kLanes)
-        oq[SH + r] = vals[4 + r] + add + (kRank ? rb + static_cast<uint32_t>(r) : 0u);
-}
-
-template <bool kRank>
-__device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, int wc, uint32_t add, uint32_t rb,
-                                            long long room, int lane, int sh)
-{
-    switch (sh) {   // warp-uniform
-    case 0: emit_staged<0, kRank>(oq, vals, wc, add, rb, room, lane); break;
-    case 1: emit_staged<1, kRank>(oq, vals, wc, add, rb, room, lane); break;
-    case 2: emit_staged<2, kRank>(oq, vals, wc, add, rb, room, lane); break;
-    default: emit_staged<3, kRank>(oq, vals, wc, add, rb, room, lane); break;
-    }
-}
-
-// The copy-out of a one-byte warp from its staged bytes (wb: its first byte;
-// the 4 bytes before and after it are staged too).  Output quad Q = 32m + l,
-// taken by lane l, holds ranks 4Q - SH .. 4Q - SH + 3, whose bytes start at
-// wb + 4Q - SH.  In delta mode the sums before each quad come from two
-// packed warp scans (a quad's sum is at most 4 * 127, so 16 bits hold a
-// warp's prefix).  Quad 0 skips the SH ranks before the warp; lane 31 writes
-// the last SH ranks after quad 127.  With kRank each value also gets its
-// rank, counted from rb.
-template <int SH, bool kDelta, bool kRank>
-__device__ __forceinline__ void emit_bytes_a(uint32_t *oq, const uint8_t *wb, uint32_t add, uint32_t rb, int lane)
-{
-    const uint32_t *ww = reinterpret_cast<const uint32_t *>(wb);
-    uint32_t x[4], qs[4], P[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int k = 32 * m + lane;
-        x[m] = SH == 0 ? ww[k] : __funnelshift_r(ww[k - 1], ww[k], 8 * (4 - SH));
-    }
-    if (SH > 0 && lane == 0) x[0] &= 0xFFFFFFFFu << (8 * SH);   // ranks before the warp
-    if (kDelta) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) qs[m] = __dp4a(x[m], 0x01010101u, 0u);
-        const uint32_t o01 = qs[0] | (qs[1] << 16), o23 = qs[2] | (qs[3] << 16);
-        const uint32_t s01 = warp_incl_scan(o01, lane), s23 = warp_incl_scan(o23, lane);
-        const uint32_t t01 = __shfl_sync(~0u, s01, 31), t23 = __shfl_sync(~0u, s23, 31);
-        const uint32_t e01 = s01 - o01, e23 = s23 - o23;
-        P[0] = e01 & 0xFFFFu;
-        P[1] = (t01 & 0xFFFFu) + (e01 >> 16);
-        P[2] = (t01 & 0xFFFFu) + (t01 >> 16) + (e23 & 0xFFFFu);
-        P[3] = (t01 & 0xFFFFu) + (t01 >> 16) + (t23 & 0xFFFFu) + (e23 >> 16);
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        uint32_t e[4];
-        uint32_t run = kDelta ? add + P[m] : add;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t b = (x[m] >> (8 * j)) & 0xFFu;
-            if (kDelta) {
-                run += b;
-                e[j] = run;
-            } else {
-                e[j] = b + add;
-            }
-        }
-        if (kRank) {
-            const uint32_t r0 = rb + static_cast<uint32_t>(4 * (32 * m + lane) - SH);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) e[j] += r0 + j;
-        }
-        uint32_t *const o = oq + 4 * (32 * m + lane);
-        if (SH == 0 || m > 0 || lane > 0) {
-            st_quad(o, make_uint4(e[0], e[1], e[2], e[3]));
-        } else {
-#pragma unroll
-            for (int j = SH; j < 4; ++j) o[j] = e[j];
-        }
-    }
-    if (SH > 0 && lane == kLanes - 1) {   // quad 128: ranks 512 - SH .. 511
-        const uint32_t xt = __funnelshift_r(ww[127], ww[128], 8 * (4 - SH));
-        uint32_t run = kDelta ? add + P[3] + qs[3] : add;
-#pragma unroll
-        for (int j = 0; j < SH; ++j) {
-            const uint32_t b = (xt >> (8 * j)) & 0xFFu;
-            const uint32_t rk = kRank ? rb + static_cast<uint32_t>(4 * 128 + j - SH) : 0u;
-            if (kDelta) {
-                run += b;
-                oq[4 * 128 + j] = run + rk;
-            } else {
-                oq[4 * 128 + j] = b + add + rk;
-            }
-        }
     }
 }
 
@@ -1361,7 +1229,7 @@ size_t stream_workspace_bytes(const uint8_t *in, size_t nbytes)
 size_t stream_workspace_bytes_any(const uint8_t *in, size_t nbytes)
 {
     const uint64_t ntiles = sd::tiles_for(reinterpret_cast<uintptr_t>(in), nbytes);
-    return std::max(sd::layout(ntiles).total, sd::layout1(ntiles).total);
+    return std::max({sd::layout(ntiles).total, sd::layout1(ntiles).total, split_workspace_bytes(in, nbytes)});
 }
 
 int launch_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
@@ -1422,6 +1290,7 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
 {
     if (rank && !delta) return VBYTE_EINVAL;
     if (passes == 1) return enqueue_onepass(in, nbytes, out, n, delta, prev, ws, status, s, rank);
+    if (passes == 3) return enqueue_split(in, nbytes, out, n, delta, prev, ws, status, s, rank);
     const uintptr_t a = reinterpret_cast<uintptr_t>(in);
     const uint64_t ntiles = sd::tiles_for(a, nbytes);
     const sd::Layout L = sd::layout(ntiles);
@@ -1465,7 +1334,7 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
 size_t workspace_bound(size_t nbytes)
 {
     const uint64_t ntiles = sd::tiles_for(15, nbytes);   // the worst alignment
-    return sd::layout(ntiles).total_b;
+    return std::max({sd::layout(ntiles).total_b, sd::layout1(ntiles).total, split_workspace_bound(nbytes)});
 }
 
 int load_kernels()

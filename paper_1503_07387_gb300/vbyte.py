@@ -553,7 +553,8 @@ def debug_inject(skip_tile: int = -1, wait_limit_ns: int = 0):
 
 def debug_force_passes(passes: int = 0):
     """vbyte_debug_force_passes: 1 = single-pass kernel, 2 = count then
-    decode, 0 = the library's choice."""
+    decode in one launch, 3 = split count / scan / decode, 0 = the library's
+    choice."""
     _check(load().vbyte_debug_force_passes(int(passes)), "vbyte_debug_force_passes")
 
 

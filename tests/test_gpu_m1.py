@@ -12,10 +12,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(autouse=True, params=[1, 2], ids=["onepass", "twopass"])
+@pytest.fixture(autouse=True, params=[1, 2, 3], ids=["onepass", "twopass", "split"])
 def kernel(request):
-    """Every test runs on both single-stream kernels: the single pass with a
-    decoupled look-back and count-then-decode."""
+    """Every test runs on each single-stream kernel: the single pass with a
+    decoupled look-back, count-then-decode in one launch, and the split
+    count / scan / decode launches."""
     vbyte.debug_force_passes(request.param)
     yield request.param
     vbyte.debug_force_passes(0)

@@ -40,7 +40,7 @@ def _canaries_intact(buf):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("passes", [1, 2])   # the split kernels have no waits
 @pytest.mark.parametrize("n,skip", [(30_000_000, 2048 + 100),   # four chunks; a tile of the second goes missing
                                     (100_000, 3)])              # one chunk
 def test_single_stream_wait_runs_out(injected, n, skip, passes):
