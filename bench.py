@@ -381,7 +381,8 @@ def roofline_of(streams, launch_ms, peak, peak_source, src_hash, kernel):
 
 def kernel_name(vbyte, streams):
     passes = {vbyte.chosen_passes(int(s["host"].size), s["n"], s["delta"]) for s in streams}
-    names = {1: "onepass_kernel (single pass, decoupled look-back)", 2: "sdecode_kernel (count then decode)"}
+    names = {1: "onepass_kernel (single pass, decoupled look-back)", 2: "sdecode_kernel (count then decode)",
+             3: "sp::count_kernel + sp::decode_kernel (split)"}
     return " + ".join(names[p] for p in sorted(passes))
 
 
@@ -921,8 +922,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE)
-    ap.add_argument("--passes", type=int, choices=[0, 1, 2], default=0,
-                    help="single-stream kernel: 1 single pass, 2 count then decode, 0 the library's choice")
+    ap.add_argument("--passes", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="single-stream kernel: 1 single pass, 2 count then decode, 3 split, 0 the library default")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)

@@ -110,14 +110,20 @@ FaultCfg fault_cfg() { return FaultCfg{g_skip_tile.load(), g_wait_ns.load()}; }
 std::atomic<int> g_passes{0};
 int forced_passes() { return g_passes.load(); }
 
-// Count then decode unless a test forced the other kernel.
+// The kernel for a single stream, by the mean code length nbytes / n (a
+// length class) and the size, from measurements on GB300 (2^26..2^28
+// values): small inputs take the single pass (fewest launches), one-byte
+// codes count-then-decode in one launch, long differential codes the
+// single pass, the rest the split launches.
 int choose_passes(size_t nbytes, size_t n, bool delta)
 {
-    (void)nbytes;
-    (void)n;
-    (void)delta;
     const int f = forced_passes();
-    return f ? f : 2;
+    if (f) return f;
+    if (nbytes < (size_t(16) << 20) || n == 0) return 1;
+    const double mean = static_cast<double>(nbytes) / static_cast<double>(n);
+    if (mean < 1.1) return 2;
+    if (delta && mean > 2.5) return 1;
+    return 3;
 }
 
 // ---- per-stream workspaces

@@ -229,6 +229,73 @@ __device__ __forceinline__ void assemble_regs(uint32_t wp, uint4 w, uint32_t tl,
     }
 }
 
+// Sum of the values whose terminators lie in a thread's slice, without
+// assembling them, for codes of any length (every byte inside the stream):
+// each byte's 7-bit payload p times 128^k, k = its place within its integer
+// (the number of continuation bytes right before it, at most four), summed
+// over the bytes of those values -- from the first byte after the last
+// terminator before the slice through the slice's last terminator.  With
+// a_i = the sum of p over those bytes with k >= i, the sum is
+// a_0 + 127 (a_1 + 128 (a_2 + 128 (a_3 + 128 a_4))) modulo 2^32, since
+// 128^k = 1 + 127 (1 + 128 + ... + 128^(k-1)).  The bytes before the four
+// before the slice count as terminators, which holds in a well-formed
+// stream whenever it matters (a run of five continuation bytes is malformed).
+__device__ __forceinline__ uint32_t sum_any_fast(uint4 w, uint32_t wp, uint32_t tl, uint32_t t20)
+{
+    if (!tl) return 0u;
+    const uint32_t lt = 31u - __clz(tl);                    // last terminator of the slice
+    const uint32_t low = t20 & 0xFu;
+    const uint32_t st = low ? 32u - __clz(low) : 0u;        // first byte of the first value (t20 bits)
+    const uint32_t mem = ((2u << (lt + 4u)) - 1u) & (~0u << st);
+    const uint32_t W[5] = {wp, w.x, w.y, w.z, w.w};
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const uint32_t pv = i ? W[i - 1] : 0u;
+        const uint32_t P = W[i] & 0x7F7F7F7Fu & nibble_to_bytes((mem >> (4 * i)) & 0xFu);
+        // 0xFF in byte b iff byte b-1 (b-2, b-3, b-4) continues: prmt replicates bit 7
+        const uint32_t m1 = prmt(__funnelshift_l(pv, W[i], 8), 0u, 0xBA98u);
+        const uint32_t m2 = m1 & prmt(__funnelshift_l(pv, W[i], 16), 0u, 0xBA98u);
+        const uint32_t m3 = m2 & prmt(__funnelshift_l(pv, W[i], 24), 0u, 0xBA98u);
+        const uint32_t m4 = m3 & prmt(pv, 0u, 0xBA98u);
+        a0 = __dp4a(P, 0x01010101u, a0);
+        a1 = __dp4a(P & m1, 0x01010101u, a1);
+        a2 = __dp4a(P & m2, 0x01010101u, a2);
+        a3 = __dp4a(P & m3, 0x01010101u, a3);
+        a4 = __dp4a(P & m4, 0x01010101u, a4);
+    }
+    return a0 + 127u * (a1 + 128u * (a2 + 128u * (a3 + 128u * a4)));
+}
+
+// Nonzero iff some 4-byte word of the slice holds two or more terminators
+// (tl: one bit per byte, four per word).
+__device__ __forceinline__ uint32_t dense_words(uint32_t tl)
+{
+    return ((tl & (tl >> 1)) & 0x7777u) | ((tl & (tl >> 2)) & 0x3333u) | ((tl & (tl >> 3)) & 0x1111u);
+}
+
+// Per-terminator assembly from registers for a slice whose words each hold
+// at most one terminator (dense_words(tl) == 0) and lie inside the stream:
+// one fixed step per word, emit(value) in order.
+template <typename F>
+__device__ __forceinline__ void assemble_words(uint32_t wp, uint4 w, uint32_t tl, uint32_t t20, F emit)
+{
+    const uint32_t W[5] = {wp, w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t nib = (tl >> (4 * j)) & 0xFu;
+        if (nib) {
+            const int o4 = __ffs(nib) - 1;
+            const int o = 4 * j + o4;
+            const uint32_t below = t20 & ((1u << (o + 4)) - 1u);   // terminators before it (t20 bits)
+            const int L = min(o + 4 - (31 - __clz(below)), 5);     // none: 5 or more bytes
+            const uint32_t lo4 = __funnelshift_r(W[j], W[j + 1], 8 * o4);
+            const uint32_t x = prmt(W[j + 1], 0u, 0x4440u | static_cast<uint32_t>(o4));
+            emit(assemble(lo4, x, L));
+        }
+    }
+}
+
 // Bit j set iff byte va + j lies inside [lo, hi).
 __device__ __forceinline__ uint32_t slice_valid(uintptr_t va, uintptr_t lo, uintptr_t hi)
 {

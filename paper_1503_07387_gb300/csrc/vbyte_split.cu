@@ -122,8 +122,15 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
         if (t == p.nwt - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((tl >> (hi - 1 - va)) & 1u))
             atomicOr(p.status, VBYTE_ERR_TRUNCATED);
         if (kDelta) {
-            if (in && !(c20 & (c20 << 1) & 0xFFFF8u))
+            // codes of at most two bytes, codes in separate words, any codes
+            // (warp-uniform choices), per-integer assembly at the stream's ends
+            const bool le2 = !(c20 & (c20 << 1) & 0xFFFF8u);
+            if (in && __all_sync(~0u, le2))
                 sum += sum_le2_fast(w[u], wp);
+            else if (in && !__any_sync(~0u, dense_words(tl)))
+                assemble_words(wp, w[u], tl, t20, [&](uint32_t v) { sum += v; });
+            else if (in)
+                sum += sum_any_fast(w[u], wp, tl, t20);
             else
                 assemble_regs(wp, w[u], tl, t20, tc, [&](uint32_t v) { sum += v; });
         }
@@ -133,7 +140,7 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
 }
 
 template <bool kDelta>
-__global__ void __launch_bounds__(kThreads) count_kernel(const Params p)
+__global__ void __launch_bounds__(kThreads, 5) count_kernel(const Params p)
 {
     __shared__ uint2 E[kMaxT];
     __shared__ uint32_t wcnt[kWarps], wsum[kWarps];
@@ -331,12 +338,19 @@ __device__ __forceinline__ void unit_stage(const uint8_t *ub, bool in, uintptr_t
             wp = c4[j];
         }
     } else {
-        // longer codes: each value assembled once, then running sums from this
+        // longer codes: each value assembled once (one fixed step per word
+        // when no word holds two terminators), then running sums from this
         // lane's offset within the unit
-        assemble_all(sw, lane, m.tl, m.t20, m.tc, [&](uint32_t v) {
-            *dst++ = v;
-            vsum += v;
-        });
+        if (in && !__any_sync(~0u, dense_words(m.tl)))
+            assemble_words(m.wprev, m.w, m.tl, m.t20, [&](uint32_t v) {
+                *dst++ = v;
+                vsum += v;
+            });
+        else
+            assemble_all(sw, lane, m.tl, m.t20, m.tc, [&](uint32_t v) {
+                *dst++ = v;
+                vsum += v;
+            });
         dst -= cnt;
         if (kDelta) {
             const uint32_t incs = warp_incl_scan(vsum, lane);

@@ -163,3 +163,23 @@ def test_plain_c_consumer(tmp_path):
     assert out[1] == bytes(oracle.encode64(np.array([1, (1 << 64) - 1], np.uint64))).hex()
     assert out[2] == "1"   # VBYTE_EINVAL, before any CUDA call
     assert out[3] == "1"   # a wait bound above the default is refused
+
+
+def test_kernel_choice_by_length_class():
+    """The single-stream kernel the library picks (host logic, no GPU): the
+    single pass for inputs under 16 MiB, count-then-decode for one-byte codes,
+    the single pass for long differential codes, the split launches else; a
+    forced choice wins until it is cleared."""
+    M = 1 << 20
+    assert vbyte.chosen_passes(4 * M, 3 * M, False) == 1
+    assert vbyte.chosen_passes(64 * M, 64 * M, True) == 2
+    assert vbyte.chosen_passes(300 * M, 60 * M, True) == 1
+    assert vbyte.chosen_passes(300 * M, 60 * M, False) == 3
+    assert vbyte.chosen_passes(96 * M, 64 * M, True) == 3
+    try:
+        vbyte.debug_force_passes(2)
+        assert vbyte.chosen_passes(4 * M, 3 * M, False) == 2
+    finally:
+        vbyte.debug_force_passes(0)
+    with pytest.raises(vbyte.VByteError):
+        vbyte.debug_force_passes(4)
