@@ -91,6 +91,12 @@ size_t vbyte_encode_delta(const uint32_t *h_in, size_t n, uint32_t prev,
 size_t vbyte_encode_delta_m1(const uint32_t *h_in, size_t n, uint32_t prev,
                              uint8_t *h_out);
 
+/* Blocked differences (Sec. 1): encode h_in[i] - h_in[i-4] modulo 2^32 with
+ * h_in[-4..-1] = h_prev4[0..3] (NULL for zeros: the paper's x_1, x_2, x_3,
+ * x_4, x_5 - x_1, ...).  Returns the number of bytes written. */
+size_t vbyte_encode_delta4(const uint32_t *h_in, size_t n, const uint32_t *h_prev4,
+                           uint8_t *h_out);
+
 /* Encode num_lists lists laid end to end: list j is
  * h_in[h_val_off[j] .. h_val_off[j+1]).  With delta != 0 each list is
  * differentially coded on its own, starting from h_prev[j] (0 when h_prev is
@@ -154,6 +160,20 @@ int vbyte_decode_delta(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
  * a piece after the first, pass as prev the last value before it plus one. */
 int vbyte_decode_delta_m1(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
                           size_t n, uint32_t prev, void *stream);
+
+/* Blocked differences (Sec. 1, "Differential coding": storing x_1, x_2, x_3,
+ * x_4, x_5 - x_1, x_6 - x_2, ... so that four running sums proceed side by
+ * side): d_out[i] = g_i + d_out[i-4] modulo 2^32 over the decoded integers
+ * g, with d_out[-4..-1] = h_prev4[0..3] (four values in HOST memory, read
+ * during the call; NULL for zeros, which gives the paper's list).  Each of
+ * the four classes of ranks modulo 4 is its own running sum.  Arguments and
+ * errors as vbyte_decode; the bytes are those vbyte_encode_delta4 writes.
+ * For a piece after the first, pass the last four values before it (the one
+ * at rank i - 4 ... i - 1 for the piece's rank i) as h_prev4, ordered by
+ * rank modulo 4 relative to the piece: h_prev4[k] is the value four ranks
+ * before the piece's k-th value. */
+int vbyte_decode_delta4(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
+                        size_t n, const uint32_t *h_prev4, void *stream);
 
 /* ---- batched GPU decoding ------------------------------------------------ */
 

@@ -369,6 +369,22 @@ int vbyte_decode_delta_m1(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, s
     return vbk::launch_decode(d_in, nbytes, d_out, n, true, prev, static_cast<cudaStream_t>(stream), true);
 }
 
+int vbyte_decode_delta4(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size_t n, const uint32_t *h_prev4,
+                        void *stream)
+{
+    if (nbytes == 0 && n == 0) return VBYTE_OK;
+    if ((nbytes && !d_in) || (n && !d_out)) return VBYTE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_out) & 3u) return VBYTE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *ws = nullptr;
+    const int rc = vbk::stream_workspace(s, vbk::stream_workspace_bytes_any(d_in, nbytes), &ws);
+    if (rc != VBYTE_OK) return rc;
+    uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+    if (nbytes == 0) return vbk::set_status_async(status, VBYTE_ERR_COUNT_MISMATCH, s);   // n > 0 from no bytes
+    const uint32_t zeros[4] = {0u, 0u, 0u, 0u};
+    return vbk::enqueue_split(d_in, nbytes, d_out, n, false, 0u, ws, status, s, false, h_prev4 ? h_prev4 : zeros);
+}
+
 int vbyte_decode_batched(const uint8_t *d_in, size_t nbytes, const uint64_t *d_byte_off, uint32_t *d_out,
                          size_t n, const uint64_t *d_val_off, size_t num_lists, void *stream)
 {

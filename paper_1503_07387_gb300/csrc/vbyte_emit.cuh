@@ -72,6 +72,49 @@ __device__ __forceinline__ void emit_staged(uint32_t *oq, const uint32_t *vals, 
     }
 }
 
+// Component k of v (k in 0..3).
+__device__ __forceinline__ uint32_t pick4(uint4 v, uint32_t k)
+{
+    return (k & 2u) ? ((k & 1u) ? v.w : v.z) : ((k & 1u) ? v.y : v.x);
+}
+
+// The same copy-out with an addend per output word position within its
+// 16-byte quad (add4.x for the words on 16-byte boundaries, add4.y for the
+// next ones, ...): in the blocked-difference variant that position fixes a
+// value's class (its rank modulo 4).
+template <int SH>
+__device__ __forceinline__ void emit_staged4(uint32_t *oq, const uint32_t *vals, int wc, uint4 add4, long long room,
+                                             int lane)
+{
+    constexpr int qa = SH ? 1 : 0;
+    const int lim = room < wc ? (room > 0 ? static_cast<int>(room) : 0) : wc;
+    const int qb = (lim + SH) >> 2;
+    for (int q = qa + lane; q < qb; q += kEmitLanes) {
+        uint4 e = staged_quad<SH>(vals, q);
+        e.x += add4.x;
+        e.y += add4.y;
+        e.z += add4.z;
+        e.w += add4.w;
+        st_quad(oq + 4 * q, e);
+    }
+    const bool whole = qb > qa;
+    const int hb = whole ? min(4 * qa - SH, lim) : lim;
+    const int tb = whole ? 4 * qb - SH : lim;
+    for (int r = lane; r < hb; r += kEmitLanes) oq[SH + r] = vals[4 + r] + pick4(add4, (SH + r) & 3);
+    for (int r = tb + lane; r < lim; r += kEmitLanes) oq[SH + r] = vals[4 + r] + pick4(add4, (SH + r) & 3);
+}
+
+__device__ __forceinline__ void emit_staged4(uint32_t *oq, const uint32_t *vals, int wc, uint4 add4, long long room,
+                                             int lane, int sh)
+{
+    switch (sh) {   // warp-uniform
+    case 0: emit_staged4<0>(oq, vals, wc, add4, room, lane); break;
+    case 1: emit_staged4<1>(oq, vals, wc, add4, room, lane); break;
+    case 2: emit_staged4<2>(oq, vals, wc, add4, room, lane); break;
+    default: emit_staged4<3>(oq, vals, wc, add4, room, lane); break;
+    }
+}
+
 // The copy-out of a one-byte warp from its staged bytes (wb: its first byte;
 // the 4 bytes before and after it are staged too).  Output quad Q = 32m + l,
 // taken by lane l, holds ranks 4Q - SH .. 4Q - SH + 3, whose bytes start at

@@ -61,6 +61,17 @@ size_t encode_gaps(const uint32_t *in, size_t n, uint32_t prev, uint8_t *out, bo
     return static_cast<size_t>(o - out);
 }
 
+// Blocked differences x_i - x_{i-4}, with x_{-4..-1} = prev4[0..3].
+size_t encode_blocks(const uint32_t *in, size_t n, const uint32_t *prev4, uint8_t *out)
+{
+    uint8_t *o = out;
+    for (size_t i = 0; i < n; ++i) {
+        const uint32_t before = i >= 4 ? in[i - 4] : (prev4 ? prev4[i] : 0u);
+        o += put_value(in[i] - before, o);   // modulo 2^32
+    }
+    return static_cast<size_t>(o - out);
+}
+
 }  // namespace
 
 extern "C" {
@@ -87,6 +98,13 @@ size_t vbyte_encode_delta_m1(const uint32_t *h_in, size_t n, uint32_t prev, uint
     if (n == 0) return 0;
     if (!h_in || !h_out) return 0;
     return encode_gaps(h_in, n, prev, h_out, true);
+}
+
+size_t vbyte_encode_delta4(const uint32_t *h_in, size_t n, const uint32_t *h_prev4, uint8_t *h_out)
+{
+    if (n == 0) return 0;
+    if (!h_in || !h_out) return 0;
+    return encode_blocks(h_in, n, h_prev4, h_out);
 }
 
 size_t vbyte_encode_batched(const uint32_t *h_in, const uint64_t *h_val_off,

@@ -69,8 +69,10 @@ size_t stream_workspace_bytes_any(const uint8_t *in, size_t nbytes);
 // alignment.
 size_t split_workspace_bytes(const uint8_t *in, size_t nbytes);
 size_t split_workspace_bound(size_t nbytes);
+// prev4 (host, four values): the blocked-difference form (delta and rank
+// false), x_i = g_i + x_{i-4} with x_{-4..-1} = prev4[0..3].
 int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank);
+                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank, const uint32_t *prev4 = nullptr);
 // The kernel vbyte_decode* use for an input of nbytes holding n values:
 // 1 (single pass), 2 (count-then-decode) or 3 (split).
 int choose_passes(size_t nbytes, size_t n, bool delta);

@@ -72,7 +72,93 @@ struct Params {
     uint4 *cpre;        // per range: values before it (lo, hi), running x before it, 0
     uint32_t *status;
     uint32_t prev;      // x_0
+    // blocked differences (x_i = g_i + x_{i-4}): per class of rank modulo 4
+    uint4 prev4;        // x_{-4} .. x_{-1}, the seeds of classes 0..3
+    uint4 *ent4;        // per warp tile: sums before it within its range, by class relative to the range
+    uint4 *ctot4;       // per range: its sums by class relative to its start
+    uint4 *cpre4;       // per range: the running value of each class (by rank modulo 4) before it
 };
+
+// ---- blocked differences: segments of (count, per-class sums)
+//
+// A segment's sums are indexed by class relative to its first rank.  r =
+// rot4(s, c) re-indexes them for a start c ranks later: r[m] = s[(m - c) & 3].
+__device__ __forceinline__ uint4 rot4(uint4 s, uint32_t c)
+{
+    switch (c & 3u) {
+    case 0: return s;
+    case 1: return make_uint4(s.w, s.x, s.y, s.z);
+    case 2: return make_uint4(s.z, s.w, s.x, s.y);
+    default: return make_uint4(s.y, s.z, s.w, s.x);
+    }
+}
+
+__device__ __forceinline__ uint4 add4(uint4 a, uint4 b) { return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+struct Seg4 {
+    uint32_t c;   // values (mod 2^32: only the class shift c & 3 and relative counts are used)
+    uint4 s;      // sums by class relative to the segment's start
+};
+
+// a, then b
+__device__ __forceinline__ Seg4 cat4(Seg4 a, Seg4 b)
+{
+    Seg4 r;
+    r.c = a.c + b.c;
+    r.s = add4(a.s, rot4(b.s, a.c));
+    return r;
+}
+
+__device__ __forceinline__ Seg4 shfl_up4(Seg4 x, int o)
+{
+    Seg4 y;
+    y.c = __shfl_up_sync(~0u, x.c, o);
+    y.s.x = __shfl_up_sync(~0u, x.s.x, o);
+    y.s.y = __shfl_up_sync(~0u, x.s.y, o);
+    y.s.z = __shfl_up_sync(~0u, x.s.z, o);
+    y.s.w = __shfl_up_sync(~0u, x.s.w, o);
+    return y;
+}
+
+__device__ __forceinline__ Seg4 warp_incl_scan4(Seg4 x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Seg4 y = shfl_up4(x, o);
+        if (lane >= o) x = cat4(y, x);
+    }
+    return x;
+}
+
+// Lane-level: f(v) for each value of a slice whose terminator is marked in
+// tc, in order (codes of any length; bytes outside the stream are zero).
+template <typename F>
+__device__ __forceinline__ void slice_values(uint4 w, uint32_t wp, uint32_t tl, uint32_t t20, uint32_t tc, bool in,
+                                             F f)
+{
+    const uint32_t c20 = ~t20 & 0xFFFFFu;
+    if (!(c20 & (c20 << 1) & 0xFFFF8u)) {   // codes of at most two bytes
+        const uint32_t c4[4] = {w.x, w.y, w.z, w.w};
+        uint32_t wpp = wp;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const Pairs pr = pairs_le2(wpp, c4[j]);
+            uint32_t q01 = prmt(pr.lob, pr.hib, 0x5140u);
+            uint32_t q23 = prmt(pr.lob, pr.hib, 0x7362u);
+            q01 -= (q01 & 0xFF00FF00u) >> 1;
+            q23 -= (q23 & 0xFF00FF00u) >> 1;
+            const uint32_t v4[4] = {q01 & 0xFFFFu, q01 >> 16, q23 & 0xFFFFu, q23 >> 16};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((tc >> (4 * j + i)) & 1u) f(v4[i]);
+            wpp = c4[j];
+        }
+    } else if (in && !dense_words(tl)) {
+        assemble_words(wp, w, tl, t20, f);
+    } else {
+        assemble_regs(wp, w, tl, t20, tc, f);
+    }
+}
 
 __device__ __forceinline__ bool interior(const Params &p, uint64_t t) { return t >= p.in_lo && t < p.in_hi; }
 
@@ -91,9 +177,11 @@ __device__ __forceinline__ uint4 load_slice(uintptr_t va, bool inside, uintptr_t
 
 // ---- count
 
-// One warp: the integers of warp tile t and (delta) their sum.
-template <bool kDelta>
-__device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, uint32_t &cnt_out, uint32_t &sum_out)
+// One warp: the integers of warp tile t and (delta) their sum, or (blocked
+// differences, kD4) their sums by class relative to the tile's first rank.
+template <bool kDelta, bool kD4>
+__device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, uint32_t &cnt_out, uint32_t &sum_out,
+                                         uint4 &s4_out)
 {
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
@@ -106,6 +194,8 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
     uint32_t before = 0;
     if (lane == 0 && t > 0) before = __ldg(reinterpret_cast<const uint32_t *>(w0 - 4));
     uint32_t cnt = 0, sum = 0;
+    uint32_t ub = 0;                               // kD4: values of the tile's earlier units
+    uint4 s4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int u = 0; u < kUnits; ++u) {
         uint32_t wp = __shfl_up_sync(~0u, w[u].w, 1);
@@ -115,10 +205,21 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
         const uint32_t tl = term4(w[u].x) | (term4(w[u].y) << 4) | (term4(w[u].z) << 8) | (term4(w[u].w) << 12);
         const uint32_t t20 = term4(wp) | (tl << 4);
         const uint32_t tc = in ? tl : (tl & slice_valid(va, lo, hi));
-        cnt += __popc(tc);
+        const uint32_t cu = __popc(tc);
+        cnt += cu;
         const uint32_t c20 = ~t20 & 0xFFFFFu;
         if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
             atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
+        if (kD4) {
+            // the lane's values by lane-relative class: add to a.x, then rotate,
+            // so a holds class (k + cu) & 3 in component k at the end
+            uint4 a = make_uint4(0u, 0u, 0u, 0u);
+            slice_values(w[u], wp, tl, t20, tc, in, [&](uint32_t v) { a = make_uint4(a.y, a.z, a.w, a.x + v); });
+            const uint32_t inc = warp_incl_scan(cu, lane);
+            // lane class k is tile class (ub + inc - cu + k) & 3
+            s4 = add4(s4, rot4(a, ub + inc));
+            ub += __shfl_sync(~0u, inc, 31);
+        }
         if (t == p.nwt - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((tl >> (hi - 1 - va)) & 1u))
             atomicOr(p.status, VBYTE_ERR_TRUNCATED);
         if (kDelta) {
@@ -137,22 +238,67 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
     }
     cnt_out = __reduce_add_sync(~0u, cnt);
     sum_out = kDelta ? __reduce_add_sync(~0u, sum) : 0u;
+    if (kD4)
+        s4_out = make_uint4(__reduce_add_sync(~0u, s4.x), __reduce_add_sync(~0u, s4.y), __reduce_add_sync(~0u, s4.z),
+                            __reduce_add_sync(~0u, s4.w));
 }
 
-template <bool kDelta>
+// Blocked differences: the range's entries scanned with cat4 (per-class sums
+// re-indexed by the counts before them).
+__device__ __forceinline__ void range_scan4(const Params &p, uint64_t t0, uint32_t nt, const uint2 *E, const uint4 *E4)
+{
+    __shared__ Seg4 wq[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t per = (nt + kThreads - 1) / kThreads;
+    const uint32_t a = min(nt, tid * per), e = min(nt, a + per);
+    Seg4 mine = {0u, make_uint4(0u, 0u, 0u, 0u)};
+    for (uint32_t i = a; i < e; ++i) mine = cat4(mine, Seg4{E[i].x, E4[i]});
+    const Seg4 inc = warp_incl_scan4(mine, lane);
+    if (lane == kLanes - 1) wq[warp] = inc;
+    __syncthreads();
+    Seg4 x = {0u, make_uint4(0u, 0u, 0u, 0u)}, tot = {0u, make_uint4(0u, 0u, 0u, 0u)};
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+        if (q < warp) x = cat4(x, wq[q]);
+        tot = cat4(tot, wq[q]);
+    }
+    Seg4 ex = shfl_up4(inc, 1);
+    if (lane == 0) ex = Seg4{0u, make_uint4(0u, 0u, 0u, 0u)};
+    x = cat4(x, ex);
+    for (uint32_t i = a; i < e; ++i) {
+        p.ent[t0 + i] = make_uint2(x.c, 0u);
+        p.ent4[t0 + i] = x.s;
+        x = cat4(x, Seg4{E[i].x, E4[i]});
+    }
+    if (tid == 0) {
+        p.ctot[blockIdx.x] = make_uint2(tot.c, 0u);
+        p.ctot4[blockIdx.x] = tot.s;
+    }
+}
+
+template <bool kDelta, bool kD4>
 __global__ void __launch_bounds__(kThreads, 5) count_kernel(const Params p)
 {
     __shared__ uint2 E[kMaxT];
+    __shared__ uint4 E4[kD4 ? kMaxT : 1];
     __shared__ uint32_t wcnt[kWarps], wsum[kWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * p.T;
     const uint32_t nt = static_cast<uint32_t>(min(static_cast<uint64_t>(p.T), p.nwt - t0));
     for (uint32_t i = warp; i < nt; i += kWarps) {
         uint32_t c, s;
-        count_wt<kDelta>(p, t0 + i, lane, c, s);
-        if (lane == 0) E[i] = make_uint2(c, s);
+        uint4 s4;
+        count_wt<kDelta, kD4>(p, t0 + i, lane, c, s, s4);
+        if (lane == 0) {
+            E[i] = make_uint2(c, s);
+            if (kD4) E4[i] = s4;
+        }
     }
     __syncthreads();
+    if (kD4) {
+        range_scan4(p, t0, nt, E, E4);
+        return;
+    }
     // exclusive scan of the range's entries: thread i takes [i per, (i + 1) per)
     const uint32_t per = (nt + kThreads - 1) / kThreads;
     const uint32_t a = min(nt, tid * per), e = min(nt, a + per);
@@ -231,6 +377,57 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const Params p)
         if (tid == 0) {
             carry_c += tc;
             carry_s += ts;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && carry_c != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+}
+
+// The blocked-difference form: cat4 over the ranges from the seed (no
+// values, each class at its x_{-4..-1}); per range the count before it and
+// each class's running value before it.
+__global__ void __launch_bounds__(kScanThreads) scan4_kernel(const Params p)
+{
+    __shared__ Seg4 wq[kScanThreads / 32];
+    __shared__ Seg4 carry;                 // the seed, then every range before the block
+    __shared__ unsigned long long carry_c; // values before the block
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Seg4 zero = {0u, make_uint4(0u, 0u, 0u, 0u)};
+    if (tid == 0) {
+        carry = Seg4{0u, p.prev4};
+        carry_c = 0;
+    }
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < p.G; b0 += kScanThreads) {
+        const uint32_t i = b0 + tid;
+        const Seg4 v = i < p.G ? Seg4{p.ctot[i].x, p.ctot4[i]} : zero;
+        const Seg4 inc = warp_incl_scan4(v, lane);   // a warp's count fits 32 bits
+        if (lane == 31) wq[warp] = inc;
+        __syncthreads();
+        Seg4 x = carry;
+        unsigned long long xc = carry_c;
+        for (int q = 0; q < warp; ++q) {
+            x = cat4(x, wq[q]);
+            xc += wq[q].c;
+        }
+        Seg4 ex = shfl_up4(inc, 1);
+        if (lane == 0) ex = zero;
+        x = cat4(x, ex);
+        xc += ex.c;
+        if (i < p.G) {
+            p.cpre[i] = make_uint4(static_cast<uint32_t>(xc), static_cast<uint32_t>(xc >> 32), 0u, 0u);
+            p.cpre4[i] = x.s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            Seg4 c = carry;
+            unsigned long long cc = carry_c;
+            for (int q = 0; q < kScanThreads / 32; ++q) {
+                c = cat4(c, wq[q]);
+                cc += wq[q].c;
+            }
+            carry = c;
+            carry_c = cc;
         }
         __syncthreads();
     }
@@ -409,7 +606,43 @@ __device__ __forceinline__ void unit_emit(const Params &p, const uint8_t *ub, ui
                        sh);
 }
 
-template <bool kDelta, bool kRank>
+// Blocked differences: per-class running sums in place over a unit's staged
+// values (quad j holds ranks 4j .. 4j + 3 of the unit, component k the class
+// k relative to the unit's first rank); returns each class's total.  Ranks
+// past wc count as zero.
+__device__ __forceinline__ uint4 class_scan(uint32_t *vals, uint32_t wc, int lane)
+{
+    const uint32_t nq = (wc + 3u) >> 2;
+    uint4 *v4 = reinterpret_cast<uint4 *>(vals + 4);
+    uint4 carry = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t j0 = 0; j0 < nq; j0 += kLanes) {
+        const uint32_t j = j0 + lane;
+        uint4 v = j < nq ? v4[j] : make_uint4(0u, 0u, 0u, 0u);
+        if (j + 1 == nq) {   // the last quad: ranks past wc
+            const uint32_t r = wc - 4u * j;
+            if (r < 2) v.y = 0u;
+            if (r < 3) v.z = 0u;
+            if (r < 4) v.w = 0u;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a = __shfl_up_sync(~0u, v.x, o), b = __shfl_up_sync(~0u, v.y, o);
+            const uint32_t c = __shfl_up_sync(~0u, v.z, o), d = __shfl_up_sync(~0u, v.w, o);
+            if (lane >= o) {
+                v.x += a;
+                v.y += b;
+                v.z += c;
+                v.w += d;
+            }
+        }
+        if (j < nq) v4[j] = add4(carry, v);
+        carry = add4(carry, make_uint4(__shfl_sync(~0u, v.x, 31), __shfl_sync(~0u, v.y, 31),
+                                       __shfl_sync(~0u, v.z, 31), __shfl_sync(~0u, v.w, 31)));
+    }
+    return carry;
+}
+
+template <bool kDelta, bool kRank, bool kD4 = false>
 __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
 {
     __shared__ WarpSmem Wsm[kWarps];
@@ -433,6 +666,9 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
     issue(1);
     unsigned long long R = 0;
     uint32_t X = 0;
+    uint4 B = make_uint4(0u, 0u, 0u, 0u);   // kD4: each class's running value (class = rank mod 4)
+    uint4 cp4 = make_uint4(0u, 0u, 0u, 0u);
+    if (kD4) cp4 = p.cpre4[blockIdx.x];
     uint2 e_next = make_uint2(0u, 0u);
     if (K) e_next = p.ent[t0 + warp];
     for (uint32_t k = 0; k < K; ++k) {
@@ -444,6 +680,7 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
         if (u == 0) {
             R = C0 + e_next.x;
             X = cp.z + e_next.y;
+            if (kD4) B = add4(cp4, rot4(p.ent4[t], static_cast<uint32_t>(C0)));
             if (k + kUnits < K) e_next = p.ent[t + kWarps];   // the next tile's prefix travels meanwhile
         }
         const uint8_t *ub = M.ring[k % kRing];
@@ -452,7 +689,27 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
         bool one;
         unit_stage<kDelta>(ub, interior(p, t), ua, lo, hi, M.vals, lane, wc, ws, one);
         __syncwarp();
-        unit_emit<kDelta, kRank>(p, ub, M.vals, one, wc, R, X, lane);
+        if (kD4) {
+            if (one) {   // one-byte integers: the bytes become the staged values
+                const uint4 w = *reinterpret_cast<const uint4 *>(ub + kHalo + lane * kBPT);
+                uint4 *d4 = reinterpret_cast<uint4 *>(M.vals + 4 + 16 * lane);
+                d4[0] = bytes_as_values(w.x);
+                d4[1] = bytes_as_values(w.y);
+                d4[2] = bytes_as_values(w.z);
+                d4[3] = bytes_as_values(w.w);
+                __syncwarp();
+            }
+            const uint4 T = class_scan(M.vals, wc, lane);
+            __syncwarp();
+            const uint32_t ow = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
+            const int sh = static_cast<int>((ow + static_cast<uint32_t>(R)) & 3u);
+            // the output word at position j of a 16-byte quad holds class (j - ow) & 3
+            emit_staged4(p.out + (static_cast<long long>(R) - sh), M.vals, static_cast<int>(wc), rot4(B, ow),
+                         static_cast<long long>(p.n) - static_cast<long long>(R), lane, sh);
+            B = add4(B, rot4(T, static_cast<uint32_t>(R)));
+        } else {
+            unit_emit<kDelta, kRank>(p, ub, M.vals, one, wc, R, X, lane);
+        }
         R += wc;
         X += ws;
         __syncwarp();   // the value buffer and this unit's slot are free again
@@ -463,7 +720,7 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
 // ---- host
 
 struct Layout {
-    size_t ent, ctot, cpre, total;
+    size_t ent, ctot, cpre, ent4, ctot4, cpre4, total;
 };
 
 uint64_t wtiles_for(uintptr_t addr, size_t nbytes) { return nbytes ? ((addr & 15u) + nbytes + kWT - 1) / kWT : 0; }
@@ -473,13 +730,17 @@ uint32_t max_ranges(uint64_t nwt)
     return static_cast<uint32_t>(std::min<uint64_t>(nwt, kMaxRanges + nwt / kMaxT));
 }
 
-Layout layout(uint64_t nwt, uint64_t G)
+// d4: with the per-class arrays of blocked differences.
+Layout layout(uint64_t nwt, uint64_t G, bool d4)
 {
     Layout L;
     L.ent = 256;   // after the status head
     L.ctot = (L.ent + 8 * nwt + 15) / 16 * 16;
     L.cpre = (L.ctot + 8 * G + 15) / 16 * 16;
-    L.total = L.cpre + 16 * G;
+    L.ent4 = L.cpre + 16 * G;
+    L.ctot4 = L.ent4 + (d4 ? 16 * nwt : 0);
+    L.cpre4 = L.ctot4 + (d4 ? 16 * G : 0);
+    L.total = L.cpre4 + (d4 ? 16 * G : 0);
     return L;
 }
 
@@ -510,19 +771,21 @@ int dev_info(Dev *out)
 size_t split_workspace_bytes(const uint8_t *in, size_t nbytes)
 {
     const uint64_t nwt = sp::wtiles_for(reinterpret_cast<uintptr_t>(in), nbytes);
-    return sp::layout(nwt, sp::max_ranges(nwt)).total;
+    return sp::layout(nwt, sp::max_ranges(nwt), true).total;
 }
 
 size_t split_workspace_bound(size_t nbytes)
 {
     const uint64_t nwt = sp::wtiles_for(15, nbytes);   // the worst alignment
-    return sp::layout(nwt, sp::max_ranges(nwt)).total;
+    return sp::layout(nwt, sp::max_ranges(nwt), true).total;
 }
 
 int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank)
+                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank, const uint32_t *prev4)
 {
     if (rank && !delta) return VBYTE_EINVAL;
+    const bool d4 = prev4 != nullptr;
+    if (d4 && (delta || rank)) return VBYTE_EINVAL;
     if (reinterpret_cast<uintptr_t>(ws) & 15u) return VBYTE_EINVAL;
     sp::Dev di;
     int rc = sp::dev_info(&di);
@@ -535,7 +798,7 @@ int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     T = std::min<uint64_t>(T, sp::kMaxT);
     const uint64_t G = (nwt + T - 1) / T;
     if (G > sp::max_ranges(nwt)) return VBYTE_EINVAL;
-    const sp::Layout L = sp::layout(nwt, G);
+    const sp::Layout L = sp::layout(nwt, G, d4);
     sp::Params p = {};
     p.in = in;
     p.nbytes = nbytes;
@@ -552,10 +815,21 @@ int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     p.cpre = reinterpret_cast<uint4 *>(ws + L.cpre);
     p.status = status;
     p.prev = prev;
+    if (d4) {
+        p.prev4 = make_uint4(prev4[0], prev4[1], prev4[2], prev4[3]);
+        p.ent4 = reinterpret_cast<uint4 *>(ws + L.ent4);
+        p.ctot4 = reinterpret_cast<uint4 *>(ws + L.ctot4);
+        p.cpre4 = reinterpret_cast<uint4 *>(ws + L.cpre4);
+        const unsigned dg = static_cast<unsigned>(G);
+        sp::count_kernel<false, true><<<dg, sp::kThreads, 0, s>>>(p);
+        sp::scan4_kernel<<<1, sp::kScanThreads, 0, s>>>(p);
+        sp::decode_kernel<false, false, true><<<dg, sp::kThreads, 0, s>>>(p);
+        return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+    }
     if (delta)
-        sp::count_kernel<true><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
+        sp::count_kernel<true, false><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
     else
-        sp::count_kernel<false><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
+        sp::count_kernel<false, false><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
     sp::scan_kernel<<<1, sp::kScanThreads, 0, s>>>(p);
     if (rank)
         sp::decode_kernel<true, true><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);

@@ -52,6 +52,8 @@ def _signatures(lib):
         "vbyte_encode_delta_m1": ([P, S, U32, P], S),
         "vbyte_encode_delta_m1_device": ([P, S, U32, P, P, P], I),
         "vbyte_decode_delta_m1": ([P, S, P, S, U32, P], I),
+        "vbyte_decode_delta4": ([P, S, P, S, P, P], I),
+        "vbyte_encode_delta4": ([P, S, P, P], S),
         "vbyte_encode_batched": ([P, P, S, I, P, P, P], S),
         "vbyte_encode_device": ([P, S, P, P, P], I),
         "vbyte_encode_delta_device": ([P, S, U32, P, P, P], I),
@@ -250,6 +252,36 @@ def decode_delta_m1(data, n: int, prev: int = 0, out=None, stream=None):
                                       ctypes.c_void_p(out.data_ptr()), n,
                                       ctypes.c_uint32(prev & 0xFFFFFFFF), _stream_handle(stream))
     _check(rc, "vbyte_decode_delta_m1")
+    return out
+
+
+def _prev4(prev4):
+    if prev4 is None:
+        return None
+    p = np.ascontiguousarray(prev4, dtype=np.uint32)
+    if p.size != 4:
+        raise ValueError("prev4 holds the four values before the list")
+    return p
+
+
+def encode_delta4(values, prev4=None) -> np.ndarray:
+    """Host encoding of the blocked differences x_i - x_{i-4} (mod 2^32),
+    x_{-4..-1} = prev4 (zeros: the paper's list)."""
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    p = _prev4(prev4)
+    out = np.empty(max(5 * v.size, 1), dtype=np.uint8)
+    nb = load().vbyte_encode_delta4(_np_ptr(v), v.size, None if p is None else _np_ptr(p), _np_ptr(out))
+    return out[:nb]
+
+
+def decode_delta4(data, n: int, prev4=None, out=None, stream=None):
+    """Decode blocked differences: out[i] = g_i + out[i-4] (mod 2^32) with
+    out[-4..-1] = prev4 (four values; None for zeros)."""
+    out = _device_args(data, n, out)
+    p = _prev4(prev4)
+    rc = load().vbyte_decode_delta4(ctypes.c_void_p(data.data_ptr()), data.numel(), ctypes.c_void_p(out.data_ptr()),
+                                    n, None if p is None else _np_ptr(p), _stream_handle(stream))
+    _check(rc, "vbyte_decode_delta4")
     return out
 
 

@@ -183,3 +183,11 @@ def test_kernel_choice_by_length_class():
         vbyte.debug_force_passes(0)
     with pytest.raises(vbyte.VByteError):
         vbyte.debug_force_passes(4)
+
+
+def test_host_encoder_delta4_matches_oracle():
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, 1 << 32, 10_001, dtype=np.uint64).astype(np.uint32)
+    for prev4 in (None, [1, 2, 3, 4], [0xFFFFFFFF] * 4):
+        assert np.array_equal(vbyte.encode_delta4(x, prev4=prev4), oracle.encode_delta4(x, prev4=prev4))
+    assert vbyte.encode_delta4(np.zeros(0, np.uint32)).size == 0
