@@ -211,13 +211,27 @@ int vbyte_decode_delta_batched(const uint8_t *d_in, size_t nbytes,
 /* An opaque, reusable batched decode of one fixed batch (the arguments of
  * vbyte_decode_batched / vbyte_decode_delta_batched; d_prev is ignored when
  * delta = 0).  Creation synchronises `stream` (the inputs must be ready),
- * allocates the plan's own workspace (cudaMalloc), and, when autotune != 0,
- * picks the batched kernel's launch parameters -- CTAs per SM and how far
- * counting runs ahead of decoding -- by timing every candidate on this
- * batch, or reuses the choice made earlier for the same length class
- * (device, delta, log2 of mean bytes per list, log2 of total bytes).  It then
- * captures the launch sequence into a CUDA graph.  Creation overwrites
- * d_out (with the decoded values) while tuning.  A plan may be launched any
+ * copies the offsets to the host, allocates the plan's own device memory
+ * (cudaMalloc), chooses how to decode, and captures the launch sequence into
+ * a CUDA graph.  The lists are grouped in length classes (class k: lists of
+ * 2^k .. 2^(k+1) - 1 bytes, as Sec. 5 groups posting lists by length).  Two
+ * kernels are candidates:
+ *   - list items: one warp decodes one item -- a whole list of at most C
+ *     bytes in a single pass, or a C-byte chunk of a longer list after a
+ *     count launch over the chunks and a scan of each list's chunk counts and
+ *     sums (count then decode) -- so the chunk size C decides, per length
+ *     class, between the single pass and count-then-decode; the decode
+ *     launch runs 128 or 256 threads per block;
+ *   - the segmented stream kernel of vbyte_decode_batched (the lists laid end
+ *     to end decoded as one stream), with CTAs per SM and how far counting
+ *     runs ahead of decoding.
+ * With autotune != 0 every candidate (C in 8, 16, 32, 64 KiB x 128 or 256
+ * threads per block, and the segmented kernel) is timed on this batch, or the
+ * choice made earlier for the same batch class (device, delta, log2 of mean
+ * bytes per list, log2 of total bytes) is reused; otherwise list items with
+ * C = 32 KiB and 256 threads per block (the segmented kernel if the offsets
+ * break their contract).  Creation overwrites d_out (with the decoded
+ * values) while tuning.  A plan may be launched any
  * number of times; launches of one plan must not overlap on the GPU (they
  * share its workspace).  Data errors go to the plan's own status word.
  * Returns VBYTE_EINVAL as vbyte_decode_batched does (and for num_lists = 0),
@@ -236,6 +250,18 @@ int vbyte_plan_get_status(vbyte_plan *plan, void *stream, uint32_t *status_out);
  * time in ms, and tuned = 0 (defaults), 1 (timed now), 2 (from the cache). */
 int vbyte_plan_describe(const vbyte_plan *plan, int *ctas_per_sm,
                         uint64_t *lead_slack, float *tuned_ms, int *tuned);
+/* The chosen kernel: 0 = the segmented stream kernel, 1 = list items; for
+ * list items the chunk size C in bytes and the decode launch's threads per
+ * block (0 and 256 for the segmented kernel). */
+int vbyte_plan_choice(const vbyte_plan *plan, int *kernel, uint64_t *chunk_bytes,
+                      int *threads_per_block);
+/* Length class k (0..63; lists of 2^k .. 2^(k+1) - 1 bytes, class 0 also the
+ * empty lists): its lists, its values, and how the plan decodes them:
+ * 0 = no lists, 1 = single pass (each list one item), 2 = count then decode
+ * (lists cut into chunks), 3 = the segmented stream kernel.  VBYTE_EINVAL for
+ * k outside 0..63. */
+int vbyte_plan_class(const vbyte_plan *plan, int k, uint64_t *lists,
+                     uint64_t *values, int *mode);
 /* Free the plan's graph and workspace (synchronises the device). */
 void vbyte_plan_destroy(vbyte_plan *plan);
 

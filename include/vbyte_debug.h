@@ -44,6 +44,14 @@ int vbyte_debug_inject(long long skip_tile, uint64_t wait_limit_ns);
  * compare them.  Returns VBYTE_OK, or VBYTE_EINVAL for another value. */
 int vbyte_debug_force_passes(int passes);
 
+/* The choice vbyte_plan_create makes from now on (process-wide), in place of
+ * its defaults or its timing: kernel 0 (the segmented stream kernel) or 1
+ * (list items of chunk_bytes, a multiple of 16 of at least 4096, with
+ * threads_per_block 128 or 256); kernel -1 restores the usual choice.
+ * Exists so that tests can check every candidate.  Returns VBYTE_OK, or
+ * VBYTE_EINVAL for another value. */
+int vbyte_debug_force_plan(int kernel, uint64_t chunk_bytes, int threads_per_block);
+
 /* The kernel (1, 2 or 3, as above) that a single-stream call on an
  * nbytes-byte input holding n values would use now. */
 int vbyte_debug_passes_for(size_t nbytes, size_t n, int delta);

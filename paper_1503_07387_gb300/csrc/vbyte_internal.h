@@ -102,6 +102,27 @@ int sbatched_max_ctas(bool delta);   // CTAs per SM of that kernel
 int load_kernels();
 int enqueue_sbatched(const BatchArgs &a, uint8_t *ws, const LaunchCfg &cfg, cudaStream_t s);
 
+// Batched decoding as list items (vbyte_split.cu, for tuned plans): a whole
+// list, or a chunk of a long one, per item; one warp decodes an item.
+struct ListItem {
+    unsigned long long b0, b1;   // input bytes [b0, b1) whose terminators the item owns
+    uint32_t list;
+    uint32_t flags;              // kItemOnly: the list's only item; kItemLast: it ends the list
+};
+constexpr uint32_t kItemOnly = 1u, kItemLast = 2u;
+// Device arrays of one item set (owned by the plan).
+struct ListPlan {
+    ListItem *items;     // decode order (longest first)
+    uint32_t nitems;
+    uint32_t *citem;     // items of chunked lists, list by list, in chunk order
+    uint32_t *cfirst;    // per chunked list its first citem entry, then the number of entries
+    uint32_t ncl;        // chunked lists
+    uint2 *cs;           // per item: count and sum
+    uint2 *rel;          // per item: count and sum of its list's earlier chunks (zeros at creation)
+    unsigned int *queue;
+};
+int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta, uint32_t *status, cudaStream_t s);
+
 // A piece of a gather: len bytes from src + src_off to dst + dst_off.
 struct GatherPiece {
     uint64_t src;

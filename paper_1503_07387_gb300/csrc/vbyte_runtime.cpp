@@ -16,20 +16,35 @@
 struct vbyte_plan {
     int dev = 0;
     vbk::BatchArgs a{};
-    vbk::LaunchCfg cfg{};
-    uint8_t *ws = nullptr;
+    int kernel = 0;              // 0: segmented stream kernel, 1: list items
+    vbk::LaunchCfg cfg{};        // kernel 0: CTAs per SM and count-ahead slack
+    uint64_t chunk = 0;          // kernel 1: lists of up to `chunk` bytes decoded whole, longer ones in chunks
+    int warps = 8;               // kernel 1: warps per CTA of the decode launch
+    uint8_t *ws = nullptr;       // status word, and kernel 0's workspace
+    void *lp_mem = nullptr;      // kernel 1's device arrays
+    vbk::ListPlan lp{};
     cudaGraphExec_t exec = nullptr;
     float tuned_ms = 0.f;
-    int tuned = 0;   // 0: defaults, 1: timed now, 2: taken from the per-class cache
+    int tuned = 0;               // 0: defaults, 1: timed now, 2: taken from the per-class cache
+    // length classes by bytes per list: class k holds lists of 2^k .. 2^(k+1) - 1 bytes (class 0 also the empty ones)
+    uint64_t cls_lists[64] = {};
+    uint64_t cls_values[64] = {};
 };
 
 namespace {
 
 // Length class of a batch: delta mode, log2 of the mean bytes per list and
-// log2 of the total bytes.  Tuned launch parameters are cached per class.
+// log2 of the total bytes.  Tuned choices are cached per class.
+struct Choice {
+    int kernel;
+    vbk::LaunchCfg cfg;
+    uint64_t chunk;
+    int warps;
+    float ms;
+};
 using ClassKey = std::tuple<int, int, int, int>;   // device, delta, log2 mean, log2 total
 std::mutex g_tune_mu;
-std::map<ClassKey, std::pair<vbk::LaunchCfg, float>> g_tuned;
+std::map<ClassKey, Choice> g_tuned;
 
 int ilog2(double x) { return x < 1.0 ? 0 : static_cast<int>(std::floor(std::log2(x))); }
 
@@ -39,9 +54,111 @@ ClassKey class_of(int dev, const vbk::BatchArgs &a)
     return ClassKey(dev, a.delta ? 1 : 0, ilog2(mean), ilog2(static_cast<double>(a.nbytes)));
 }
 
-// Median time of `reps` runs of cfg on s (after one untimed run).
-int time_cfg(const vbk::BatchArgs &a, uint8_t *ws, const vbk::LaunchCfg &cfg, cudaStream_t s, int reps,
-             float *ms)
+// The offset arrays' contract, checked on the host copies.
+bool offsets_ok(const std::vector<uint64_t> &bo, const std::vector<uint64_t> &vo, const vbk::BatchArgs &a)
+{
+    if (bo.front() != 0 || vo.front() != 0 || bo.back() != a.nbytes || vo.back() != a.n) return false;
+    for (size_t j = 0; j < a.L; ++j)
+        if (bo[j] > bo[j + 1] || vo[j] > vo[j + 1]) return false;
+    return true;
+}
+
+// Items for chunk size C: lists of at most C bytes whole, longer lists cut
+// at 16-byte boundaries of the input every C bytes; decode order longest
+// first; the chunked lists' items in chunk order.
+struct HostItems {
+    std::vector<vbk::ListItem> items;
+    std::vector<uint32_t> citem, cfirst;
+};
+
+HostItems build_items(const std::vector<uint64_t> &bo, uintptr_t in, uint64_t C)
+{
+    HostItems h;
+    std::vector<vbk::ListItem> raw;
+    std::vector<std::pair<size_t, size_t>> chunked;   // (first raw item, items)
+    const size_t L = bo.size() - 1;
+    raw.reserve(L + bo.back() / C + 1);
+    for (size_t j = 0; j < L; ++j) {
+        const uint64_t b0 = bo[j], b1 = bo[j + 1];
+        if (b1 - b0 <= C) {
+            raw.push_back({b0, b1, static_cast<uint32_t>(j), vbk::kItemOnly | vbk::kItemLast});
+            continue;
+        }
+        const size_t first = raw.size();
+        const uint64_t a = ((in + b0) & ~static_cast<uint64_t>(15)) - in;   // the list's first 16-byte boundary (at or before b0)
+        uint64_t st = b0;
+        for (uint64_t k = 1;; ++k) {
+            const uint64_t e = a + k * C;
+            if (e >= b1) {
+                raw.push_back({st, b1, static_cast<uint32_t>(j), vbk::kItemLast});
+                break;
+            }
+            raw.push_back({st, e, static_cast<uint32_t>(j), 0u});
+            st = e;
+        }
+        chunked.emplace_back(first, raw.size() - first);
+    }
+    std::vector<uint32_t> order(raw.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<uint32_t>(i);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        return raw[x].b1 - raw[x].b0 > raw[y].b1 - raw[y].b0;
+    });
+    std::vector<uint32_t> pos(raw.size());
+    h.items.resize(raw.size());
+    for (size_t i = 0; i < order.size(); ++i) {
+        h.items[i] = raw[order[i]];
+        pos[order[i]] = static_cast<uint32_t>(i);
+    }
+    for (const auto &c : chunked) {
+        h.cfirst.push_back(static_cast<uint32_t>(h.citem.size()));
+        for (size_t r = c.first; r < c.first + c.second; ++r) h.citem.push_back(pos[r]);
+    }
+    h.cfirst.push_back(static_cast<uint32_t>(h.citem.size()));
+    return h;
+}
+
+// Upload an item set into one device allocation (`rel` zeroed).
+int upload_items(const HostItems &h, void **mem, vbk::ListPlan *lp, cudaStream_t s)
+{
+    const size_t ni = h.items.size(), nc = h.citem.size(), nf = h.cfirst.size();
+    auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    const size_t o_items = 0, o_citem = up16(o_items + ni * sizeof(vbk::ListItem));
+    const size_t o_cfirst = up16(o_citem + nc * 4), o_cs = up16(o_cfirst + nf * 4);
+    const size_t o_rel = up16(o_cs + ni * 8), o_q = up16(o_rel + ni * 8), total = o_q + 16;
+    uint8_t *m = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&m), total) != cudaSuccess) {
+        cudaGetLastError();
+        return VBYTE_ENOMEM;
+    }
+    *mem = m;
+    lp->items = reinterpret_cast<vbk::ListItem *>(m + o_items);
+    lp->nitems = static_cast<uint32_t>(ni);
+    lp->citem = reinterpret_cast<uint32_t *>(m + o_citem);
+    lp->cfirst = reinterpret_cast<uint32_t *>(m + o_cfirst);
+    lp->ncl = static_cast<uint32_t>(nf - 1);
+    lp->cs = reinterpret_cast<uint2 *>(m + o_cs);
+    lp->rel = reinterpret_cast<uint2 *>(m + o_rel);
+    lp->queue = reinterpret_cast<unsigned int *>(m + o_q);
+    if (ni && cudaMemcpyAsync(lp->items, h.items.data(), ni * sizeof(vbk::ListItem), cudaMemcpyHostToDevice, s) !=
+                  cudaSuccess)
+        return VBYTE_ECUDA;
+    if (nc && cudaMemcpyAsync(lp->citem, h.citem.data(), nc * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return VBYTE_ECUDA;
+    if (cudaMemcpyAsync(lp->cfirst, h.cfirst.data(), nf * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return VBYTE_ECUDA;
+    if (cudaMemsetAsync(lp->rel, 0, ni * 8, s) != cudaSuccess) return VBYTE_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
+int enqueue_plan(const vbyte_plan &P, cudaStream_t s)
+{
+    if (P.kernel == 1) return vbk::enqueue_list_plan(P.a, P.lp, P.warps, reinterpret_cast<uint32_t *>(P.ws), s);
+    return vbk::enqueue_sbatched(P.a, P.ws, P.cfg, s);
+}
+
+// Median time of `reps` runs of the plan's current choice on s (after one
+// untimed run).
+int time_plan(const vbyte_plan &P, cudaStream_t s, int reps, float *ms)
 {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return VBYTE_ECUDA;
@@ -49,11 +166,11 @@ int time_cfg(const vbk::BatchArgs &a, uint8_t *ws, const vbk::LaunchCfg &cfg, cu
         cudaEventDestroy(e0);
         return VBYTE_ECUDA;
     }
-    int rc = vbk::enqueue_sbatched(a, ws, cfg, s);
+    int rc = enqueue_plan(P, s);
     std::vector<float> t;
     for (int r = 0; r < reps && rc == VBYTE_OK; ++r) {
         cudaEventRecord(e0, s);
-        rc = vbk::enqueue_sbatched(a, ws, cfg, s);
+        rc = enqueue_plan(P, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = VBYTE_ECUDA;
         float x = 0.f;
@@ -67,6 +184,30 @@ int time_cfg(const vbk::BatchArgs &a, uint8_t *ws, const vbk::LaunchCfg &cfg, cu
     *ms = t[t.size() / 2];
     return VBYTE_OK;
 }
+
+void free_items(vbyte_plan *P)
+{
+    if (P->lp_mem) cudaFree(P->lp_mem);
+    P->lp_mem = nullptr;
+    P->lp = vbk::ListPlan{};
+}
+
+// Make the plan's kernel 1 arrays those of chunk size C.
+int set_items(vbyte_plan *P, const std::vector<uint64_t> &bo, uint64_t C, cudaStream_t s)
+{
+    free_items(P);
+    const HostItems h = build_items(bo, reinterpret_cast<uintptr_t>(P->a.in), C);
+    return upload_items(h, &P->lp_mem, &P->lp, s);
+}
+
+constexpr uint64_t kChunks[] = {8u << 10, 16u << 10, 32u << 10, 64u << 10};
+constexpr int kWarpChoices[] = {4, 8};
+
+// vbyte_debug_force_plan
+std::mutex g_force_mu;
+int g_force_kernel = -1;
+uint64_t g_force_chunk = 0;
+int g_force_warps = 8;
 
 }  // namespace
 
@@ -94,6 +235,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
         if (s) cudaStreamDestroy(s);
         if (P->exec) cudaGraphExecDestroy(P->exec);
         if (P->ws) cudaFree(P->ws);
+        free_items(P);
         delete P;
         return code;
     };
@@ -102,49 +244,107 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(VBYTE_ECUDA);
     if (cudaMalloc(&P->ws, vbk::sbatched_workspace_bytes(a)) != cudaSuccess) return fail(VBYTE_ENOMEM);
     if (cudaMemsetAsync(P->ws, 0, sizeof(uint32_t), s) != cudaSuccess) return fail(VBYTE_ECUDA);
+    // the offsets on the host: length classes and list items
+    std::vector<uint64_t> bo(num_lists + 1), vo(num_lists + 1);
+    if (cudaMemcpy(bo.data(), d_byte_off, bo.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(vo.data(), d_val_off, vo.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(VBYTE_ECUDA);
+    const bool items_ok = offsets_ok(bo, vo, a);
+    if (items_ok) {
+        for (size_t j = 0; j < num_lists; ++j) {
+            const uint64_t nb = bo[j + 1] - bo[j];
+            const int k = nb ? 63 - __builtin_clzll(nb) : 0;
+            P->cls_lists[k] += 1;
+            P->cls_values[k] += vo[j + 1] - vo[j];
+        }
+    }
+    // defaults: list items of 32 KiB chunks, 8 warps per CTA (the segmented
+    // stream kernel when the offsets break their contract: it reports that)
+    P->kernel = items_ok ? 1 : 0;
+    P->chunk = 32u << 10;
+    P->warps = 8;
+    int forced = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_force_mu);
+        if (g_force_kernel == 0 || (g_force_kernel == 1 && items_ok)) {
+            forced = g_force_kernel;
+            P->kernel = g_force_kernel;
+            P->chunk = g_force_chunk;
+            P->warps = g_force_warps;
+        }
+    }
 
-    if (autotune) {
+    if (autotune && forced < 0) {
         const ClassKey key = class_of(P->dev, a);
         bool cached = false;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tuned.find(key);
-            if (it != g_tuned.end()) {
-                P->cfg = it->second.first;
-                P->tuned_ms = it->second.second;
+            if (it != g_tuned.end() && (items_ok || it->second.kernel == 0)) {
+                P->kernel = it->second.kernel;
+                P->cfg = it->second.cfg;
+                P->chunk = it->second.chunk;
+                P->warps = it->second.warps;
+                P->tuned_ms = it->second.ms;
                 P->tuned = 2;
                 cached = true;
             }
         }
         if (!cached) {
+            Choice best{0, vbk::LaunchCfg(), 0, 8, 0.f};
+            bool have = false;
+            auto consider = [&](const Choice &c, float ms) {
+                if (!have || ms < best.ms) {
+                    best = c;
+                    best.ms = ms;
+                    have = true;
+                }
+            };
+            // the segmented stream kernel
             const int occ = vbk::sbatched_max_ctas(a.delta);
-            const uint64_t slacks[] = {3584, 4608, 5632};
-            float best = 0.f;
-            for (int c = 1; c <= occ; ++c) {
-                for (uint64_t sl : slacks) {
-                    vbk::LaunchCfg cfg;
-                    cfg.ctas_per_sm = c;
-                    cfg.lead_slack = sl;
-                    float ms = 0.f;
-                    rc = time_cfg(a, P->ws, cfg, s, 3, &ms);
-                    if (rc != VBYTE_OK) return fail(rc);
-                    if (P->tuned == 0 || ms < best) {
-                        best = ms;
-                        P->cfg = cfg;
-                        P->tuned = 1;
+            for (uint64_t sl : {uint64_t(3584), uint64_t(4608)}) {
+                P->kernel = 0;
+                P->cfg.ctas_per_sm = occ;
+                P->cfg.lead_slack = sl;
+                float ms = 0.f;
+                if ((rc = time_plan(*P, s, 3, &ms)) != VBYTE_OK) return fail(rc);
+                consider(Choice{0, P->cfg, 0, 8, 0.f}, ms);
+            }
+            // list items: chunk size (which length classes are decoded whole
+            // in one pass and which by count-then-decode) x warps per CTA
+            if (items_ok) {
+                for (uint64_t C : kChunks) {
+                    if ((rc = set_items(P, bo, C, s)) != VBYTE_OK) return fail(rc);
+                    for (int w : kWarpChoices) {
+                        P->kernel = 1;
+                        P->chunk = C;
+                        P->warps = w;
+                        float ms = 0.f;
+                        if ((rc = time_plan(*P, s, 3, &ms)) != VBYTE_OK) return fail(rc);
+                        consider(Choice{1, vbk::LaunchCfg(), C, w, 0.f}, ms);
                     }
                 }
             }
-            P->tuned_ms = best;
+            P->kernel = best.kernel;
+            P->cfg = best.cfg;
+            P->chunk = best.chunk;
+            P->warps = best.warps;
+            P->tuned_ms = best.ms;
+            P->tuned = 1;
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned[key] = {P->cfg, best};
+            g_tuned[key] = best;
         }
         // the tuning runs' data errors belong to no caller launch
         if (cudaMemsetAsync(P->ws, 0, sizeof(uint32_t), s) != cudaSuccess) return fail(VBYTE_ECUDA);
     }
+    if (P->kernel == 1) {
+        if ((rc = set_items(P, bo, P->chunk, s)) != VBYTE_OK) return fail(rc);
+    } else {
+        free_items(P);
+    }
 
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(VBYTE_ECUDA);
-    rc = vbk::enqueue_sbatched(a, P->ws, P->cfg, s);
+    rc = enqueue_plan(*P, s);
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (rc != VBYTE_OK) return fail(rc);
     if (ce != cudaSuccess) return fail(VBYTE_ECUDA);
@@ -186,6 +386,45 @@ int vbyte_plan_describe(const vbyte_plan *plan, int *ctas_per_sm, uint64_t *lead
     return VBYTE_OK;
 }
 
+int vbyte_debug_force_plan(int kernel, uint64_t chunk_bytes, int threads_per_block)
+{
+    if (kernel < -1 || kernel > 1) return VBYTE_EINVAL;
+    if (kernel == 1 && (chunk_bytes < 4096 || chunk_bytes % 16 || (threads_per_block != 128 && threads_per_block != 256)))
+        return VBYTE_EINVAL;
+    std::lock_guard<std::mutex> lk(g_force_mu);
+    g_force_kernel = kernel;
+    g_force_chunk = chunk_bytes;
+    g_force_warps = threads_per_block / 32;
+    return VBYTE_OK;
+}
+
+int vbyte_plan_choice(const vbyte_plan *plan, int *kernel, uint64_t *chunk_bytes, int *threads_per_block)
+{
+    if (!plan) return VBYTE_EINVAL;
+    if (kernel) *kernel = plan->kernel;
+    if (chunk_bytes) *chunk_bytes = plan->kernel == 1 ? plan->chunk : 0;
+    if (threads_per_block) *threads_per_block = plan->kernel == 1 ? plan->warps * 32 : 256;
+    return VBYTE_OK;
+}
+
+int vbyte_plan_class(const vbyte_plan *plan, int k, uint64_t *lists, uint64_t *values, int *mode)
+{
+    if (!plan || k < 0 || k > 63) return VBYTE_EINVAL;
+    if (lists) *lists = plan->cls_lists[k];
+    if (values) *values = plan->cls_values[k];
+    if (mode) {
+        int m = 0;
+        if (plan->cls_lists[k]) {
+            if (plan->kernel == 0)
+                m = 3;
+            else
+                m = ((uint64_t(2) << k) - 1 <= plan->chunk) ? 1 : 2;   // the whole class fits one item
+        }
+        *mode = m;
+    }
+    return VBYTE_OK;
+}
+
 void vbyte_plan_destroy(vbyte_plan *plan)
 {
     if (!plan) return;
@@ -194,6 +433,7 @@ void vbyte_plan_destroy(vbyte_plan *plan)
     cudaSetDevice(plan->dev);
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->ws) cudaFree(plan->ws);
+    free_items(plan);
     cudaSetDevice(cur);
     delete plan;
 }

@@ -445,18 +445,19 @@ static_assert(sizeof(WarpSmem) % 16 == 0 && kSlot % 16 == 0, "unit buffers keep 
 // Stage unit u of warp tile t into `slot` (the 16 bytes before the unit at
 // slot[0..16), the unit at slot[16..528)); bytes outside the stream as zero.
 // The caller commits.
-__device__ __forceinline__ void issue_unit(const Params &p, uint64_t t, int u, int lane, uint8_t *slot)
+// Stage the unit at ua (16-byte aligned) and the 16 bytes before it into
+// `slot`; bytes outside [lo, hi) as zero.  inside: all of them lie in
+// [lo, hi).  The caller commits.
+__device__ __forceinline__ void stage_unit(uintptr_t ua, int lane, uint8_t *slot, uintptr_t lo, uintptr_t hi,
+                                           bool inside)
 {
-    const uintptr_t ua = p.base + (static_cast<uintptr_t>(t) << 11) + u * kUnit;
     const uintptr_t va = ua + lane * kBPT;
     uint8_t *dst = slot + kHalo + lane * kBPT;
-    if (interior(p, t) && (t > 0 || u > 0)) {   // the unit and the 16 bytes before it are inside
+    if (inside) {
         cp_async16(dst, reinterpret_cast<const void *>(va));
         if (lane == 0) cp_async16(slot, reinterpret_cast<const void *>(ua - 16));
         return;
     }
-    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
-    const uintptr_t hi = lo + p.nbytes;
     if (va >= lo && va + kBPT <= hi) {
         cp_async16(dst, reinterpret_cast<const void *>(va));
     } else {
@@ -472,13 +473,26 @@ __device__ __forceinline__ void issue_unit(const Params &p, uint64_t t, int u, i
     }
 }
 
+__device__ __forceinline__ void issue_unit(const Params &p, uint64_t t, int u, int lane, uint8_t *slot)
+{
+    const uintptr_t ua = p.base + (static_cast<uintptr_t>(t) << 11) + u * kUnit;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    // the unit and the 16 bytes before it are inside the stream
+    const bool inside = interior(p, t) && (t > 0 || u > 0);
+    stage_unit(ua, lane, slot, lo, lo + p.nbytes, inside);
+}
+
 // One warp: decode the staged unit ub into vals (warp rank r at vals[4 + r];
-// delta: running sums from the unit's first value).  Returns the unit's
-// value count and sum; one = every slice holds one-byte integers only (the
-// values stay as bytes and vals is untouched).
-template <bool kDelta>
+// delta: running sums from the unit's first value).  The unit owns the
+// integers whose terminators lie in [lo, hi); in: it owns all its bytes.
+// Returns the unit's value count and sum; one = every slice holds one-byte
+// integers only (the values stay as bytes and vals is untouched).  kCheck:
+// also record runs of five continuation bytes and (dend != 0) a stream that
+// ends at dend inside an integer.
+template <bool kDelta, bool kCheck = false>
 __device__ __forceinline__ void unit_stage(const uint8_t *ub, bool in, uintptr_t ua, uintptr_t lo, uintptr_t hi,
-                                           uint32_t *vals, int lane, uint32_t &wc, uint32_t &ws, bool &one)
+                                           uint32_t *vals, int lane, uint32_t &wc, uint32_t &ws, bool &one,
+                                           uint32_t *status = nullptr, uintptr_t dend = 0)
 {
     const uint4 w0 = *reinterpret_cast<const uint4 *>(ub + kHalo + lane * kBPT);
     const uint32_t wp0 = reinterpret_cast<const uint32_t *>(ub)[(kHalo + lane * kBPT) / 4 - 1];
@@ -496,6 +510,12 @@ __device__ __forceinline__ void unit_stage(const uint8_t *ub, bool in, uintptr_t
     const uint32_t cnt = __popc(m.tc);
     const uint32_t c20 = ~m.t20 & 0xFFFFFu;
     const bool notB = (c20 & (c20 << 1) & 0xFFFF8u) != 0;
+    if (kCheck) {
+        if (c20 & (c20 << 1) & (c20 << 2) & (c20 << 3) & (c20 << 4) & 0xFFFF0u)
+            atomicOr(status, VBYTE_ERR_MALFORMED_LONG);
+        if (dend && dend - 1 >= va && dend - 1 < va + kBPT && !((m.tl >> (dend - 1 - va)) & 1u))
+            atomicOr(status, VBYTE_ERR_TRUNCATED);
+    }
     const uint32_t inc = warp_incl_scan(cnt, lane);
     wc = __shfl_sync(~0u, inc, 31);
     uint32_t *dst = vals + 4 + inc - cnt;
@@ -717,7 +737,190 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
     cp_async_wait_all();
 }
 
+// ---- batched lists as work items (tuned plans)
+//
+// A plan cuts the batch into items: a whole list of at most C bytes, or a
+// C-byte chunk of a longer list (chunks start on 16-byte boundaries of the
+// input).  One warp decodes one item by itself, taking items from a queue,
+// longest first: a whole list in a single pass (its first value's rank and
+// x_0 are vo[j] and prev[j]), a chunk from the count and sum of its list's
+// earlier chunks (a count launch over the chunks, then one warp per chunked
+// list scans them).  Per-list data errors are checked by the decode launch;
+// a chunked list's count by the scan.
+
+using Item = ListItem;
+constexpr uint32_t kOnly = kItemOnly, kLast = kItemLast;
+
+struct LParams {
+    const uint8_t *in;
+    uint32_t *out;
+    const uint64_t *bo, *vo;     // list byte and value offsets
+    const uint32_t *prevs;       // per-list x_0, or null (zeros)
+    const Item *items;           // in decode order
+    uint32_t nitems;
+    const uint32_t *citem;       // the items of chunked lists, list by list, chunk by chunk
+    const uint32_t *cfirst;      // per chunked list: its first citem entry; cfirst[ncl] = the entries
+    uint32_t ncl;
+    uint2 *cs;                   // per item: its count and sum (chunked lists)
+    uint2 *rel;                  // per item: count and sum of its list's earlier chunks (zero for first chunks)
+    unsigned int *queue;         // the decode launch's next item (cleared before it)
+    uint32_t *status;
+};
+
+// One warp: the integers whose terminators lie in [c0, c1) and (delta) their
+// sum; the bytes of the list are [lo, hi) (others read as zero).
+template <bool kDelta>
+__device__ __forceinline__ void count_range(uintptr_t c0, uintptr_t c1, uintptr_t lo, uintptr_t hi, int lane,
+                                            uint32_t &cnt_out, uint32_t &sum_out)
+{
+    uint32_t cnt = 0, sum = 0;
+    const uintptr_t a0 = c0 & ~static_cast<uintptr_t>(15);
+    // the 4 bytes before the first unit
+    uint32_t last = 0;
+    if (lane == 0) last = load_slice(a0 - 16, a0 - 16 >= lo && a0 <= hi, lo, hi).w;
+    for (uintptr_t g = a0; g < c1; g += kUnits * kUnit) {
+        uint4 w[kUnits];
+#pragma unroll
+        for (int u = 0; u < kUnits; ++u) {
+            const uintptr_t va = g + u * kUnit + lane * kBPT;
+            w[u] = va < c1 ? load_slice(va, va >= lo && va + kBPT <= hi, lo, hi) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnits; ++u) {
+            uint32_t wp = __shfl_up_sync(~0u, w[u].w, 1);
+            if (lane == 0) wp = last;
+            last = __shfl_sync(~0u, w[u].w, kLanes - 1);
+            const uintptr_t va = g + u * kUnit + lane * kBPT;
+            const uint32_t tl = term4(w[u].x) | (term4(w[u].y) << 4) | (term4(w[u].z) << 8) | (term4(w[u].w) << 12);
+            const uint32_t t20 = term4(wp) | (tl << 4);
+            const bool own = va >= c0 && va + kBPT <= c1;
+            const uint32_t tc = own ? tl : (tl & slice_valid(va, c0, c1));
+            cnt += __popc(tc);
+            if (kDelta) {
+                const uint32_t c20 = ~t20 & 0xFFFFFu;
+                if (own && !(c20 & (c20 << 1) & 0xFFFF8u))
+                    sum += sum_le2_fast(w[u], wp);
+                else if (own)
+                    sum += sum_any_fast(w[u], wp, tl, t20);
+                else
+                    assemble_regs(wp, w[u], tl, t20, tc, [&](uint32_t v) { sum += v; });
+            }
+        }
+    }
+    cnt_out = __reduce_add_sync(~0u, cnt);
+    sum_out = kDelta ? __reduce_add_sync(~0u, sum) : 0u;
+}
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kThreads) lists_count_kernel(const LParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t nci = p.ncl ? p.cfirst[p.ncl] : 0u;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(p.in);
+    for (uint32_t e = gw; e < nci; e += nwarps) {
+        const uint32_t i = p.citem[e];
+        const Item it = p.items[i];
+        uint32_t c, s;
+        count_range<kDelta>(base + it.b0, base + it.b1, base + p.bo[it.list], base + p.bo[it.list + 1], lane, c, s);
+        if (lane == 0) p.cs[i] = make_uint2(c, s);
+    }
+}
+
+// One warp per chunked list: the count and sum of each chunk's earlier
+// chunks, and the list's count against its value offsets.
+__global__ void __launch_bounds__(kThreads) lists_scan_kernel(const LParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (uint32_t c = gw; c < p.ncl; c += nwarps) {
+        const uint32_t e0 = p.cfirst[c], e1 = p.cfirst[c + 1];
+        uint32_t cc = 0, cx = 0;
+        for (uint32_t b = e0; b < e1; b += kLanes) {
+            const uint32_t e = b + lane;
+            const uint2 v = e < e1 ? p.cs[p.citem[e]] : make_uint2(0u, 0u);
+            const uint32_t ic = warp_incl_scan(v.x, lane), is = warp_incl_scan(v.y, lane);
+            if (e < e1) p.rel[p.citem[e]] = make_uint2(cc + ic - v.x, cx + is - v.y);
+            cc += __shfl_sync(~0u, ic, 31);
+            cx += __shfl_sync(~0u, is, 31);
+        }
+        if (lane == 0) {
+            const uint32_t j = p.items[p.citem[e0]].list;
+            if (cc != p.vo[j + 1] - p.vo[j]) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+        }
+    }
+}
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kThreads, 5) lists_decode_kernel(const LParams p)
+{
+    extern __shared__ __align__(16) unsigned char lsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem &M = reinterpret_cast<WarpSmem *>(lsm)[warp];
+    if (lane < kRing) *reinterpret_cast<uint4 *>(M.ring[lane] + kHalo + kUnit) = make_uint4(0u, 0u, 0u, 0u);
+    const uintptr_t base = reinterpret_cast<uintptr_t>(p.in);
+    const uint32_t ow = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
+    (void)ow;
+    for (;;) {
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(p.queue, 1u);
+        i = __shfl_sync(~0u, i, 0);
+        if (i >= p.nitems) break;
+        const Item it = p.items[i];
+        const uint2 r = p.rel[i];
+        const uint32_t j = it.list;
+        unsigned long long R = p.vo[j] + r.x;
+        uint32_t X = (kDelta && p.prevs ? p.prevs[j] : 0u) + r.y;
+        const uintptr_t c0 = base + it.b0, c1 = base + it.b1;
+        const uintptr_t lo = base + p.bo[j], hi = base + p.bo[j + 1];
+        const uintptr_t a0 = c0 & ~static_cast<uintptr_t>(15);
+        const uint32_t K = c1 > c0 ? static_cast<uint32_t>((c1 - a0 + kUnit - 1) / kUnit) : 0u;
+        auto issue = [&](uint32_t k) {
+            if (k < K) {
+                const uintptr_t ua = a0 + static_cast<uintptr_t>(k) * kUnit;
+                stage_unit(ua, lane, M.ring[k % kRing], lo, hi, ua - 16 >= lo && ua + kUnit <= hi);
+            }
+            cp_async_commit();
+        };
+        issue(0);
+        issue(1);
+        for (uint32_t k = 0; k < K; ++k) {
+            cp_async_wait_prior<1>();
+            __syncwarp();
+            issue(k + 2);
+            const uint8_t *ub = M.ring[k % kRing];
+            const uintptr_t ua = a0 + static_cast<uintptr_t>(k) * kUnit;
+            const bool in = ua >= c0 && ua + kUnit <= c1 && ua - 16 >= lo;
+            uint32_t wc, ws;
+            bool one;
+            unit_stage<kDelta, true>(ub, in, ua, c0, c1, M.vals, lane, wc, ws, one, p.status,
+                                     (it.flags & kLast) ? hi : 0);
+            __syncwarp();
+            // the output's end: this list's last value (a count beyond it is an error)
+            Params q;
+            q.out = p.out;
+            q.n = p.vo[j + 1];
+            unit_emit<kDelta, false>(q, ub, M.vals, one, wc, R, X, lane);
+            R += wc;
+            X += ws;
+            __syncwarp();
+        }
+        cp_async_wait_all();
+        if (lane == 0 && (it.flags & kOnly) && R != p.vo[j + 1]) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+    }
+}
+
 // ---- host
+
+int lists_occupancy(int warps_per_cta)
+{
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lists_decode_kernel<true>, warps_per_cta * kLanes,
+                                                  warps_per_cta * sizeof(WarpSmem));
+    return occ > 0 ? occ : 1;
+}
 
 struct Layout {
     size_t ent, ctot, cpre, ent4, ctot4, cpre4, total;
@@ -772,6 +975,50 @@ size_t split_workspace_bytes(const uint8_t *in, size_t nbytes)
 {
     const uint64_t nwt = sp::wtiles_for(reinterpret_cast<uintptr_t>(in), nbytes);
     return sp::layout(nwt, sp::max_ranges(nwt), true).total;
+}
+
+int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta, uint32_t *status, cudaStream_t s)
+{
+    if (warps_per_cta != 4 && warps_per_cta != 8) return VBYTE_EINVAL;
+    sp::Dev di;
+    int rc = sp::dev_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    sp::LParams p = {};
+    p.in = a.in;
+    p.out = a.out;
+    p.bo = a.bo;
+    p.vo = a.vo;
+    p.prevs = a.delta ? a.prevs : nullptr;
+    p.items = lp.items;
+    p.nitems = lp.nitems;
+    p.citem = lp.citem;
+    p.cfirst = lp.cfirst;
+    p.ncl = lp.ncl;
+    p.cs = lp.cs;
+    p.rel = lp.rel;
+    p.queue = lp.queue;
+    p.status = status;
+    if (cudaMemsetAsync(lp.queue, 0, sizeof(unsigned int), s) != cudaSuccess) return VBYTE_ECUDA;
+    if (lp.ncl) {
+        const unsigned g = static_cast<unsigned>(std::max(1, di.sms * 4));
+        if (a.delta)
+            sp::lists_count_kernel<true><<<g, sp::kThreads, 0, s>>>(p);
+        else
+            sp::lists_count_kernel<false><<<g, sp::kThreads, 0, s>>>(p);
+        const unsigned gs = static_cast<unsigned>((lp.ncl + sp::kWarps - 1) / sp::kWarps);
+        sp::lists_scan_kernel<<<gs, sp::kThreads, 0, s>>>(p);
+    }
+    const int occ = sp::lists_occupancy(warps_per_cta);
+    const unsigned g = static_cast<unsigned>(std::min<uint64_t>(static_cast<uint64_t>(di.sms) * occ,
+                                                                (lp.nitems + warps_per_cta - 1) / warps_per_cta));
+    const size_t smem = warps_per_cta * sizeof(sp::WarpSmem);
+    if (g) {
+        if (a.delta)
+            sp::lists_decode_kernel<true><<<g, warps_per_cta * sp::kLanes, smem, s>>>(p);
+        else
+            sp::lists_decode_kernel<false><<<g, warps_per_cta * sp::kLanes, smem, s>>>(p);
+    }
+    return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
 size_t split_workspace_bound(size_t nbytes)

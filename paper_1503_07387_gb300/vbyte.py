@@ -68,6 +68,9 @@ def _signatures(lib):
         "vbyte_plan_get_status": ([P, P, P], I),
         "vbyte_plan_describe": ([P, P, P, P, P], I),
         "vbyte_plan_destroy": ([P], None),
+        "vbyte_plan_choice": ([P, P, P, P], I),
+        "vbyte_plan_class": ([P, I, P, P, P], I),
+        "vbyte_debug_force_plan": ([I, ctypes.c_uint64, I], I),
         "vbyte_decode_each": ([P, P, P, P, S, I, P, P], I),
         "vbyte_server_create": ([P, P, S, P, P, S, I, P, P], I),
         "vbyte_server_submit": ([P, P, S, P], I),
@@ -372,8 +375,27 @@ class Plan:
         c, sl, ms, tu = ctypes.c_int(0), ctypes.c_uint64(0), ctypes.c_float(0), ctypes.c_int(0)
         _check(load().vbyte_plan_describe(self._h, ctypes.byref(c), ctypes.byref(sl), ctypes.byref(ms),
                                           ctypes.byref(tu)), "vbyte_plan_describe")
-        return {"ctas_per_sm": c.value, "lead_slack_tiles": int(sl.value), "tuned_ms": round(ms.value, 5),
-                "tuned": {0: "defaults", 1: "timed", 2: "cached for the length class"}[tu.value]}
+        k, cb, tpb = ctypes.c_int(0), ctypes.c_uint64(0), ctypes.c_int(0)
+        _check(load().vbyte_plan_choice(self._h, ctypes.byref(k), ctypes.byref(cb), ctypes.byref(tpb)),
+               "vbyte_plan_choice")
+        classes = []
+        modes = {1: "single pass", 2: "count then decode", 3: "segmented stream"}
+        for kk in range(64):
+            nl, nv, md = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_int(0)
+            _check(load().vbyte_plan_class(self._h, kk, ctypes.byref(nl), ctypes.byref(nv), ctypes.byref(md)),
+                   "vbyte_plan_class")
+            if nl.value:
+                classes.append({"bytes_class": kk, "lists": int(nl.value), "values": int(nv.value),
+                                "mode": modes[md.value]})
+        out = {"kernel": {0: "segmented stream", 1: "list items"}[k.value],
+               "tuned_ms": round(ms.value, 5),
+               "tuned": {0: "defaults", 1: "timed", 2: "cached for the length class"}[tu.value],
+               "classes": classes}
+        if k.value == 1:
+            out.update(chunk_bytes=int(cb.value), threads_per_block=tpb.value)
+        else:
+            out.update(ctas_per_sm=c.value, lead_slack_tiles=int(sl.value))
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
@@ -588,6 +610,13 @@ def debug_force_passes(passes: int = 0):
     decode in one launch, 3 = split count / scan / decode, 0 = the library's
     choice."""
     _check(load().vbyte_debug_force_passes(int(passes)), "vbyte_debug_force_passes")
+
+
+def debug_force_plan(kernel: int = -1, chunk_bytes: int = 0, threads_per_block: int = 256):
+    """vbyte_debug_force_plan: make later plans use kernel 0 (segmented
+    stream) or 1 (list items of chunk_bytes); -1 restores the usual choice."""
+    _check(load().vbyte_debug_force_plan(int(kernel), int(chunk_bytes), int(threads_per_block)),
+           "vbyte_debug_force_plan")
 
 
 def chosen_passes(nbytes: int, n: int, delta: bool) -> int:
