@@ -226,7 +226,9 @@ int vbyte_decode_delta_batched(const uint8_t *d_in, size_t nbytes,
  *     to end decoded as one stream), with CTAs per SM and how far counting
  *     runs ahead of decoding.
  * With autotune != 0 every candidate (C in 8, 16, 32, 64 KiB x 128 or 256
- * threads per block, and the segmented kernel) is timed on this batch, or the
+ * threads per block; with 256 threads also the table-driven steps of Sec. 4
+ * in place of per-terminator assembly; and the segmented kernel) is timed on
+ * this batch, or the
  * choice made earlier for the same batch class (device, delta, log2 of mean
  * bytes per list, log2 of total bytes) is reused; otherwise list items with
  * C = 32 KiB and 256 threads per block (the segmented kernel if the offsets
@@ -250,7 +252,8 @@ int vbyte_plan_get_status(vbyte_plan *plan, void *stream, uint32_t *status_out);
  * time in ms, and tuned = 0 (defaults), 1 (timed now), 2 (from the cache). */
 int vbyte_plan_describe(const vbyte_plan *plan, int *ctas_per_sm,
                         uint64_t *lead_slack, float *tuned_ms, int *tuned);
-/* The chosen kernel: 0 = the segmented stream kernel, 1 = list items; for
+/* The chosen kernel: 0 = the segmented stream kernel, 1 = list items, 2 =
+ * list items decoded by the table-driven steps of Sec. 4 (vbyte_table); for
  * list items the chunk size C in bytes and the decode launch's threads per
  * block (0 and 256 for the segmented kernel). */
 int vbyte_plan_choice(const vbyte_plan *plan, int *kernel, uint64_t *chunk_bytes,
@@ -382,6 +385,29 @@ int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out,
 int vbyte_decode_noalloc(const uint8_t *d_in, size_t nbytes, uint32_t *d_out,
                          size_t n, int delta, uint32_t prev, uint32_t *d_status,
                          void *stream);
+
+/* ---- the table-driven step (Sec. 4) ------------------------------------ */
+
+/* The decoding table of Masked VByte (Sec. 4) as this library builds it, on
+ * the host and in each CTA's shared memory: h_entries[m] (4096 entries) for
+ * the 12-bit mask m of the high bits of the next 12 bytes (bit b: byte b) is
+ * the number of bytes consumed (bits 0..3; 0: an integer of more than five
+ * bytes, malformed) and the case (bits 4..11): 0..63, the next six integers
+ * take one or two bytes each; 64..144, else the next four take at most three
+ * bytes; 145..169, else the next two take at most five bytes; 255 for mask 0
+ * (twelve one-byte integers).  h_cases[i] (170 entries) describes case i:
+ * bits 0..2 the number of integers, bits 3+3t..5+3t the t-th length, bits
+ * 24..27 the bytes consumed.  Host memory only; returns VBYTE_EINVAL for a
+ * null pointer. */
+int vbyte_table(uint16_t *h_entries, uint32_t *h_cases);
+
+/* Decode a byte stream on the host by the table-driven steps (a table step
+ * per whole 12-byte window, then one integer at a time, as Sec. 4 falls back
+ * to the conventional decoder near the end); stores the first cap values in
+ * h_out and returns how many the stream holds.  It gives Algorithm 1's
+ * values; it exists to pin the table to them. */
+size_t vbyte_table_decode(const uint8_t *h_in, size_t nbytes, uint32_t *h_out,
+                          size_t cap);
 
 /* ---- status ---------------------------------------------------------- */
 

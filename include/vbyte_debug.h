@@ -39,20 +39,24 @@ int vbyte_debug_inject(long long skip_tile, uint64_t wait_limit_ns);
  * earlier tiles' published counts and sums), 2 = count then decode in one
  * launch (a count pass runs a fixed number of tiles ahead of the decode
  * pass), 3 = split (separate count, scan and decode launches; no CTA waits
- * on another), 0 = the library's choice (the default).  All give identical
+ * on another), 4 = split with the decode launch following the table-driven
+ * steps of Sec. 4 (vbyte_table) in place of per-terminator assembly (the
+ * gaps-minus-one variant keeps assembly), 0 = the library's choice (the
+ * default).  All give identical
  * results; this exists so that tests can check each and benchmarks can
  * compare them.  Returns VBYTE_OK, or VBYTE_EINVAL for another value. */
 int vbyte_debug_force_passes(int passes);
 
 /* The choice vbyte_plan_create makes from now on (process-wide), in place of
- * its defaults or its timing: kernel 0 (the segmented stream kernel) or 1
+ * its defaults or its timing: kernel 0 (the segmented stream kernel), 1
  * (list items of chunk_bytes, a multiple of 16 of at least 4096, with
- * threads_per_block 128 or 256); kernel -1 restores the usual choice.
+ * threads_per_block 128 or 256) or 2 (the same, decoding by the table-driven
+ * steps of Sec. 4); kernel -1 restores the usual choice.
  * Exists so that tests can check every candidate.  Returns VBYTE_OK, or
  * VBYTE_EINVAL for another value. */
 int vbyte_debug_force_plan(int kernel, uint64_t chunk_bytes, int threads_per_block);
 
-/* The kernel (1, 2 or 3, as above) that a single-stream call on an
+/* The kernel (1 to 4, as above) that a single-stream call on an
  * nbytes-byte input holding n values would use now. */
 int vbyte_debug_passes_for(size_t nbytes, size_t n, int delta);
 

@@ -477,7 +477,7 @@ size_t vbyte_workspace_size(size_t nbytes) { return vbk::workspace_bound(nbytes)
 
 int vbyte_debug_force_passes(int passes)
 {
-    if (passes < 0 || passes > 3) return VBYTE_EINVAL;
+    if (passes < 0 || passes > 4) return VBYTE_EINVAL;
     vbk::g_passes.store(passes);
     return VBYTE_OK;
 }

@@ -58,8 +58,8 @@ size_t workspace_bound(size_t nbytes);
 // only): the gaps-minus-one variant, every value plus its rank.
 // passes: 2 = count-then-decode (the workspace layout of
 // stream_workspace_bytes), 1 = single pass with a decoupled look-back, 3 = the
-// split count / scan / decode launches (1 and 3 need
-// stream_workspace_bytes_any).
+// split count / scan / decode launches, 4 = the split launches decoding by the
+// table-driven steps of Sec. 4 (1, 3 and 4 need stream_workspace_bytes_any).
 int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
                    uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank = false, int passes = 2);
 // Workspace bytes for a single-stream call with any of the kernels.
@@ -71,8 +71,11 @@ size_t split_workspace_bytes(const uint8_t *in, size_t nbytes);
 size_t split_workspace_bound(size_t nbytes);
 // prev4 (host, four values): the blocked-difference form (delta and rank
 // false), x_i = g_i + x_{i-4} with x_{-4..-1} = prev4[0..3].
+// table: decode by the table-driven steps of Sec. 4 (vbyte_table.cuh) in
+// place of per-terminator assembly.
 int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank, const uint32_t *prev4 = nullptr);
+                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank, const uint32_t *prev4 = nullptr,
+                  bool table = false);
 // The kernel vbyte_decode* use for an input of nbytes holding n values:
 // 1 (single pass), 2 (count-then-decode) or 3 (split).
 int choose_passes(size_t nbytes, size_t n, bool delta);
@@ -121,7 +124,9 @@ struct ListPlan {
     uint2 *rel;          // per item: count and sum of its list's earlier chunks (zeros at creation)
     unsigned int *queue;
 };
-int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta, uint32_t *status, cudaStream_t s);
+// table: the items' units decoded by the table-driven steps of Sec. 4.
+int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta, uint32_t *status, cudaStream_t s,
+                      bool table = false);
 
 // A piece of a gather: len bytes from src + src_off to dst + dst_off.
 struct GatherPiece {

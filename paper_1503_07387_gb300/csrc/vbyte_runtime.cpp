@@ -20,6 +20,7 @@ struct vbyte_plan {
     vbk::LaunchCfg cfg{};        // kernel 0: CTAs per SM and count-ahead slack
     uint64_t chunk = 0;          // kernel 1: lists of up to `chunk` bytes decoded whole, longer ones in chunks
     int warps = 8;               // kernel 1: warps per CTA of the decode launch
+    bool table = false;          // kernel 1: units decoded by the table-driven steps of Sec. 4
     uint8_t *ws = nullptr;       // status word, and kernel 0's workspace
     void *lp_mem = nullptr;      // kernel 1's device arrays
     vbk::ListPlan lp{};
@@ -40,6 +41,7 @@ struct Choice {
     vbk::LaunchCfg cfg;
     uint64_t chunk;
     int warps;
+    bool table;
     float ms;
 };
 using ClassKey = std::tuple<int, int, int, int>;   // device, delta, log2 mean, log2 total
@@ -152,7 +154,8 @@ int upload_items(const HostItems &h, void **mem, vbk::ListPlan *lp, cudaStream_t
 
 int enqueue_plan(const vbyte_plan &P, cudaStream_t s)
 {
-    if (P.kernel == 1) return vbk::enqueue_list_plan(P.a, P.lp, P.warps, reinterpret_cast<uint32_t *>(P.ws), s);
+    if (P.kernel == 1)
+        return vbk::enqueue_list_plan(P.a, P.lp, P.warps, reinterpret_cast<uint32_t *>(P.ws), s, P.table);
     return vbk::enqueue_sbatched(P.a, P.ws, P.cfg, s);
 }
 
@@ -208,6 +211,7 @@ std::mutex g_force_mu;
 int g_force_kernel = -1;
 uint64_t g_force_chunk = 0;
 int g_force_warps = 8;
+bool g_force_table = false;
 
 }  // namespace
 
@@ -271,6 +275,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
             P->kernel = g_force_kernel;
             P->chunk = g_force_chunk;
             P->warps = g_force_warps;
+            P->table = g_force_table;
         }
     }
 
@@ -285,13 +290,14 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
                 P->cfg = it->second.cfg;
                 P->chunk = it->second.chunk;
                 P->warps = it->second.warps;
+                P->table = it->second.table;
                 P->tuned_ms = it->second.ms;
                 P->tuned = 2;
                 cached = true;
             }
         }
         if (!cached) {
-            Choice best{0, vbk::LaunchCfg(), 0, 8, 0.f};
+            Choice best{0, vbk::LaunchCfg(), 0, 8, false, 0.f};
             bool have = false;
             auto consider = [&](const Choice &c, float ms) {
                 if (!have || ms < best.ms) {
@@ -308,7 +314,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
                 P->cfg.lead_slack = sl;
                 float ms = 0.f;
                 if ((rc = time_plan(*P, s, 3, &ms)) != VBYTE_OK) return fail(rc);
-                consider(Choice{0, P->cfg, 0, 8, 0.f}, ms);
+                consider(Choice{0, P->cfg, 0, 8, false, 0.f}, ms);
             }
             // list items: chunk size (which length classes are decoded whole
             // in one pass and which by count-then-decode) x warps per CTA
@@ -316,12 +322,17 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
                 for (uint64_t C : kChunks) {
                     if ((rc = set_items(P, bo, C, s)) != VBYTE_OK) return fail(rc);
                     for (int w : kWarpChoices) {
-                        P->kernel = 1;
-                        P->chunk = C;
-                        P->warps = w;
-                        float ms = 0.f;
-                        if ((rc = time_plan(*P, s, 3, &ms)) != VBYTE_OK) return fail(rc);
-                        consider(Choice{1, vbk::LaunchCfg(), C, w, 0.f}, ms);
+                        // units by per-terminator assembly, and (256 threads)
+                        // by the table-driven steps of Sec. 4
+                        for (int tb = 0; tb < (w == 8 ? 2 : 1); ++tb) {
+                            P->kernel = 1;
+                            P->chunk = C;
+                            P->warps = w;
+                            P->table = tb != 0;
+                            float ms = 0.f;
+                            if ((rc = time_plan(*P, s, 3, &ms)) != VBYTE_OK) return fail(rc);
+                            consider(Choice{1, vbk::LaunchCfg(), C, w, tb != 0, 0.f}, ms);
+                        }
                     }
                 }
             }
@@ -329,6 +340,7 @@ int vbyte_plan_create(vbyte_plan **plan_out, const uint8_t *d_in, size_t nbytes,
             P->cfg = best.cfg;
             P->chunk = best.chunk;
             P->warps = best.warps;
+            P->table = best.table;
             P->tuned_ms = best.ms;
             P->tuned = 1;
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -388,11 +400,12 @@ int vbyte_plan_describe(const vbyte_plan *plan, int *ctas_per_sm, uint64_t *lead
 
 int vbyte_debug_force_plan(int kernel, uint64_t chunk_bytes, int threads_per_block)
 {
-    if (kernel < -1 || kernel > 1) return VBYTE_EINVAL;
-    if (kernel == 1 && (chunk_bytes < 4096 || chunk_bytes % 16 || (threads_per_block != 128 && threads_per_block != 256)))
+    if (kernel < -1 || kernel > 2) return VBYTE_EINVAL;
+    if (kernel >= 1 && (chunk_bytes < 4096 || chunk_bytes % 16 || (threads_per_block != 128 && threads_per_block != 256)))
         return VBYTE_EINVAL;
     std::lock_guard<std::mutex> lk(g_force_mu);
-    g_force_kernel = kernel;
+    g_force_table = kernel == 2;
+    g_force_kernel = kernel == 2 ? 1 : kernel;
     g_force_chunk = chunk_bytes;
     g_force_warps = threads_per_block / 32;
     return VBYTE_OK;
@@ -401,7 +414,7 @@ int vbyte_debug_force_plan(int kernel, uint64_t chunk_bytes, int threads_per_blo
 int vbyte_plan_choice(const vbyte_plan *plan, int *kernel, uint64_t *chunk_bytes, int *threads_per_block)
 {
     if (!plan) return VBYTE_EINVAL;
-    if (kernel) *kernel = plan->kernel;
+    if (kernel) *kernel = plan->kernel == 1 && plan->table ? 2 : plan->kernel;
     if (chunk_bytes) *chunk_bytes = plan->kernel == 1 ? plan->chunk : 0;
     if (threads_per_block) *threads_per_block = plan->kernel == 1 ? plan->warps * 32 : 256;
     return VBYTE_OK;

@@ -39,6 +39,7 @@
 #include "vbyte_device.cuh"
 #include "vbyte_emit.cuh"
 #include "vbyte_internal.h"
+#include "vbyte_table.cuh"
 
 namespace vbk {
 namespace sp {
@@ -489,10 +490,66 @@ __device__ __forceinline__ void issue_unit(const Params &p, uint64_t t, int u, i
 // integers only (the values stay as bytes and vals is untouched).  kCheck:
 // also record runs of five continuation bytes and (dend != 0) a stream that
 // ends at dend inside an integer.
-template <bool kDelta, bool kCheck = false>
+// The table-driven step (Sec. 4) for one lane: from the first byte of its
+// first integer, the high-bit mask of the next 12 bytes picks (bytes
+// consumed, case) from T; the case's lengths D give its integers; those whose
+// terminators lie in the lane's slice and in tc are emitted in order.  An
+// entry with nothing consumed (an integer of more than five bytes) hands the
+// rest of the slice to per-terminator assembly.
+template <typename F>
+__device__ __forceinline__ void table_steps(const uint32_t *sw, int lane, const SliceMasks &m, const uint16_t *T,
+                                            const uint32_t *D, F emit)
+{
+    const uint32_t q0 = kHalo + lane * kBPT;
+    const uint32_t n0 = sw[q0 / 4 + 4], n1 = sw[q0 / 4 + 5], n2 = sw[q0 / 4 + 6];   // the 12 bytes after the slice
+    // bit b: byte b - 4 of the slice has its high bit set
+    const uint32_t cont =
+        ~(term4(m.wprev) | (m.tl << 4) | (term4(n0) << 20) | (term4(n1) << 24) | (term4(n2) << 28));
+    if (!m.tl) return;
+    const uint32_t low = m.t20 & 0xFu;
+    uint32_t b = low ? 32u - __clz(low) : 0u;   // first byte of the first integer
+    const uint32_t endb = 31u - __clz(m.tl) + 4u;   // the slice's last terminator
+    while (b <= endb) {
+        const uint32_t e = T[(cont >> b) & 0xFFFu];
+        const uint32_t c = e & 15u, id = e >> 4;
+        if (!c) {   // malformed: the remaining terminators one by one
+            const uint32_t keep = b >= 4 ? ~((1u << (b - 4)) - 1u) : ~0u;
+            assemble_all(sw, lane, m.tl, m.t20, m.tc & keep, emit);
+            return;
+        }
+        if (id == tab::kTwelve) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const int t = static_cast<int>(b) + i - 4;   // slice position of the one-byte integer
+                if (t >= 0 && t < kBPT && ((m.tc >> t) & 1u)) {
+                    const uint32_t q = q0 + t;
+                    emit((sw[q >> 2] >> (8 * (q & 3))) & 0xFFu);
+                }
+            }
+        } else {
+            const uint32_t d = D[id];
+            uint32_t o = b;
+            for (uint32_t t = 0; t < tab::case_k(d); ++t) {
+                const uint32_t L = tab::case_len(d, static_cast<int>(t));
+                const int tp = static_cast<int>(o + L) - 5;   // slice position of the terminator
+                if (tp >= 0 && tp < kBPT && ((m.tc >> tp) & 1u)) {
+                    const uint32_t q = q0 + tp;
+                    const uint32_t A = sw[(q >> 2) - 1];
+                    const uint32_t B = sw[q >> 2];
+                    emit(assemble(__funnelshift_r(A, B, 8 * q), prmt(B, 0u, 0x4440u | (q & 3u)), static_cast<int>(L)));
+                }
+                o += L;
+            }
+        }
+        b += c;
+    }
+}
+
+template <bool kDelta, bool kCheck = false, bool kTable = false>
 __device__ __forceinline__ void unit_stage(const uint8_t *ub, bool in, uintptr_t ua, uintptr_t lo, uintptr_t hi,
                                            uint32_t *vals, int lane, uint32_t &wc, uint32_t &ws, bool &one,
-                                           uint32_t *status = nullptr, uintptr_t dend = 0)
+                                           uint32_t *status = nullptr, uintptr_t dend = 0,
+                                           const uint16_t *T = nullptr, const uint32_t *D = nullptr)
 {
     const uint4 w0 = *reinterpret_cast<const uint4 *>(ub + kHalo + lane * kBPT);
     const uint32_t wp0 = reinterpret_cast<const uint32_t *>(ub)[(kHalo + lane * kBPT) / 4 - 1];
@@ -520,7 +577,23 @@ __device__ __forceinline__ void unit_stage(const uint8_t *ub, bool in, uintptr_t
     wc = __shfl_sync(~0u, inc, 31);
     uint32_t *dst = vals + 4 + inc - cnt;
     uint32_t vsum = 0;
-    if (!__any_sync(~0u, notB)) {
+    if (kTable) {
+        // the table-driven steps for every code length, then running sums
+        table_steps(sw, lane, m, T, D, [&](uint32_t v) {
+            *dst++ = v;
+            vsum += v;
+        });
+        dst -= cnt;
+        if (kDelta) {
+            const uint32_t incs = warp_incl_scan(vsum, lane);
+            ws = __shfl_sync(~0u, incs, 31);
+            uint32_t run = incs - vsum;
+            for (uint32_t i = 0; i < cnt; ++i) {
+                run += dst[i];
+                dst[i] = run;
+            }
+        }
+    } else if (!__any_sync(~0u, notB)) {
         // codes of at most two bytes: the lane's sum by the byte-weight
         // formula, then the values (with running sums) in one SWAR pass
         uint32_t run = 0;
@@ -662,12 +735,30 @@ __device__ __forceinline__ uint4 class_scan(uint32_t *vals, uint32_t wc, int lan
     return carry;
 }
 
-template <bool kDelta, bool kRank, bool kD4 = false>
+// The table and case descriptors of the table-driven step, built by the CTA.
+struct TableSmem {
+    uint16_t T[4096];
+    uint32_t D[tab::kCases];
+};
+
+__device__ __forceinline__ void fill_table(TableSmem &S)
+{
+    for (uint32_t i = threadIdx.x; i < 4096; i += blockDim.x) S.T[i] = static_cast<uint16_t>(tab::table_entry(i));
+    for (uint32_t i = threadIdx.x; i < static_cast<uint32_t>(tab::kCases); i += blockDim.x) S.D[i] = tab::case_desc(i);
+}
+
+template <bool kDelta, bool kRank, bool kD4 = false, bool kTable = false>
 __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
 {
     __shared__ WarpSmem Wsm[kWarps];
+    extern __shared__ __align__(16) unsigned char dsm[];   // kTable: the table (dynamic shared memory)
+    TableSmem &Tab = *reinterpret_cast<TableSmem *>(dsm);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     WarpSmem &M = Wsm[warp];
+    if (kTable) {
+        fill_table(Tab);
+        __syncthreads();
+    }
     if (lane < kRing) *reinterpret_cast<uint4 *>(M.ring[lane] + kHalo + kUnit) = make_uint4(0u, 0u, 0u, 0u);
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
@@ -707,7 +798,8 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
         const uintptr_t ua = p.base + (static_cast<uintptr_t>(t) << 11) + u * kUnit;
         uint32_t wc, ws;
         bool one;
-        unit_stage<kDelta>(ub, interior(p, t), ua, lo, hi, M.vals, lane, wc, ws, one);
+        unit_stage<kDelta, false, kTable>(ub, interior(p, t), ua, lo, hi, M.vals, lane, wc, ws, one, nullptr, 0,
+                                          Tab.T, Tab.D);
         __syncwarp();
         if (kD4) {
             if (one) {   // one-byte integers: the bytes become the staged values
@@ -853,12 +945,17 @@ __global__ void __launch_bounds__(kThreads) lists_scan_kernel(const LParams p)
     }
 }
 
-template <bool kDelta>
+template <bool kDelta, bool kTable = false>
 __global__ void __launch_bounds__(kThreads, 5) lists_decode_kernel(const LParams p)
 {
     extern __shared__ __align__(16) unsigned char lsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem &M = reinterpret_cast<WarpSmem *>(lsm)[warp];
+    TableSmem &Tb = *reinterpret_cast<TableSmem *>(lsm + (blockDim.x >> 5) * sizeof(WarpSmem));
+    if (kTable) {
+        fill_table(Tb);
+        __syncthreads();
+    }
     if (lane < kRing) *reinterpret_cast<uint4 *>(M.ring[lane] + kHalo + kUnit) = make_uint4(0u, 0u, 0u, 0u);
     const uintptr_t base = reinterpret_cast<uintptr_t>(p.in);
     const uint32_t ow = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
@@ -895,8 +992,8 @@ __global__ void __launch_bounds__(kThreads, 5) lists_decode_kernel(const LParams
             const bool in = ua >= c0 && ua + kUnit <= c1 && ua - 16 >= lo;
             uint32_t wc, ws;
             bool one;
-            unit_stage<kDelta, true>(ub, in, ua, c0, c1, M.vals, lane, wc, ws, one, p.status,
-                                     (it.flags & kLast) ? hi : 0);
+            unit_stage<kDelta, true, kTable>(ub, in, ua, c0, c1, M.vals, lane, wc, ws, one, p.status,
+                                             (it.flags & kLast) ? hi : 0, Tb.T, Tb.D);
             __syncwarp();
             // the output's end: this list's last value (a count beyond it is an error)
             Params q;
@@ -914,11 +1011,20 @@ __global__ void __launch_bounds__(kThreads, 5) lists_decode_kernel(const LParams
 
 // ---- host
 
-int lists_occupancy(int warps_per_cta)
+size_t lists_smem(int warps_per_cta, bool table)
+{
+    return warps_per_cta * sizeof(WarpSmem) + (table ? sizeof(TableSmem) : 0);
+}
+
+int lists_occupancy(int warps_per_cta, bool table)
 {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lists_decode_kernel<true>, warps_per_cta * kLanes,
-                                                  warps_per_cta * sizeof(WarpSmem));
+    if (table)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lists_decode_kernel<true, true>, warps_per_cta * kLanes,
+                                                      lists_smem(warps_per_cta, true));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lists_decode_kernel<true>, warps_per_cta * kLanes,
+                                                      lists_smem(warps_per_cta, false));
     return occ > 0 ? occ : 1;
 }
 
@@ -977,7 +1083,8 @@ size_t split_workspace_bytes(const uint8_t *in, size_t nbytes)
     return sp::layout(nwt, sp::max_ranges(nwt), true).total;
 }
 
-int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta, uint32_t *status, cudaStream_t s)
+int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta, uint32_t *status, cudaStream_t s,
+                      bool table)
 {
     if (warps_per_cta != 4 && warps_per_cta != 8) return VBYTE_EINVAL;
     sp::Dev di;
@@ -1008,15 +1115,20 @@ int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta,
         const unsigned gs = static_cast<unsigned>((lp.ncl + sp::kWarps - 1) / sp::kWarps);
         sp::lists_scan_kernel<<<gs, sp::kThreads, 0, s>>>(p);
     }
-    const int occ = sp::lists_occupancy(warps_per_cta);
+    const int occ = sp::lists_occupancy(warps_per_cta, table);
     const unsigned g = static_cast<unsigned>(std::min<uint64_t>(static_cast<uint64_t>(di.sms) * occ,
                                                                 (lp.nitems + warps_per_cta - 1) / warps_per_cta));
-    const size_t smem = warps_per_cta * sizeof(sp::WarpSmem);
+    const size_t smem = sp::lists_smem(warps_per_cta, table);
+    const unsigned nt = static_cast<unsigned>(warps_per_cta * sp::kLanes);
     if (g) {
-        if (a.delta)
-            sp::lists_decode_kernel<true><<<g, warps_per_cta * sp::kLanes, smem, s>>>(p);
+        if (table && a.delta)
+            sp::lists_decode_kernel<true, true><<<g, nt, smem, s>>>(p);
+        else if (table)
+            sp::lists_decode_kernel<false, true><<<g, nt, smem, s>>>(p);
+        else if (a.delta)
+            sp::lists_decode_kernel<true><<<g, nt, smem, s>>>(p);
         else
-            sp::lists_decode_kernel<false><<<g, warps_per_cta * sp::kLanes, smem, s>>>(p);
+            sp::lists_decode_kernel<false><<<g, nt, smem, s>>>(p);
     }
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
@@ -1028,7 +1140,7 @@ size_t split_workspace_bound(size_t nbytes)
 }
 
 int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bool delta, uint32_t prev,
-                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank, const uint32_t *prev4)
+                  uint8_t *ws, uint32_t *status, cudaStream_t s, bool rank, const uint32_t *prev4, bool table)
 {
     if (rank && !delta) return VBYTE_EINVAL;
     const bool d4 = prev4 != nullptr;
@@ -1078,12 +1190,17 @@ int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     else
         sp::count_kernel<false, false><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
     sp::scan_kernel<<<1, sp::kScanThreads, 0, s>>>(p);
+    const unsigned g = static_cast<unsigned>(G);
     if (rank)
-        sp::decode_kernel<true, true><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
+        sp::decode_kernel<true, true><<<g, sp::kThreads, 0, s>>>(p);
+    else if (table && delta)
+        sp::decode_kernel<true, false, false, true><<<g, sp::kThreads, sizeof(sp::TableSmem), s>>>(p);
+    else if (table)
+        sp::decode_kernel<false, false, false, true><<<g, sp::kThreads, sizeof(sp::TableSmem), s>>>(p);
     else if (delta)
-        sp::decode_kernel<true, false><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
+        sp::decode_kernel<true, false><<<g, sp::kThreads, 0, s>>>(p);
     else
-        sp::decode_kernel<false, false><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
+        sp::decode_kernel<false, false><<<g, sp::kThreads, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 

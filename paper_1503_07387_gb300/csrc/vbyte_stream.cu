@@ -1291,6 +1291,7 @@ int enqueue_stream(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, bo
     if (rank && !delta) return VBYTE_EINVAL;
     if (passes == 1) return enqueue_onepass(in, nbytes, out, n, delta, prev, ws, status, s, rank);
     if (passes == 3) return enqueue_split(in, nbytes, out, n, delta, prev, ws, status, s, rank);
+    if (passes == 4) return enqueue_split(in, nbytes, out, n, delta, prev, ws, status, s, rank, nullptr, !rank);
     const uintptr_t a = reinterpret_cast<uintptr_t>(in);
     const uint64_t ntiles = sd::tiles_for(a, nbytes);
     const sd::Layout L = sd::layout(ntiles);

@@ -71,6 +71,8 @@ def _signatures(lib):
         "vbyte_plan_choice": ([P, P, P, P], I),
         "vbyte_plan_class": ([P, I, P, P, P], I),
         "vbyte_debug_force_plan": ([I, ctypes.c_uint64, I], I),
+        "vbyte_table": ([P, P], I),
+        "vbyte_table_decode": ([P, S, P, S], S),
         "vbyte_decode_each": ([P, P, P, P, S, I, P, P], I),
         "vbyte_server_create": ([P, P, S, P, P, S, I, P, P], I),
         "vbyte_server_submit": ([P, P, S, P], I),
@@ -387,11 +389,11 @@ class Plan:
             if nl.value:
                 classes.append({"bytes_class": kk, "lists": int(nl.value), "values": int(nv.value),
                                 "mode": modes[md.value]})
-        out = {"kernel": {0: "segmented stream", 1: "list items"}[k.value],
+        out = {"kernel": {0: "segmented stream", 1: "list items", 2: "list items, table-driven"}[k.value],
                "tuned_ms": round(ms.value, 5),
                "tuned": {0: "defaults", 1: "timed", 2: "cached for the length class"}[tu.value],
                "classes": classes}
-        if k.value == 1:
+        if k.value in (1, 2):
             out.update(chunk_bytes=int(cb.value), threads_per_block=tpb.value)
         else:
             out.update(ctas_per_sm=c.value, lead_slack_tiles=int(sl.value))
@@ -607,16 +609,38 @@ def debug_inject(skip_tile: int = -1, wait_limit_ns: int = 0):
 
 def debug_force_passes(passes: int = 0):
     """vbyte_debug_force_passes: 1 = single-pass kernel, 2 = count then
-    decode in one launch, 3 = split count / scan / decode, 0 = the library's
-    choice."""
+    decode in one launch, 3 = split count / scan / decode, 4 = split with the
+    table-driven steps of Sec. 4, 0 = the library's choice."""
     _check(load().vbyte_debug_force_passes(int(passes)), "vbyte_debug_force_passes")
 
 
 def debug_force_plan(kernel: int = -1, chunk_bytes: int = 0, threads_per_block: int = 256):
     """vbyte_debug_force_plan: make later plans use kernel 0 (segmented
-    stream) or 1 (list items of chunk_bytes); -1 restores the usual choice."""
+    stream), 1 (list items of chunk_bytes) or 2 (list items, table-driven
+    steps); -1 restores the usual choice."""
     _check(load().vbyte_debug_force_plan(int(kernel), int(chunk_bytes), int(threads_per_block)),
            "vbyte_debug_force_plan")
+
+
+def table():
+    """The table-driven step's table (Sec. 4): (entries uint16[4096], cases
+    uint32[170]) as vbyte_table documents them."""
+    e = np.zeros(4096, dtype=np.uint16)
+    c = np.zeros(170, dtype=np.uint32)
+    _check(load().vbyte_table(_np_ptr(e), _np_ptr(c)), "vbyte_table")
+    return e, c
+
+
+def table_decode(data, n=None) -> np.ndarray:
+    """Host decoding by the table-driven steps (vbyte_table_decode)."""
+    b = np.ascontiguousarray(data, dtype=np.uint8)
+    cap = b.size if n is None else n
+    out = np.empty(max(cap, 1), dtype=np.uint32)
+    cnt = load().vbyte_table_decode(_np_ptr(b), b.size, _np_ptr(out), cap)
+    if cnt > cap:
+        out = np.empty(cnt, dtype=np.uint32)
+        cnt = load().vbyte_table_decode(_np_ptr(b), b.size, _np_ptr(out), cnt)
+    return out[:cnt].copy()
 
 
 def chosen_passes(nbytes: int, n: int, delta: bool) -> int:

@@ -182,7 +182,7 @@ def test_kernel_choice_by_length_class():
     finally:
         vbyte.debug_force_passes(0)
     with pytest.raises(vbyte.VByteError):
-        vbyte.debug_force_passes(4)
+        vbyte.debug_force_passes(5)
 
 
 def test_host_encoder_delta4_matches_oracle():

@@ -14,10 +14,17 @@ pytestmark = pytest.mark.gpu
 
 SENTINEL = 0xA5A5A5A5
 GUARD = 37
-CHOICES = [(1, 4096, 128), (1, 8 << 10, 256), (1, 32 << 10, 128), (1, 128 << 10, 256), (0, 0, 256)]
+CHOICES = [(1, 4096, 128), (1, 8 << 10, 256), (1, 32 << 10, 128), (1, 128 << 10, 256), (0, 0, 256),
+           (2, 16 << 10, 256), (2, 4096, 128)]
 
 
-@pytest.fixture(params=CHOICES, ids=lambda c: "segmented" if c[0] == 0 else f"items{c[1] >> 10}k_t{c[2]}")
+def _cid(c):
+    if c[0] == 0:
+        return "segmented"
+    return f"{'table' if c[0] == 2 else 'items'}{c[1] >> 10}k_t{c[2]}"
+
+
+@pytest.fixture(params=CHOICES, ids=_cid)
 def choice(request):
     vbyte.debug_force_plan(*request.param)
     yield request.param
@@ -125,8 +132,9 @@ def test_describe_reports_a_mode_per_class(choice):
         else:
             whole = (2 << c["bytes_class"]) - 1 <= chunk
             assert c["mode"] == ("single pass" if whole else "count then decode")
-    if kernel == 1:
+    if kernel >= 1:
         assert info["chunk_bytes"] == chunk and info["threads_per_block"] == tpb
+        assert info["kernel"] == ("list items, table-driven" if kernel == 2 else "list items")
 
 
 @pytest.mark.slow
