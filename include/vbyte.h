@@ -286,14 +286,16 @@ int vbyte_decode_each(const uint8_t *d_in, const uint64_t *h_byte_off,
  * current device and decodes queries, each naming up to max_batch_lists of
  * its lists, as they arrive.  A scheduler thread admits waiting queries in
  * arrival order into a batch as long as the batch's decoded output fits in
- * the free part of a device arena (arena_bytes), its compressed lists fit
- * the staging buffer (staging_bytes) and the batch limits hold; up to
- * max_inflight batches run at once, each on its own stream, so queries that
- * arrive while others are on the GPU start as soon as a slot and arena
- * space free up.  A batch's lists are gathered end to end on the device and
- * decoded with one batched launch (per_list = 0), or each list is decoded
- * with its own vbyte_decode / vbyte_decode_delta call (per_list = 1, the
- * comparison form).  A query's values (the concatenation of its lists'
+ * the free part of a device arena (arena_bytes), its compressed lists take
+ * at most staging_bytes and the batch limits hold; up to max_inflight
+ * batches run at once, each on its own stream, so queries that arrive while
+ * others are on the GPU start as soon as a slot and arena space free up.
+ * per_list = 0: a batch is decoded in place with one set of launches -- its
+ * lists become work items (a whole list, or a 32 KiB chunk of a long one)
+ * that warps decode straight from the pool into the arena; per_list = 1 (a
+ * comparison form): each list with its own vbyte_decode / vbyte_decode_delta
+ * call; per_list = 2 (another): the lists gathered end to end into a staging
+ * buffer of staging_bytes, then one segmented batched launch.  A query's values (the concatenation of its lists'
  * values, in the order named) stay in the arena until it is released.  All
  * device memory is allocated at creation.  The pool and its offsets must
  * not change while the server lives. */
@@ -304,7 +306,7 @@ typedef struct vbyte_server_config {
     int max_inflight;        /* batches on the GPU at once */
     int max_batch_queries;   /* queries per batch */
     int max_batch_lists;     /* lists per batch (and per query) */
-    int per_list;            /* 1: one single-stream call per list */
+    int per_list;            /* 0 in place, 1 one call per list, 2 gather then batched */
 } vbyte_server_config;
 int vbyte_server_create(vbyte_server **srv, const uint8_t *d_pool,
                         size_t pool_bytes, const uint64_t *h_byte_off,

@@ -3,9 +3,12 @@
 // scheduler thread admits them in arrival order, as far as the device arena
 // has room for their decoded output, into batches that run on several
 // streams at once (continuous batching), and records each query's
-// completion time.  A batch's lists are gathered end to end into a staging
-// buffer and decoded with one batched launch; the comparison form decodes
-// every list with its own single-stream call.
+// completion time.  A batch is decoded in place: its lists become work items
+// (a whole list, or a chunk of a long one) that warps decode straight from
+// the pool into the query's arena space (the list-item kernels of batched
+// plans).  Comparison forms: every list with its own single-stream call, and
+// the lists gathered end to end into a staging buffer and decoded with one
+// segmented batched launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +33,8 @@ double now_s() { return std::chrono::duration<double>(Clock::now().time_since_ep
 
 constexpr uint64_t kArenaUnit = 256;                 // arena allocation granule (bytes)
 constexpr uint32_t kPieceBytes = 64u << 10;          // gather piece size
+constexpr uint64_t kItemBytes = 32u << 10;           // in-place form: lists of more bytes are cut into chunks
+constexpr int kItemWarps = 8;                        // in-place form: warps per CTA of the decode launch
 
 struct Query {
     std::vector<uint32_t> lists;
@@ -135,12 +140,119 @@ struct vbyte_server {
         }
     }
 
+    // ---- in place: the batch's lists as work items over the pool.  Virtual
+    // list v (its batch position) has entries 2v and 2v + 1 in the batch's
+    // offset arrays: its pool bytes, its output ranks within the batch's
+    // arena block, and x_0 -- the layout the list-item kernels read.
+    int launch_items(Slot &sl, uint32_t *out)
+    {
+        const size_t nl = sl.lists.size();
+        std::vector<vbk::ListItem> raw;
+        std::vector<std::pair<size_t, size_t>> chunked;
+        raw.reserve(2 * nl);
+        const uintptr_t in = reinterpret_cast<uintptr_t>(d_pool);
+        for (size_t v = 0; v < nl; ++v) {
+            const uint32_t j = sl.lists[v];
+            const uint64_t b0 = bo[j], b1 = bo[j + 1];
+            const uint32_t lv = static_cast<uint32_t>(2 * v);
+            if (b1 - b0 <= kItemBytes) {
+                raw.push_back({b0, b1, lv, vbk::kItemOnly | vbk::kItemLast});
+                continue;
+            }
+            const size_t first = raw.size();
+            const uint64_t a = ((in + b0) & ~static_cast<uint64_t>(15)) - in;
+            uint64_t st = b0;
+            for (uint64_t k = 1;; ++k) {
+                const uint64_t e = a + k * kItemBytes;
+                if (e >= b1) {
+                    raw.push_back({st, b1, lv, vbk::kItemLast});
+                    break;
+                }
+                raw.push_back({st, e, lv, 0u});
+                st = e;
+            }
+            chunked.emplace_back(first, raw.size() - first);
+        }
+        // decode order: longest first
+        std::vector<uint32_t> order(raw.size()), pos(raw.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<uint32_t>(i);
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+            return raw[x].b1 - raw[x].b0 > raw[y].b1 - raw[y].b0;
+        });
+        const size_t ni = raw.size();
+        size_t nci = 0;
+        for (const auto &c : chunked) nci += c.second;
+        const size_t ncl = chunked.size();
+        auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+        const size_t o_items = 0, o_citem = up16(ni * sizeof(vbk::ListItem)), o_cfirst = up16(o_citem + nci * 4);
+        const size_t o_bo = up16(o_cfirst + (ncl + 1) * 4), o_vo = o_bo + 16 * nl, o_pv = o_vo + 16 * nl;
+        const size_t o_rel = up16(o_pv + 8 * nl), upload = o_rel + 8 * ni;
+        const size_t o_cs = up16(upload), o_q = up16(o_cs + 8 * ni), total = o_q + 16;
+        if (total > sl.desc_bytes) return VBYTE_EINVAL;
+        vbk::ListItem *hi = reinterpret_cast<vbk::ListItem *>(sl.h_desc + o_items);
+        for (size_t i = 0; i < ni; ++i) {
+            hi[i] = raw[order[i]];
+            pos[order[i]] = static_cast<uint32_t>(i);
+        }
+        uint32_t *hci = reinterpret_cast<uint32_t *>(sl.h_desc + o_citem);
+        uint32_t *hcf = reinterpret_cast<uint32_t *>(sl.h_desc + o_cfirst);
+        size_t e = 0;
+        for (size_t c = 0; c < ncl; ++c) {
+            hcf[c] = static_cast<uint32_t>(e);
+            for (size_t r = chunked[c].first; r < chunked[c].first + chunked[c].second; ++r) hci[e++] = pos[r];
+        }
+        hcf[ncl] = static_cast<uint32_t>(e);
+        uint64_t *hbo = reinterpret_cast<uint64_t *>(sl.h_desc + o_bo);
+        uint64_t *hvo = reinterpret_cast<uint64_t *>(sl.h_desc + o_vo);
+        uint32_t *hpv = reinterpret_cast<uint32_t *>(sl.h_desc + o_pv);
+        uint64_t o = 0;
+        for (size_t v = 0; v < nl; ++v) {
+            const uint32_t j = sl.lists[v];
+            hbo[2 * v] = bo[j];
+            hbo[2 * v + 1] = bo[j + 1];
+            hvo[2 * v] = o;
+            o += vo[j + 1] - vo[j];
+            hvo[2 * v + 1] = o;
+            hpv[2 * v] = delta ? prev[j] : 0u;
+            hpv[2 * v + 1] = 0u;
+        }
+        std::memset(sl.h_desc + o_rel, 0, 8 * ni);
+        if (cudaMemcpyAsync(sl.d_desc, sl.h_desc, upload, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+            return VBYTE_ECUDA;
+        vbk::ListPlan lp{};
+        lp.items = reinterpret_cast<vbk::ListItem *>(sl.d_desc + o_items);
+        lp.nitems = static_cast<uint32_t>(ni);
+        lp.citem = reinterpret_cast<uint32_t *>(sl.d_desc + o_citem);
+        lp.cfirst = reinterpret_cast<uint32_t *>(sl.d_desc + o_cfirst);
+        lp.ncl = static_cast<uint32_t>(ncl);
+        lp.cs = reinterpret_cast<uint2 *>(sl.d_desc + o_cs);
+        lp.rel = reinterpret_cast<uint2 *>(sl.d_desc + o_rel);
+        lp.queue = reinterpret_cast<unsigned int *>(sl.d_desc + o_q);
+        const vbk::BatchArgs a{d_pool, pool_bytes, reinterpret_cast<const uint64_t *>(sl.d_desc + o_bo), out, o,
+                               reinterpret_cast<const uint64_t *>(sl.d_desc + o_vo), 2 * nl,
+                               delta ? reinterpret_cast<const uint32_t *>(sl.d_desc + o_pv) : nullptr, delta};
+        uint32_t *d_status = nullptr;
+        if (vbk::status_word(sl.stream, &d_status) != VBYTE_OK) return VBYTE_ECUDA;
+        return vbk::enqueue_list_plan(a, lp, kItemWarps, d_status, sl.stream);
+    }
+
+    // descriptor bytes a slot needs for the in-place form
+    static size_t items_desc_bytes(const vbyte_server_config &c)
+    {
+        const size_t nl = static_cast<size_t>(c.max_batch_lists);
+        const size_t ni = 2 * nl + c.staging_bytes / kItemBytes + 1;
+        return ni * (sizeof(vbk::ListItem) + 4 + 16) + (nl + 2) * 4 + nl * 40 + 256;
+    }
+
     // ---- one batch on slot sl (queries already marked on the GPU)
     int launch(Slot &sl, uint64_t block_units_off)
     {
         cudaGetLastError();   // clear non-sticky results of earlier queries
         uint32_t *out = d_arena + block_units_off * (kArenaUnit / 4);
-        if (cfg.per_list) {
+        if (cfg.per_list == 0) {
+            const int rc = launch_items(sl, out);
+            if (rc != VBYTE_OK) return rc;
+        } else if (cfg.per_list == 1) {
             uint64_t o = 0;
             for (uint32_t j : sl.lists) {
                 const uint64_t nb = bo[j + 1] - bo[j], nv = vo[j + 1] - vo[j];
@@ -331,7 +443,7 @@ int vbyte_server_create(vbyte_server **out, const uint8_t *d_pool, size_t pool_b
 {
     if (!out || !cfg || !h_byte_off || !h_val_off || num_lists == 0 || (pool_bytes && !d_pool)) return VBYTE_EINVAL;
     if (cfg->arena_bytes < kArenaUnit || cfg->staging_bytes == 0 || cfg->max_inflight < 1 ||
-        cfg->max_batch_queries < 1 || cfg->max_batch_lists < 1)
+        cfg->max_batch_queries < 1 || cfg->max_batch_lists < 1 || cfg->per_list < 0 || cfg->per_list > 2)
         return VBYTE_EINVAL;
     *out = nullptr;
     if (h_byte_off[0] != 0 || h_byte_off[num_lists] != pool_bytes || h_val_off[0] != 0) return VBYTE_EINVAL;
@@ -374,18 +486,20 @@ int vbyte_server_create(vbyte_server **out, const uint8_t *d_pool, size_t pool_b
     for (size_t j = 0; j < num_lists; ++j) max_list = std::max(max_list, h_byte_off[j + 1] - h_byte_off[j]);
     const size_t nl = static_cast<size_t>(cfg->max_batch_lists);
     const size_t np = cfg->staging_bytes / kPieceBytes + nl + 1;
-    const size_t desc = (nl + 1) * 16 + nl * 4 + 16 + np * sizeof(vbk::GatherPiece);
+    const size_t desc = std::max((nl + 1) * 16 + nl * 4 + 16 + np * sizeof(vbk::GatherPiece),
+                                 vbyte_server::items_desc_bytes(*cfg));
     S->slots.resize(static_cast<size_t>(cfg->max_inflight));
     for (Slot &sl : S->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) return fail(VBYTE_ECUDA);
         if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) return fail(VBYTE_ECUDA);
-        if (!cfg->per_list && cudaMalloc(&sl.d_staging, cfg->staging_bytes) != cudaSuccess) return fail(VBYTE_ENOMEM);
+        if (cfg->per_list == 2 && cudaMalloc(&sl.d_staging, cfg->staging_bytes) != cudaSuccess)
+            return fail(VBYTE_ENOMEM);
         if (cudaMalloc(&sl.d_desc, desc) != cudaSuccess) return fail(VBYTE_ENOMEM);
         if (cudaMallocHost(&sl.h_desc, desc) != cudaSuccess) return fail(VBYTE_ENOMEM);
         if (cudaMallocHost(&sl.h_status, 4) != cudaSuccess) return fail(VBYTE_ENOMEM);
         sl.desc_bytes = desc;
         // every workspace the loop will use is allocated now
-        if (vbk::reserve_workspace(sl.stream, cfg->per_list ? max_list : cfg->staging_bytes) != VBYTE_OK)
+        if (vbk::reserve_workspace(sl.stream, cfg->per_list == 1 ? max_list : cfg->staging_bytes) != VBYTE_OK)
             return fail(VBYTE_ENOMEM);
         uint32_t *d_status = nullptr;
         if (vbk::status_word(sl.stream, &d_status) != VBYTE_OK) return fail(VBYTE_ECUDA);

@@ -427,11 +427,16 @@ class _DeviceView:
 
 class Server:
     """vbyte_server_*: a resident pool of compressed lists and a continuous-
-    batching request loop (the scheduler runs in a native thread)."""
+    batching request loop (the scheduler runs in a native thread).  form:
+    "in_place" (batches decoded from the pool as list items), "per_list"
+    (one single-stream call per list) or "gather" (lists gathered, then one
+    segmented batched launch); per_list=True is form="per_list"."""
+
+    FORMS = {"in_place": 0, "per_list": 1, "gather": 2}
 
     def __init__(self, pool, h_byte_off, h_val_off, delta: bool, h_prev=None, arena_bytes: int = 1 << 30,
                  staging_bytes: int = 256 << 20, max_inflight: int = 4, max_batch_queries: int = 64,
-                 max_batch_lists: int = 512, per_list: bool = False):
+                 max_batch_lists: int = 512, per_list: bool = False, form: str | None = None):
         import torch
         if not isinstance(pool, torch.Tensor) or pool.dtype != torch.uint8 or not pool.is_cuda:
             raise TypeError("pool must be a CUDA uint8 tensor")
@@ -439,8 +444,8 @@ class Server:
         self._vo = np.ascontiguousarray(h_val_off, dtype=np.uint64)
         self._pv = None if h_prev is None else np.ascontiguousarray(h_prev, dtype=np.uint32)
         self._pool = pool
-        cfg = _ServerConfig(arena_bytes, staging_bytes, max_inflight, max_batch_queries, max_batch_lists,
-                            int(per_list))
+        mode = self.FORMS[form] if form is not None else int(bool(per_list))
+        cfg = _ServerConfig(arena_bytes, staging_bytes, max_inflight, max_batch_queries, max_batch_lists, mode)
         h = ctypes.c_void_p()
         rc = load().vbyte_server_create(ctypes.byref(h), ctypes.c_void_p(pool.data_ptr()), pool.numel(),
                                         _np_ptr(self._bo), _np_ptr(self._vo), self._bo.size - 1, int(delta),

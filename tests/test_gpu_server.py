@@ -33,11 +33,11 @@ def _server(pool, **kw):
     return vbyte.Server(pool["d"], pool["bo"], pool["vo"], True, pool["prev"], **kw)
 
 
-@pytest.mark.parametrize("per_list", [False, True])
-def test_alone_and_in_the_mix_are_identical(pool, per_list):
+@pytest.mark.parametrize("form", ["in_place", "per_list", "gather"])
+def test_alone_and_in_the_mix_are_identical(pool, form):
     import torch
     srv = _server(pool, arena_bytes=64 << 20, staging_bytes=16 << 20, max_inflight=3, max_batch_queries=32,
-                  per_list=per_list)
+                  form=form)
     _, qoff, qlists = inputs.query_stream(pool["lens"], 300, 1000.0, seed=32)
     probe = [int(x) for x in qlists[qoff[7]:qoff[8]]]
     # alone
@@ -74,12 +74,13 @@ def test_alone_and_in_the_mix_are_identical(pool, per_list):
     torch.cuda.synchronize()
 
 
-def test_admission_waits_for_arena_space(pool):
+@pytest.mark.parametrize("form", ["in_place", "gather"])
+def test_admission_waits_for_arena_space(pool, form):
     # an arena that holds only a few queries' output at a time
     lens = pool["lens"]
     big = [int(j) for j in np.argsort(-lens)[:3]]
     need = int(lens[big].sum()) * 4
-    srv = _server(pool, arena_bytes=need + 4096, staging_bytes=64 << 20, max_inflight=4)
+    srv = _server(pool, arena_bytes=need + 4096, staging_bytes=64 << 20, max_inflight=4, form=form)
     qs = [srv.submit(big) for _ in range(6)]
     for q in qs:
         _, st = srv.wait(q)

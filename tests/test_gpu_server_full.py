@@ -34,21 +34,21 @@ def _expected(pool, lists):
     return torch.cat([pool["want"][int(vo[j]):int(vo[j + 1])] for j in lists])
 
 
-def _server(pool, per_list):
+def _server(pool, form):
     import torch
     free, _ = torch.cuda.mem_get_info()
     arena = int(min(free * 0.25, 8 << 30)) // 4096 * 4096
     return vbyte.Server(pool["d"], pool["bo"], pool["vo"], True, pool["prev"], arena_bytes=arena,
                         staging_bytes=512 << 20, max_inflight=4, max_batch_queries=64, max_batch_lists=512,
-                        per_list=per_list)
+                        form=form)
 
 
-@pytest.mark.parametrize("per_list", [False, True])
-def test_every_query_matches_the_oracle(pool, per_list):
+@pytest.mark.parametrize("form", ["in_place", "per_list", "gather"])
+def test_every_query_matches_the_oracle(pool, form):
     import torch
     nq = 300
     _, qoff, ql = inputs.query_stream(pool["lens"], nq, 20000.0, seed=41)
-    srv = _server(pool, per_list)
+    srv = _server(pool, form)
     probe = [int(x) for x in ql[qoff[5]:qoff[6]]]
     # the probe alone
     q = srv.submit(probe)
@@ -93,7 +93,7 @@ def test_every_query_matches_the_oracle(pool, per_list):
 def test_replay_at_a_stated_rate(pool):
     # open-loop Poisson arrivals at 20,000 q/s: every query completes without a data error
     arr, qoff, ql = inputs.query_stream(pool["lens"], 2000, 20000.0, seed=42)
-    srv = _server(pool, False)
+    srv = _server(pool, "in_place")
     lat, st = srv.replay(arr, qoff, ql)
     assert np.all(st == 0) and np.all(lat > 0)
     assert srv.stats()["queries"] == 2000
