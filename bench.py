@@ -438,10 +438,12 @@ def run_gpu(args):
         for name in [b for b in BLOCKS if b != args.workload]:
             blocks[name] = run_block(args, name, stream, peak, peak_source, src_hash)
 
-    encode = decode64 = batched = serving = None
+    encode = decode64 = batched = serving = delta4 = None
     if ws == 1:
         if not args.no_encode:
             encode = run_encode(args, stream, peak)
+        if not args.no_delta4:
+            delta4 = run_delta4(args, stream, peak)
         if not args.no_decode64:
             try:
                 decode64 = run_decode64(args, stream, peak)
@@ -495,6 +497,7 @@ def run_gpu(args):
         "serving": serving,
         "encode": encode,
         "decode64": decode64,
+        "delta4": delta4,
     }
     print(json.dumps(line))
     if ws > 1:
@@ -649,6 +652,46 @@ def run_decode64(args, stream, peak):
     return {"form": "vbyte_decode_delta64 / vbyte_decode64", "status": status, "streams": res}
 
 
+def run_delta4(args, stream, peak):
+    """Blocked differences (x_i - x_{i-4}, Sec. 1): 2^26 values of four
+    interleaved sorted id lists, so each stored integer is one list's gap;
+    checked bit for bit against the ids and timed with CUDA events: Gints/s
+    and the HBM roofline (input bytes + 4n per call)."""
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    n = 1 << 26
+    g = inputs.geometric_gaps(n, seed=3).astype(np.uint64) + 1
+    x = np.zeros(n, dtype=np.uint64)
+    for k in range(4):
+        x[k::4] = np.cumsum(g[k::4])
+    x = x.astype(np.uint32)
+    b = vbyte.encode_delta4(x)
+    d = torch.from_numpy(b).cuda()
+    out = torch.empty(n, dtype=torch.uint32, device="cuda")
+    for _ in range(3):
+        vbyte.decode_delta4(d, n, out=out, stream=stream)
+    torch.cuda.synchronize()
+    exact = bool(torch.equal(out.view(torch.int32), torch.from_numpy(x.view(np.int32)).cuda()))
+    reps = max(5, min(args.steps, 200))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        vbyte.decode_delta4(d, n, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    algo = int(b.size) + 4 * n
+    achieved = algo / (ms * 1e-3) / 1e9
+    res = {"workload": "2^26 values of four interleaved sorted id lists (gaps 2 + Geometric(0.1))",
+           "n": n, "nbytes": int(b.size), "ms": round(ms, 5), "value": round(n / (ms * 1e-3) / 1e9, 3),
+           "unit": "Gints/s", "bit_exact": exact, "status": int(vbyte.get_status(stream)),
+           "form": "vbyte_decode_delta4 (split count, scan and decode launches)",
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "algorithmic_bytes_per_call": algo}}
+    del d, out
+    return res
+
+
 def run_batched(args, peak):
     """Batched differential decoding of 100,000 rank-Zipf posting lists (about
     1.2e8 values): a tuned plan replayed from a CUDA graph against one
@@ -703,6 +746,34 @@ def run_batched(args, peak):
     st_e = vbyte.get_status(stream)
     exact_b = bool(torch.equal(out_b.view(torch.int32), dwant))
     exact_e = bool(torch.equal(out_e.view(torch.int32), dwant))
+    # the lean per-list form: the same 100,000 calls captured once into a
+    # CUDA graph (one memset and one kernel per list, no host work per call)
+    graph = None
+    if not args.no_graph_each:
+        gs = torch.cuda.Stream()
+        out_g = torch.empty(n, dtype=torch.uint32, device="cuda")
+        torch.cuda.synchronize()
+        vbyte.decode_each(d, hbo, vo, n, True, prev, out=out_g, stream=gs)   # grows the stream's workspace
+        gs.synchronize()
+        g = torch.cuda.CUDAGraph()
+        t0 = time.perf_counter()
+        with torch.cuda.graph(g, stream=gs):
+            vbyte.decode_each(d, hbo, vo, n, True, prev, out=out_g, stream=gs)
+        cap_s = time.perf_counter() - t0
+        g.replay()
+        torch.cuda.synchronize()
+        ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ge0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        ge1.record(stream)
+        torch.cuda.synchronize()
+        g_ms = ge0.elapsed_time(ge1) / reps
+        graph = {"value": round(n / (g_ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms": round(g_ms, 3),
+                 "capture_s": round(cap_s, 2), "bit_exact_vs_oracle": bool(torch.equal(out_g.view(torch.int32), dwant)),
+                 "status": int(vbyte.get_status(gs)),
+                 "form": "the 100,000 vbyte_decode_delta calls captured into one CUDA graph, replayed"}
+        del g, out_g
     med = ms[len(ms) // 2]
     algo = hb.size + 4 * n + 16 * (L + 1)
     # the oracle on every host core, lists split between threads
@@ -726,7 +797,9 @@ def run_batched(args, peak):
                                  "algorithmic_bytes": algo}},
         "per_list": {"value": round(n / (each_ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms": round(each_ms, 3),
                      "form": "vbyte_decode_each (one vbyte_decode_delta per list)"},
+        "per_list_graph": graph,
         "speedup": round(each_ms / med, 2),
+        "speedup_vs_graph": round(graph["ms"] / med, 2) if graph else None,
         "bit_exact_vs_oracle": {"batched": exact_b, "per_list": exact_e},
         "status": st_b | st_e,
         "cpu_baseline": {"value": round(n / cpu_s / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -741,8 +814,8 @@ def run_batched(args, peak):
 def run_serving(args, pool):
     """Open-loop Poisson query streams against the resident 100,000-list pool:
     each query names 2..8 lists drawn proportionally to length; continuous
-    batching (gather + one batched launch per batch) against the same loop
-    decoding every list with its own call.  Per rate, at least
+    batching (each batch decoded in place from the pool as list items)
+    against the same loop decoding every list with its own call.  Per rate, at least
     args.serve_seconds of arrivals or args.serve_queries queries, whichever is
     fewer, after an untimed warm-up.  Latency runs from a query's scheduled
     arrival to the scheduler seeing its batch complete."""
@@ -759,7 +832,8 @@ def run_serving(args, pool):
         vals = int(sum(int(pool["lens"][ql[qoff[i]:qoff[i + 1]]].sum()) for i in range(nq)))
         row = {"rate_qps": rate, "queries": nq, "seconds_of_arrivals": round(float(arr[-1]), 2), "values": vals}
         for form, per_list in (("batched", False), ("per_list", True)):
-            srv = vbyte.Server(pool["d"], pool["bo"], pool["vo"], True, pool["prev"], per_list=per_list, **cfg)
+            srv = vbyte.Server(pool["d"], pool["bo"], pool["vo"], True, pool["prev"],
+                               form="per_list" if per_list else "in_place", **cfg)
             w = min(nq, max(100, int(rate * 0.2)))   # untimed warm-up: 0.2 s at the same rate
             srv.replay(arr[:w], qoff[:w + 1], ql[:int(qoff[w])])
             s0 = srv.stats()
@@ -934,6 +1008,8 @@ def main():
     ap.add_argument("--no-encode", action="store_true")
     ap.add_argument("--no-decode64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-delta4", action="store_true")
+    ap.add_argument("--no-graph-each", action="store_true")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000, 50000])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-queries", type=int, default=100_000)

@@ -16,12 +16,15 @@
 //             the high bit set);
 //   scan64:   one CTA turns the per-tile counts and sums into the values
 //             before each tile and prev plus the sum of every integer before
-//             it, and checks the total count against n;
+//             it (1024 tiles per round, a carry between rounds), and checks
+//             the total count against n;
 //   decode64: per tile, every integer that ends in it, assembled from its own
 //             bytes (at most nine before its terminator; the 16 bytes staged
 //             ahead of the tile cover them), placed by a block scan of the
-//             per-thread counts into shared memory, prefix-summed there in
-//             delta mode, and written out with coalesced 8-byte stores.
+//             per-thread counts into shared memory (one padding slot every
+//             16, so that a warp's stores do not share banks), prefix-summed
+//             there in delta mode, and written out with coalesced 8-byte
+//             stores.
 // Tiles start at the input address rounded down to 16 bytes, so every
 // staged chunk is one aligned 16-byte load; bytes of a chunk outside the
 // input are staged as zero and never counted.
@@ -66,9 +69,15 @@ struct CountShared {
     uint32_t wcnt[kWarps];
 };
 
+// The tile's integers in order, one padding slot after every 16: a thread's
+// run of 16 consecutive ranks then starts 17 slots after its neighbour's, so
+// the 32 lanes of a warp touch 32 different 8-byte bank pairs.
+constexpr int kPadded = kTile + kTile / 16;
+__device__ __forceinline__ uint32_t slot(uint32_t j) { return j + (j >> 4); }
+
 struct DecodeShared {
     alignas(16) uint8_t bytes[kHalo + kTile];
-    alignas(16) unsigned long long vals[kTile];   // the tile's integers, in order
+    alignas(16) unsigned long long vals[kPadded];
     unsigned long long wsum[kWarps];
     uint32_t wcnt[kWarps];
 };
@@ -262,46 +271,50 @@ __global__ void __launch_bounds__(kThreads) count64_kernel(Params p)
     }
 }
 
+// One CTA, 1024 tiles per round (coalesced), a carry between rounds.
 template <bool kDelta>
 __global__ void __launch_bounds__(kScanThreads) scan64_kernel(Params p)
 {
     __shared__ unsigned long long wc[kScanThreads / 32], ws[kScanThreads / 32];
+    __shared__ unsigned long long carry_c, carry_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t T = p.ntiles;
-    const uint64_t per = (T + kScanThreads - 1) / kScanThreads;
-    const uint64_t i0 = std::min<uint64_t>(T, per * tid), i1 = std::min<uint64_t>(T, i0 + per);
-    uint64_t c = 0, s = 0;
-    for (uint64_t i = i0; i < i1; ++i) {
-        c += p.tcnt[i];
-        if (kDelta) s += p.tsum[i];
-    }
-    const uint64_t ci = warp_incl<uint64_t>(c, lane);
-    const uint64_t si = kDelta ? warp_incl<uint64_t>(s, lane) : 0;
-    if (lane == 31) {
-        wc[warp] = ci;
-        ws[warp] = si;
+    if (tid == 0) {
+        carry_c = 0;
+        carry_s = p.prev;
     }
     __syncthreads();
-    uint64_t cb = 0, sb = 0, call = 0;
-    for (int k = 0; k < kScanThreads / 32; ++k) {
-        if (k < warp) {
-            cb += wc[k];
-            sb += ws[k];
+    for (uint64_t b0 = 0; b0 < p.ntiles; b0 += kScanThreads) {
+        const uint64_t i = b0 + tid;
+        const uint64_t c = i < p.ntiles ? p.tcnt[i] : 0u;
+        const uint64_t s = (kDelta && i < p.ntiles) ? p.tsum[i] : 0u;
+        const uint64_t ci = warp_incl<uint64_t>(c, lane);
+        const uint64_t si = kDelta ? warp_incl<uint64_t>(s, lane) : 0u;
+        if (lane == 31) {
+            wc[warp] = ci;
+            ws[warp] = si;
         }
-        call += wc[k];
-    }
-    uint64_t ce = cb + ci - c, se = p.prev + sb + si - s;
-    for (uint64_t i = i0; i < i1; ++i) {
-        const uint64_t x = p.tcnt[i];
-        p.tcnt[i] = ce;
-        ce += x;
-        if (kDelta) {
-            const uint64_t y = p.tsum[i];
-            p.tsum[i] = se;
-            se += y;
+        __syncthreads();
+        uint64_t cb = carry_c, sb = carry_s, tc = 0, ts = 0;
+        for (int k = 0; k < kScanThreads / 32; ++k) {
+            if (k < warp) {
+                cb += wc[k];
+                sb += ws[k];
+            }
+            tc += wc[k];
+            ts += ws[k];
         }
+        if (i < p.ntiles) {
+            p.tcnt[i] = cb + ci - c;
+            if (kDelta) p.tsum[i] = sb + si - s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            carry_c += tc;
+            carry_s += ts;
+        }
+        __syncthreads();
     }
-    if (tid == 0 && call != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+    if (tid == 0 && carry_c != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
 }
 
 template <bool kDelta>
@@ -316,25 +329,25 @@ __global__ void __launch_bounds__(kThreads) decode64_kernel(Params p)
         tile_range(p, t, &a, &b);
         uint32_t C = 0;
         uint32_t rank = block_excl<uint32_t>(slice_count(S.bytes, tid, a, b), S.wcnt, &C);
-        walk<true>(S.bytes, tid, a, b, [&](uint64_t v) { S.vals[rank++] = v; });
+        walk<true>(S.bytes, tid, a, b, [&](uint64_t v) { S.vals[slot(rank++)] = v; });
         __syncthreads();
         if (kDelta) {
             // running sums of the tile's integers from prev + everything before it
             const uint32_t j0 = kSlice * tid, j1 = min(j0 + kSlice, C);
             uint64_t run = 0;
-            for (uint32_t j = j0; j < j1; ++j) run += S.vals[j];
+            for (uint32_t j = j0; j < j1; ++j) run += S.vals[slot(j)];
             unsigned long long tot;
             uint64_t x = p.tsum[t] + block_excl<unsigned long long>(run, S.wsum, &tot);
             for (uint32_t j = j0; j < j1; ++j) {
-                x += S.vals[j];
-                S.vals[j] = x;
+                x += S.vals[slot(j)];
+                S.vals[slot(j)] = x;
             }
             __syncthreads();
         }
         const uint64_t r0 = p.tcnt[t];
         for (uint32_t j = tid; j < C; j += kThreads) {
             const uint64_t g = r0 + j;
-            if (g < p.n) p.out[g] = S.vals[j];
+            if (g < p.n) p.out[g] = S.vals[slot(j)];
         }
         __syncthreads();   // the next stage and scan reuse S
     }
