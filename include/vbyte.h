@@ -346,8 +346,13 @@ void vbyte_server_destroy(vbyte_server *srv);
 /* End-to-end form of vbyte_decode / vbyte_decode_delta for data in host memory: copies
  * h_in to the device, decodes (differentially when delta != 0) and copies the
  * n values back to h_out, through library-owned device buffers kept per
- * stream.  Synchronises the stream before returning.  The data-error status
- * is still read with vbyte_get_status(). */
+ * stream.  Inputs of 128 MiB or more go in pieces of 64 MiB: while later
+ * pieces are still being copied in, earlier ones are counted and decoded
+ * (the split count, scan and decode launches, the scan carrying the count
+ * and running sum from piece to piece) and their values copied back, on
+ * library-owned streams ordered after `stream`; page-locked h_in and h_out
+ * let the copies in both directions overlap.  Synchronises the stream before
+ * returning.  The data-error status is still read with vbyte_get_status(). */
 int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out,
                       size_t n, int delta, uint32_t prev, void *stream);
 

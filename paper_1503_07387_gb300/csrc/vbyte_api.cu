@@ -430,6 +430,15 @@ int vbyte_decode_host(const uint8_t *h_in, size_t nbytes, uint32_t *h_out, size_
             hb->cap_out = n;
         }
     }
+    // large inputs: pieces copied in, decoded and copied back with the copies
+    // in both directions and the kernels overlapping
+    if (nbytes >= 2 * vbk::kPipePiece && n) {
+        uint8_t *ws = nullptr;
+        int rc = vbk::stream_workspace(s, vbk::pipe_workspace_bytes(nbytes), &ws);
+        if (rc != VBYTE_OK) return rc;
+        return vbk::decode_host_pipelined(h_in, nbytes, h_out, n, delta != 0, prev, hb->d_in, hb->d_out, ws,
+                                          reinterpret_cast<uint32_t *>(ws), s, vbk::kPipePiece);
+    }
     if (nbytes && cudaMemcpyAsync(hb->d_in, h_in, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return VBYTE_ECUDA;
     int rc = vbk::launch_decode(hb->d_in, nbytes, hb->d_out, n, delta != 0, prev, s);

@@ -128,6 +128,15 @@ struct ListPlan {
 int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta, uint32_t *status, cudaStream_t s,
                       bool table = false);
 
+// Decoding from host buffers in pieces of about kPipePiece bytes with the
+// copies and kernels overlapping (vbyte_split.cu); d_in and d_out hold the
+// whole input and output, ws pipe_workspace_bytes(nbytes).
+constexpr size_t kPipePiece = size_t(64) << 20;
+size_t pipe_workspace_bytes(size_t nbytes);
+int decode_host_pipelined(const uint8_t *h_in, size_t nbytes, uint32_t *h_out, size_t n, bool delta, uint32_t prev,
+                          uint8_t *d_in, uint32_t *d_out, uint8_t *ws, uint32_t *status, cudaStream_t s,
+                          size_t piece_bytes);
+
 // A piece of a gather: len bytes from src + src_off to dst + dst_off.
 struct GatherPiece {
     uint64_t src;

@@ -34,6 +34,8 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "vbyte.h"
 #include "vbyte_device.cuh"
@@ -68,6 +70,7 @@ struct Params {
     uint64_t in_hi;
     uint32_t T;         // warp tiles per range
     uint32_t G;         // ranges (CTAs of the count and decode launches)
+    uint32_t range0;    // the first range of a launch (pieces of a pipelined decode; else 0)
     uint2 *ent;         // per warp tile: (count, sum) before it within its range
     uint2 *ctot;        // per range: (count, sum) of the range
     uint4 *cpre;        // per range: values before it (lo, hi), running x before it, 0
@@ -272,8 +275,8 @@ __device__ __forceinline__ void range_scan4(const Params &p, uint64_t t0, uint32
         x = cat4(x, Seg4{E[i].x, E4[i]});
     }
     if (tid == 0) {
-        p.ctot[blockIdx.x] = make_uint2(tot.c, 0u);
-        p.ctot4[blockIdx.x] = tot.s;
+        p.ctot[blockIdx.x + p.range0] = make_uint2(tot.c, 0u);
+        p.ctot4[blockIdx.x + p.range0] = tot.s;
     }
 }
 
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 5) count_kernel(const Params p)
     __shared__ uint4 E4[kD4 ? kMaxT : 1];
     __shared__ uint32_t wcnt[kWarps], wsum[kWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * p.T;
+    const uint64_t t0 = static_cast<uint64_t>(blockIdx.x + p.range0) * p.T;
     const uint32_t nt = static_cast<uint32_t>(min(static_cast<uint64_t>(p.T), p.nwt - t0));
     for (uint32_t i = warp; i < nt; i += kWarps) {
         uint32_t c, s;
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 5) count_kernel(const Params p)
         xc += v.x;
         xs += v.y;
     }
-    if (tid == 0) p.ctot[blockIdx.x] = make_uint2(tc, ts);
+    if (tid == 0) p.ctot[blockIdx.x + p.range0] = make_uint2(tc, ts);
 }
 
 // ---- scan of the range totals (one CTA)
@@ -382,6 +385,59 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const Params p)
         __syncthreads();
     }
     if (tid == 0 && carry_c != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+}
+
+// A piece of a pipelined decode: the prefixes of ranges [range0, r1), from
+// the carry the earlier pieces left (values before the piece, running x;
+// the first piece starts from none and prev); then the carry after the
+// piece.  The last piece checks the total against n.
+__global__ void __launch_bounds__(kScanThreads) scan_piece_kernel(const Params p, uint32_t r1,
+                                                                  unsigned long long *carry, bool first, bool last)
+{
+    __shared__ unsigned long long wc[kScanThreads / 32];
+    __shared__ uint32_t wsm[kScanThreads / 32];
+    __shared__ unsigned long long carry_c;
+    __shared__ uint32_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        carry_c = first ? 0ull : carry[0];
+        carry_s = first ? p.prev : static_cast<uint32_t>(carry[1]);
+    }
+    __syncthreads();
+    for (uint32_t b0 = p.range0; b0 < r1; b0 += kScanThreads) {
+        const uint32_t i = b0 + tid;
+        const uint2 v = i < r1 ? p.ctot[i] : make_uint2(0u, 0u);
+        const uint32_t ic = warp_incl_scan(v.x, lane), is = warp_incl_scan(v.y, lane);
+        if (lane == 31) {
+            wc[warp] = ic;
+            wsm[warp] = is;
+        }
+        __syncthreads();
+        unsigned long long bc = carry_c, tc = 0;
+        uint32_t bs = carry_s, ts = 0;
+        for (int q = 0; q < kScanThreads / 32; ++q) {
+            if (q < warp) {
+                bc += wc[q];
+                bs += wsm[q];
+            }
+            tc += wc[q];
+            ts += wsm[q];
+        }
+        const unsigned long long xc = bc + ic - v.x;
+        const uint32_t xs = bs + is - v.y;
+        if (i < r1) p.cpre[i] = make_uint4(static_cast<uint32_t>(xc), static_cast<uint32_t>(xc >> 32), xs, 0u);
+        __syncthreads();
+        if (tid == 0) {
+            carry_c += tc;
+            carry_s += ts;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        carry[0] = carry_c;
+        carry[1] = carry_s;
+        if (last && carry_c != p.n) atomicOr(p.status, VBYTE_ERR_COUNT_MISMATCH);
+    }
 }
 
 // The blocked-difference form: cat4 over the ranges from the seed (no
@@ -762,11 +818,11 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
     if (lane < kRing) *reinterpret_cast<uint4 *>(M.ring[lane] + kHalo + kUnit) = make_uint4(0u, 0u, 0u, 0u);
     const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
     const uintptr_t hi = lo + p.nbytes;
-    const uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * p.T;
+    const uint64_t t0 = static_cast<uint64_t>(blockIdx.x + p.range0) * p.T;
     const uint32_t nt = static_cast<uint32_t>(min(static_cast<uint64_t>(p.T), p.nwt - t0));
     const uint32_t mine = nt > static_cast<uint32_t>(warp) ? (nt - warp + kWarps - 1) / kWarps : 0u;
     const uint32_t K = mine * kUnits;   // units of this warp: tiles warp, warp + 8, ... of the range
-    const uint4 cp = p.cpre[blockIdx.x];
+    const uint4 cp = p.cpre[blockIdx.x + p.range0];
     const unsigned long long C0 = cp.x | (static_cast<unsigned long long>(cp.y) << 32);
     auto issue = [&](uint32_t k) {
         if (k < K) issue_unit(p, t0 + warp + (k / kUnits) * kWarps, static_cast<int>(k % kUnits), lane,
@@ -779,7 +835,7 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
     uint32_t X = 0;
     uint4 B = make_uint4(0u, 0u, 0u, 0u);   // kD4: each class's running value (class = rank mod 4)
     uint4 cp4 = make_uint4(0u, 0u, 0u, 0u);
-    if (kD4) cp4 = p.cpre4[blockIdx.x];
+    if (kD4) cp4 = p.cpre4[blockIdx.x + p.range0];
     uint2 e_next = make_uint2(0u, 0u);
     if (K) e_next = p.ent[t0 + warp];
     for (uint32_t k = 0; k < K; ++k) {
@@ -1131,6 +1187,152 @@ int enqueue_list_plan(const BatchArgs &a, const ListPlan &lp, int warps_per_cta,
             sp::lists_decode_kernel<false><<<g, nt, smem, s>>>(p);
     }
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
+}
+
+// ---- decoding from host buffers, pipelined
+//
+// The input is cut into pieces of whole ranges (R ranges of T warp tiles).
+// A copy stream moves the pieces to the device one after another; the
+// compute stream counts each piece once its bytes (and the 16 before) are
+// there, scans its ranges from the carry of the pieces before it, decodes it,
+// and records how many values precede the next piece; the host reads that and
+// queues the piece's values back on a third stream as soon as they are
+// decoded.  Copies in the two directions and the kernels overlap.
+
+namespace {
+struct PipeStreams {
+    cudaStream_t up = nullptr, work = nullptr, down = nullptr;
+    std::vector<cudaEvent_t> ev;
+    unsigned long long *h_after = nullptr;   // pinned: values after each piece
+    size_t pieces = 0;
+};
+std::mutex g_pipe_mu;
+std::map<std::pair<int, uintptr_t>, PipeStreams> g_pipe;
+
+int pipe_streams(cudaStream_t s, size_t pieces, PipeStreams **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VBYTE_ECUDA;
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    PipeStreams &P = g_pipe[{dev, reinterpret_cast<uintptr_t>(s)}];
+    if (!P.up) {
+        if (cudaStreamCreateWithFlags(&P.up, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&P.work, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&P.down, cudaStreamNonBlocking) != cudaSuccess)
+            return VBYTE_ECUDA;
+    }
+    while (P.ev.size() < 3 * pieces + 3) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return VBYTE_ECUDA;
+        P.ev.push_back(e);
+    }
+    if (P.pieces < pieces) {
+        if (P.h_after) cudaFreeHost(P.h_after);
+        P.h_after = nullptr;
+        if (cudaMallocHost(&P.h_after, pieces * sizeof(unsigned long long)) != cudaSuccess) return VBYTE_ENOMEM;
+        P.pieces = pieces;
+    }
+    *out = &P;
+    return VBYTE_OK;
+}
+}  // namespace
+
+size_t pipe_workspace_bytes(size_t nbytes)
+{
+    // ranges of at least one tile: an ent word per tile, ctot and cpre per range, the carry
+    const uint64_t nwt = sp::wtiles_for(15, nbytes);
+    return 256 + 8 * nwt + 16 + 24 * nwt + 64;
+}
+
+int decode_host_pipelined(const uint8_t *h_in, size_t nbytes, uint32_t *h_out, size_t n, bool delta, uint32_t prev,
+                          uint8_t *d_in, uint32_t *d_out, uint8_t *ws, uint32_t *status, cudaStream_t s,
+                          size_t piece_bytes)
+{
+    sp::Dev di;
+    int rc = sp::dev_info(&di);
+    if (rc != VBYTE_OK) return rc;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(d_in);
+    const uint64_t nwt = sp::wtiles_for(a, nbytes);
+    const uint64_t R = static_cast<uint64_t>(di.sms) * di.occ;                  // ranges per piece
+    const uint64_t T = std::max<uint64_t>(1, std::min<uint64_t>(sp::kMaxT, piece_bytes / sp::kWT / R));
+    const uint64_t TP = T * R;                                                   // warp tiles per piece
+    const uint64_t K = (nwt + TP - 1) / TP;                                      // pieces
+    const uint64_t G = (nwt + T - 1) / T;
+    PipeStreams *P = nullptr;
+    if ((rc = pipe_streams(s, K, &P)) != VBYTE_OK) return rc;
+    // workspace: ent per tile, ctot and cpre per range, the carry
+    uint8_t *w = ws + 256;
+    uint2 *ent = reinterpret_cast<uint2 *>(w);
+    uint2 *ctot = reinterpret_cast<uint2 *>(w + (8 * nwt + 15) / 16 * 16);
+    uint4 *cpre = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(ctot) + (8 * G + 15) / 16 * 16);
+    unsigned long long *carry = reinterpret_cast<unsigned long long *>(cpre + G);
+    sp::Params p = {};
+    p.in = d_in;
+    p.nbytes = nbytes;
+    p.out = d_out;
+    p.n = n;
+    p.base = a & ~static_cast<uintptr_t>(15);
+    p.nwt = nwt;
+    p.in_lo = p.base == a ? 0u : 1u;
+    p.in_hi = (a + nbytes - p.base) / sp::kWT;
+    p.T = static_cast<uint32_t>(T);
+    p.G = static_cast<uint32_t>(G);
+    p.ent = ent;
+    p.ctot = ctot;
+    p.cpre = cpre;
+    p.status = status;
+    p.prev = prev;
+    cudaEvent_t start = P->ev[3 * K], end_work = P->ev[3 * K + 1], end_down = P->ev[3 * K + 2];
+    if (cudaEventRecord(start, s) != cudaSuccess) return VBYTE_ECUDA;
+    for (cudaStream_t x : {P->up, P->work, P->down})
+        if (cudaStreamWaitEvent(x, start, 0) != cudaSuccess) return VBYTE_ECUDA;
+    // the input, piece by piece (piece i: its tiles, clipped to the input)
+    const uint64_t skew = a - p.base;
+    for (uint64_t i = 0; i < K; ++i) {
+        const uint64_t b0 = i == 0 ? 0 : i * TP * sp::kWT - skew;
+        const uint64_t b1 = std::min<uint64_t>(nbytes, (i + 1) * TP * sp::kWT - skew);
+        if (b1 > b0 && cudaMemcpyAsync(d_in + b0, h_in + b0, b1 - b0, cudaMemcpyHostToDevice, P->up) != cudaSuccess)
+            return VBYTE_ECUDA;
+        if (cudaEventRecord(P->ev[i], P->up) != cudaSuccess) return VBYTE_ECUDA;
+    }
+    // count, scan and decode each piece once its bytes (and those before) are there
+    for (uint64_t i = 0; i < K; ++i) {
+        const uint64_t r0 = i * R, r1 = std::min<uint64_t>(G, (i + 1) * R);
+        if (cudaStreamWaitEvent(P->work, P->ev[i], 0) != cudaSuccess) return VBYTE_ECUDA;
+        p.range0 = static_cast<uint32_t>(r0);
+        const unsigned g = static_cast<unsigned>(r1 - r0);
+        if (delta)
+            sp::count_kernel<true, false><<<g, sp::kThreads, 0, P->work>>>(p);
+        else
+            sp::count_kernel<false, false><<<g, sp::kThreads, 0, P->work>>>(p);
+        sp::scan_piece_kernel<<<1, sp::kScanThreads, 0, P->work>>>(p, static_cast<uint32_t>(r1), carry, i == 0,
+                                                                   i + 1 == K);
+        if (cudaMemcpyAsync(P->h_after + i, carry, 8, cudaMemcpyDeviceToHost, P->work) != cudaSuccess)
+            return VBYTE_ECUDA;
+        if (cudaEventRecord(P->ev[K + i], P->work) != cudaSuccess) return VBYTE_ECUDA;
+        if (delta)
+            sp::decode_kernel<true, false><<<g, sp::kThreads, 0, P->work>>>(p);
+        else
+            sp::decode_kernel<false, false><<<g, sp::kThreads, 0, P->work>>>(p);
+        if (cudaEventRecord(P->ev[2 * K + i], P->work) != cudaSuccess) return VBYTE_ECUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) return VBYTE_ECUDA;
+    // each piece's values back as soon as they are decoded
+    unsigned long long before = 0;
+    for (uint64_t i = 0; i < K; ++i) {
+        if (cudaEventSynchronize(P->ev[K + i]) != cudaSuccess) return VBYTE_ECUDA;
+        const unsigned long long after = std::min<unsigned long long>(P->h_after[i], n);
+        if (cudaStreamWaitEvent(P->down, P->ev[2 * K + i], 0) != cudaSuccess) return VBYTE_ECUDA;
+        if (after > before &&
+            cudaMemcpyAsync(h_out + before, d_out + before, (after - before) * 4, cudaMemcpyDeviceToHost, P->down) !=
+                cudaSuccess)
+            return VBYTE_ECUDA;
+        before = std::max(before, after);
+    }
+    if (cudaEventRecord(end_work, P->work) != cudaSuccess || cudaStreamWaitEvent(s, end_work, 0) != cudaSuccess ||
+        cudaEventRecord(end_down, P->down) != cudaSuccess || cudaStreamWaitEvent(s, end_down, 0) != cudaSuccess)
+        return VBYTE_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 
 size_t split_workspace_bound(size_t nbytes)
