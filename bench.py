@@ -94,14 +94,22 @@ WORKLOADS = {
 HEADLINE = "roofline_stress_2^28"
 BLOCKS = ["plain_uniform_bits_1e6", "differential_2x2^26"]   # reported beside the headline
 
-# Small cases for ncu captures (one stream, larger than L2, a few launches).
+# Single streams for ncu captures, a few launches each: (generator, n,
+# differential, seed, default 0), the seeds those of the workloads above.
+# The 2^28 streams are the headline's own (at most 2.4 GB on the device);
+# the 2^26 ones are smaller cases of the same kernels for --set full.
 PROFILE_CASES = {
+    "one_two_plain_2^28": ("one_two_byte_mix", 1 << 28, False),
+    "one_two_delta_2^28": ("one_two_byte_mix", 1 << 28, True),
+    "full_range_plain_2^28": ("full_range", 1 << 28, False),
+    "full_range_delta_2^28": ("full_range", 1 << 28, True),
     "one_two_plain_2^26": ("one_two_byte_mix", 1 << 26, False),
     "one_two_delta_2^26": ("one_two_byte_mix", 1 << 26, True),
     "full_range_plain_2^26": ("full_range", 1 << 26, False),
     "full_range_delta_2^26": ("full_range", 1 << 26, True),
     "geometric_delta_2^26": ("geometric_gaps", 1 << 26, True),
-    "uniform300_delta_2^26": ("uniform_gaps", 1 << 26, True),
+    "uniform300_delta_2^26": ("uniform_gaps", 1 << 26, True, 1),
+    "uniform_bits_plain_1e6": ("uniform_bits", 1_000_000, False),
 }
 
 
@@ -146,9 +154,11 @@ def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
     return ws * units_per_rank / seconds / 1e9
 
 
-# the translation unit of the decode kernels and every header it includes
-KERNEL_SOURCES = ["paper_1503_07387_gb300/csrc/vbyte_stream.cu", "paper_1503_07387_gb300/csrc/vbyte_device.cuh",
-                  "paper_1503_07387_gb300/csrc/vbyte_internal.h"]
+# the translation units of the stream decode kernels, every header they
+# include, and the dispatcher that picks a kernel per stream
+KERNEL_SOURCES = ["paper_1503_07387_gb300/csrc/" + f for f in
+                  ("vbyte_stream.cu", "vbyte_split.cu", "vbyte_device.cuh", "vbyte_emit.cuh",
+                   "vbyte_table.cuh", "vbyte_internal.h", "vbyte_api.cu")] + ["include/vbyte.h"]
 
 
 def _code_only(src: str) -> str:
@@ -382,7 +392,8 @@ def roofline_of(streams, launch_ms, peak, peak_source, src_hash, kernel):
 def kernel_name(vbyte, streams):
     passes = {vbyte.chosen_passes(int(s["host"].size), s["n"], s["delta"]) for s in streams}
     names = {1: "onepass_kernel (single pass, decoupled look-back)", 2: "sdecode_kernel (count then decode)",
-             3: "sp::count_kernel + sp::decode_kernel (split)"}
+             3: "sp::count_kernel + sp::decode_kernel (split)",
+             4: "sp::count_kernel + sp::decode_kernel (split, table-driven step)"}
     return " + ".join(names[p] for p in sorted(passes))
 
 
@@ -524,15 +535,18 @@ def run_e2e(args, streams, stream, ws):
     if ws > 1:
         dist.barrier()
     te = time.perf_counter()
+    marks = [te]
     for _ in range(e2e_steps):
         for i, s in enumerate(streams):
             vbyte.decode_host(h_in[i], s["n"], delta=s["delta"], out=h_out[i], stream=stream)
-    e2e_s = max_over_ranks(time.perf_counter() - te, ws, "cuda")
+        marks.append(time.perf_counter())
+    e2e_s = max_over_ranks(marks[-1] - te, ws, "cuda")
     status = vbyte.get_status()
     total = sum(s["n"] for s in streams)
     return {"value": round(whole_job_rate(total * e2e_steps, ws, e2e_s), 3), "unit": UNIT,
             "h2d_bytes_per_step": int(sum(s["host"].size for s in streams)),
             "d2h_bytes_per_step": int(4 * total), "steps": e2e_steps,
+            "step_ms": [round(1e3 * (b - a), 2) for a, b in zip(marks, marks[1:])],
             "api": "vbyte_decode_host (pinned host buffers, copies inside the call)", "status": status}
 
 
@@ -895,8 +909,8 @@ def run_profile_case(args):
     """One small stream decoded a few times (the command ncu captures)."""
     import torch
     from paper_1503_07387_gb300 import vbyte
-    gen, n, delta = PROFILE_CASES[args.profile_case]
-    v = getattr(inputs, gen)(n, seed=0)
+    gen, n, delta, *seed = PROFILE_CASES[args.profile_case]
+    v = getattr(inputs, gen)(n, seed=seed[0] if seed else 0)
     b = vbyte.encode(v)
     if args.passes:
         vbyte.debug_force_passes(args.passes)

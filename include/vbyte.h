@@ -29,6 +29,10 @@
  *     cudaMallocAsync on that stream; a call made while the stream is being
  *     captured into a CUDA graph never allocates and returns VBYTE_ENOMEM if
  *     the workspace is too small (run the same call once before capture).
+ *   - A stream is driven by one host thread at a time: a call that grows a
+ *     stream's workspace frees the old one in stream order, so two threads
+ *     queueing work on the same stream at once can race on it.  Calls on
+ *     different streams may come from any threads.
  *   - Return codes are synchronous argument/launch checks (VBYTE_OK ...).
  *     Errors that depend on the data are recorded asynchronously in the
  *     per-stream status word (VBYTE_ERR_* bits) and read with

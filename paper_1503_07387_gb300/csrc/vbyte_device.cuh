@@ -274,26 +274,28 @@ __device__ __forceinline__ uint32_t dense_words(uint32_t tl)
     return ((tl & (tl >> 1)) & 0x7777u) | ((tl & (tl >> 2)) & 0x3333u) | ((tl & (tl >> 3)) & 0x1111u);
 }
 
-// Per-terminator assembly from registers for a slice whose words each hold
-// at most one terminator (dense_words(tl) == 0) and lie inside the stream:
-// one fixed step per word, emit(value) in order.
-template <typename F>
-__device__ __forceinline__ void assemble_words(uint32_t wp, uint4 w, uint32_t tl, uint32_t t20, F emit)
+// Values of a slice whose words each hold at most one terminator
+// (dense_words(tl) == 0) and lie inside the stream, all four words at once
+// and without branches: v[j] is the value ending in word j when bit j of the
+// result is set.  A value's length follows from the terminator of the word
+// before it (the last one, for the word before the slice): none there means
+// five bytes -- or more, which is malformed and reported by the count pass.
+__device__ __forceinline__ uint32_t words4(uint32_t wp, uint4 w, uint32_t tl, uint32_t t20, uint32_t (&v)[4])
 {
     const uint32_t W[5] = {wp, w.x, w.y, w.z, w.w};
+    int prev = 31 - __clz(t20 & 0xFu);   // last terminator of the word before (-1: none)
+    uint32_t nz = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t nib = (tl >> (4 * j)) & 0xFu;
-        if (nib) {
-            const int o4 = __ffs(nib) - 1;
-            const int o = 4 * j + o4;
-            const uint32_t below = t20 & ((1u << (o + 4)) - 1u);   // terminators before it (t20 bits)
-            const int L = min(o + 4 - (31 - __clz(below)), 5);     // none: 5 or more bytes
-            const uint32_t lo4 = __funnelshift_r(W[j], W[j + 1], 8 * o4);
-            const uint32_t x = prmt(W[j + 1], 0u, 0x4440u | static_cast<uint32_t>(o4));
-            emit(assemble(lo4, x, L));
-        }
+        const int o4 = 31 - __clz(nib);   // the word's terminator (-1: none)
+        const int L = min(4 + o4 - prev, 5);
+        const uint32_t sh = static_cast<uint32_t>(o4) & 3u;
+        v[j] = assemble(__funnelshift_r(W[j], W[j + 1], 8 * sh), prmt(W[j + 1], 0u, 0x4440u | sh), L);
+        nz |= (nib ? 1u : 0u) << j;
+        prev = o4;
     }
+    return nz;
 }
 
 // Bit j set iff byte va + j lies inside [lo, hi).

@@ -21,10 +21,10 @@
 //   * scan: one CTA turns the range totals into each range's prefix: values
 //     before it and the running x before it (from prev).
 //   * decode: every warp on its own.  Its units travel through a ring of
-//     three shared-memory buffers with cp.async (two units ahead), each unit
-//     is decoded into the warp's value buffer (one-byte units stay as bytes)
-//     and written out with coalesced 16-byte stores.  No CTA barrier after
-//     the start, no wait on another CTA.
+//     four shared-memory buffers with cp.async (three units ahead), each
+//     unit is decoded into the warp's value buffer (one-byte units stay as
+//     bytes) and written out with coalesced 16-byte stores.  No CTA barrier
+//     after the start, no wait on another CTA.
 // The input is read twice (count, decode); the per-tile words add 8 bytes per
 // 2 KiB.
 #include <cuda_runtime.h>
@@ -53,7 +53,7 @@ constexpr int kUnit = kLanes * kBPT;            // 512 bytes per warp step
 constexpr int kUnits = 4;                       // units per warp tile
 constexpr int kWT = kUnit * kUnits;             // 2 KiB warp tile
 constexpr uint32_t kMaxT = 1024;                // warp tiles per CTA range
-constexpr int kRing = 3;                        // unit buffers per warp
+constexpr int kRing = 4;                        // unit buffers per warp (kRing - 1 in flight)
 constexpr int kSlot = kHalo + kUnit + 16;       // a unit, the 16 bytes before and after it
 constexpr int kVal = kUnit + 16;                // staged values of one unit
 constexpr uint32_t kMaxRanges = 8192;           // bound on the ranges beyond nwt / kMaxT
@@ -158,7 +158,11 @@ __device__ __forceinline__ void slice_values(uint4 w, uint32_t wp, uint32_t tl, 
             wpp = c4[j];
         }
     } else if (in && !dense_words(tl)) {
-        assemble_words(wp, w, tl, t20, f);
+        uint32_t v[4];
+        const uint32_t nz = words4(wp, w, tl, t20, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((nz >> j) & 1u) f(v[j]);
     } else {
         assemble_regs(wp, w, tl, t20, tc, f);
     }
@@ -232,8 +236,12 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
             const bool le2 = !(c20 & (c20 << 1) & 0xFFFF8u);
             if (in && __all_sync(~0u, le2))
                 sum += sum_le2_fast(w[u], wp);
-            else if (in && !__any_sync(~0u, dense_words(tl)))
-                assemble_words(wp, w[u], tl, t20, [&](uint32_t v) { sum += v; });
+            else if (in && !__any_sync(~0u, dense_words(tl))) {
+                uint32_t v[4];
+                const uint32_t nz = words4(wp, w[u], tl, t20, v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sum += ((nz >> j) & 1u) ? v[j] : 0u;
+            }
             else if (in)
                 sum += sum_any_fast(w[u], wp, tl, t20);
             else
@@ -684,19 +692,38 @@ __device__ __forceinline__ void unit_stage(const uint8_t *ub, bool in, uintptr_t
             wp = c4[j];
         }
     } else {
-        // longer codes: each value assembled once (one fixed step per word
-        // when no word holds two terminators), then running sums from this
-        // lane's offset within the unit
-        if (in && !__any_sync(~0u, dense_words(m.tl)))
-            assemble_words(m.wprev, m.w, m.tl, m.t20, [&](uint32_t v) {
-                *dst++ = v;
-                vsum += v;
-            });
-        else
-            assemble_all(sw, lane, m.tl, m.t20, m.tc, [&](uint32_t v) {
-                *dst++ = v;
-                vsum += v;
-            });
+        // longer codes: each value assembled once -- in registers, one fixed
+        // step per word, when no word holds two terminators (running sums
+        // from this lane's offset within the unit taken there too), else one
+        // terminator at a time through the value buffer
+        if (in && !__any_sync(~0u, dense_words(m.tl))) {
+            uint32_t v[4];
+            const uint32_t nz = words4(m.wprev, m.w, m.tl, m.t20, v);
+            uint32_t run = 0;
+            if (kDelta) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) vsum += ((nz >> j) & 1u) ? v[j] : 0u;
+                const uint32_t incs = warp_incl_scan(vsum, lane);
+                ws = __shfl_sync(~0u, incs, 31);
+                run = incs - vsum;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if ((nz >> j) & 1u) {
+                    if (kDelta) {
+                        run += v[j];
+                        *dst++ = run;
+                    } else {
+                        *dst++ = v[j];
+                    }
+                }
+            }
+            return;
+        }
+        assemble_all(sw, lane, m.tl, m.t20, m.tc, [&](uint32_t v) {
+            *dst++ = v;
+            vsum += v;
+        });
         dst -= cnt;
         if (kDelta) {
             const uint32_t incs = warp_incl_scan(vsum, lane);
@@ -829,8 +856,8 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
                               M.ring[k % kRing]);
         cp_async_commit();
     };
-    issue(0);
-    issue(1);
+#pragma unroll
+    for (int i = 0; i < kRing - 1; ++i) issue(i);
     unsigned long long R = 0;
     uint32_t X = 0;
     uint4 B = make_uint4(0u, 0u, 0u, 0u);   // kD4: each class's running value (class = rank mod 4)
@@ -839,9 +866,9 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
     uint2 e_next = make_uint2(0u, 0u);
     if (K) e_next = p.ent[t0 + warp];
     for (uint32_t k = 0; k < K; ++k) {
-        cp_async_wait_prior<1>();   // unit k has landed (for this lane)
-        __syncwarp();               // ... for every lane
-        issue(k + 2);
+        cp_async_wait_prior<kRing - 2>();   // unit k has landed (for this lane)
+        __syncwarp();                       // ... for every lane
+        issue(k + kRing - 1);
         const uint32_t u = k % kUnits;
         const uint64_t t = t0 + warp + (k / kUnits) * kWarps;
         if (u == 0) {
