@@ -905,10 +905,74 @@ def _oracle_prefix(oracle, s, m, nb):
 
 # --------------------------------------------------------------- profile case --
 
+# Other kernels' cases: the batched plan on the 100,000-list workload, the
+# device encoder and the 64-bit decoder on their bench inputs.
+OTHER_PROFILE_CASES = ["batched_plan_1e5_lists", "encode_delta_geometric_2^26", "decode64_geometric_ids_2^26",
+                       "decode64_uniform_bits_2^26"]
+
+
+def _profile_other(args):
+    import torch
+    from paper_1503_07387_gb300 import vbyte
+    case = args.profile_case
+    launches = args.warmup + args.steps
+    if case == "batched_plan_1e5_lists":
+        ids, vo = inputs.posting_lists()
+        prev = inputs.full_range(vo.size - 1, seed=17)
+        hb, hbo = vbyte.encode_batched(ids, vo, True, prev)
+        n = int(vo[-1])
+        d = torch.from_numpy(hb).cuda()
+        dbo = torch.from_numpy(hbo.view(np.int64)).cuda()
+        dvo = torch.from_numpy(vo.view(np.int64)).cuda()
+        dp = torch.from_numpy(prev.view(np.int32)).cuda()
+        out = torch.empty(n, dtype=torch.uint32, device="cuda")
+        # the tuner's choice on this batch, forced so that no tuning launches
+        # come before the captured ones: list items of 32 KiB, 128 threads
+        vbyte.debug_force_plan(1, 32 << 10, 128)
+        plan = vbyte.Plan(d, dbo, dvo, n, True, prev=dp, out=out)
+        vbyte.debug_force_plan(-1)
+        for _ in range(launches):
+            plan.launch()
+        torch.cuda.synchronize()
+        st = plan.get_status()
+        info = {"nbytes": int(hb.size), "n": n, "plan": plan.describe()}
+    elif case == "encode_delta_geometric_2^26":
+        x = np.cumsum(inputs.geometric_gaps(1 << 26, seed=0).astype(np.uint64)).astype(np.uint32)
+        dx = torch.from_numpy(x.view(np.int32)).cuda()
+        buf = torch.empty(5 * x.size, dtype=torch.uint8, device="cuda")
+        nb = torch.empty(1, dtype=torch.int64, device="cuda")
+        for _ in range(launches):
+            vbyte.encode_device(dx, delta=True, out=buf, nbytes=nb)
+        torch.cuda.synchronize()
+        st = vbyte.get_status()
+        info = {"n": int(x.size), "nbytes": int(nb.item())}
+    else:
+        n = 1 << 26
+        if case == "decode64_geometric_ids_2^26":
+            x = np.cumsum(inputs.geometric_gaps(n, seed=0).astype(np.uint64)) + np.uint64(1 << 40)
+            host, delta = vbyte.encode_delta64(x), True
+        else:
+            x, delta = inputs.uniform_bits64(n, seed=1), False
+            host = vbyte.encode64(x)
+        d = torch.from_numpy(host).cuda()
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+        for _ in range(launches):
+            (vbyte.decode_delta64 if delta else vbyte.decode64)(d, n, out=out)
+        torch.cuda.synchronize()
+        st = vbyte.get_status()
+        info = {"n": n, "nbytes": int(host.size), "delta": delta}
+    print(json.dumps({"profile_case": case, "launches": launches, "status": st, **info}))
+    if st:
+        raise SystemExit(1)
+
+
 def run_profile_case(args):
     """One small stream decoded a few times (the command ncu captures)."""
     import torch
     from paper_1503_07387_gb300 import vbyte
+    if args.profile_case in OTHER_PROFILE_CASES:
+        _profile_other(args)
+        return
     gen, n, delta, *seed = PROFILE_CASES[args.profile_case]
     v = getattr(inputs, gen)(n, seed=seed[0] if seed else 0)
     b = vbyte.encode(v)
@@ -1012,7 +1076,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE)
     ap.add_argument("--passes", type=int, choices=[0, 1, 2, 3], default=0,
                     help="single-stream kernel: 1 single pass, 2 count then decode, 3 split, 0 the library default")
-    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None)
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES) + OTHER_PROFILE_CASES, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--e2e-steps", type=int, default=5)

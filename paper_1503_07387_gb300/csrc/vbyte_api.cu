@@ -113,8 +113,8 @@ int forced_passes() { return g_passes.load(); }
 // The kernel for a single stream, by the mean code length nbytes / n (a
 // length class) and the size, from measurements on GB300 (2^26..2^28
 // values): small inputs take the single pass (fewest launches), one-byte
-// codes count-then-decode in one launch, long differential codes the
-// single pass, the rest the split launches.
+// codes count-then-decode in one launch (the input read once), the rest the
+// split launches.
 int choose_passes(size_t nbytes, size_t n, bool delta)
 {
     const int f = forced_passes();
@@ -122,7 +122,6 @@ int choose_passes(size_t nbytes, size_t n, bool delta)
     if (nbytes < (size_t(16) << 20) || n == 0) return 1;
     const double mean = static_cast<double>(nbytes) / static_cast<double>(n);
     if (mean < 1.1) return 2;
-    if (delta && mean > 2.5) return 1;
     return 3;
 }
 

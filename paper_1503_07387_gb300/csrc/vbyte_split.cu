@@ -912,6 +912,242 @@ __global__ void __launch_bounds__(kThreads, 5) decode_kernel(const Params p)
     cp_async_wait_all();
 }
 
+// ---- decode in 1 KiB warp steps (the stream decode launch)
+//
+// A warp step is 1 KiB of a warp tile, 32 bytes per lane, loaded straight
+// into registers one step ahead: no shared-memory staging of the input.
+// Each lane's values come from its eight words and the four bytes before
+// them; they are staged, with running sums in differential mode, at their
+// output positions -- step rank r at position s = r + sh, sh the output
+// misalignment of the step's first value -- so that every output quad is one
+// aligned 16-byte load, and one padding quad follows every 32 positions, so
+// that lanes whose runs start 32 positions apart write different banks.  The
+// launch's warps take the warp tiles of its interval round-robin; a tile's
+// prefix comes from the count and scan launches.  A step of one-byte
+// integers only is staged as bytes and written by the byte copy-out.
+
+constexpr int kW2 = 4;                               // warps per CTA
+constexpr int kThreads2 = kW2 * kLanes;
+constexpr int kStep = 1024;                          // bytes per warp step
+constexpr int kPos = kStep + 8;                      // positions: sh, the values, the last quad
+constexpr int kVals2 = kPos + 4 * (kPos / 32 + 1);   // padded words per warp
+static_assert(kVals2 * 4 >= 16 + kStep + 16, "the byte stage fits the value buffer");
+
+__device__ __forceinline__ uint32_t pidx(uint32_t s) { return s + ((s >> 5) << 2); }
+
+struct Step2 {
+    uint4 a, b;        // the lane's 32 bytes
+    uint32_t before;   // lane 0, first step of a tile: the 4 bytes before the tile (0 before tile 0)
+};
+
+__device__ __forceinline__ void load_step(const Params &p, uint64_t t, int h, int lane, uintptr_t lo, uintptr_t hi,
+                                          Step2 &st)
+{
+    const bool in = interior(p, t);
+    const uintptr_t va = p.base + (static_cast<uintptr_t>(t) << 11) + h * kStep + lane * 32;
+    st.a = load_slice(va, in, lo, hi);
+    st.b = load_slice(va + 16, in, lo, hi);
+    st.before = 0u;
+    if (h == 0 && lane == 0 && t > 0) st.before = __ldg(reinterpret_cast<const uint32_t *>(va - 4));
+}
+
+// Exclusive warp scan; *tot gets the warp's total.
+__device__ __forceinline__ uint32_t warp_excl(uint32_t x, int lane, uint32_t *tot)
+{
+    const uint32_t inc = warp_incl_scan(x, lane);
+    *tot = __shfl_sync(~0u, inc, 31);
+    return inc - x;
+}
+
+template <bool kDelta, bool kRank>
+__global__ void __launch_bounds__(kThreads2, 8) decode2_kernel(const Params p, uint64_t tb, uint64_t te)
+{
+    __shared__ __align__(16) uint32_t Vs[kW2][kVals2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *const V = Vs[warp];
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p.in);
+    const uintptr_t hi = lo + p.nbytes;
+    const uint64_t NW = static_cast<uint64_t>(gridDim.x) * kW2;
+    const uint64_t t0 = tb + static_cast<uint64_t>(blockIdx.x) * kW2 + warp;
+    if (t0 >= te) return;
+    const uint64_t K = 2 * ((te - t0 + NW - 1) / NW);   // steps of this warp
+    const uint32_t out_word = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.out) >> 2);
+    const long long n = static_cast<long long>(p.n);
+    Step2 cur, nxt;
+    load_step(p, t0, 0, lane, lo, hi, nxt);
+    uint2 e_nxt = p.ent[t0];
+    uint4 c_nxt = p.cpre[static_cast<uint32_t>(t0) / p.T];
+    unsigned long long R = 0;   // rank of the step's first value
+    uint32_t X = 0;             // running x before it
+    uint32_t last = 0;          // the previous step's last word (lane 31), same tile
+    for (uint64_t k = 0; k < K; ++k) {
+        const uint64_t t = t0 + (k >> 1) * NW;
+        const int h = static_cast<int>(k & 1u);
+        cur = nxt;
+        if (h == 0) {
+            R = (c_nxt.x | (static_cast<unsigned long long>(c_nxt.y) << 32)) + e_nxt.x;
+            X = c_nxt.z + e_nxt.y;
+        }
+        if (k + 1 < K) {   // the next step's bytes (and the next tile's prefix) travel meanwhile
+            const uint64_t tn = t0 + ((k + 1) >> 1) * NW;
+            load_step(p, tn, static_cast<int>((k + 1) & 1u), lane, lo, hi, nxt);
+            if (h == 1) {
+                e_nxt = p.ent[tn];
+                c_nxt = p.cpre[static_cast<uint32_t>(tn) / p.T];
+            }
+        }
+        const bool in = interior(p, t);
+        uint32_t wprev = __shfl_up_sync(~0u, cur.b.w, 1);
+        if (lane == 0) wprev = h ? last : cur.before;
+        last = __shfl_sync(~0u, cur.b.w, kLanes - 1);
+        const uintptr_t va = p.base + (static_cast<uintptr_t>(t) << 11) + h * kStep + lane * 32;
+        const uint32_t tlA = term4(cur.a.x) | (term4(cur.a.y) << 4) | (term4(cur.a.z) << 8) | (term4(cur.a.w) << 12);
+        const uint32_t tlB = term4(cur.b.x) | (term4(cur.b.y) << 4) | (term4(cur.b.z) << 8) | (term4(cur.b.w) << 12);
+        const uint32_t tcA = in ? tlA : (tlA & slice_valid(va, lo, hi));
+        const uint32_t tcB = in ? tlB : (tlB & slice_valid(va + 16, lo, hi));
+        const uint32_t t20A = term4(wprev) | (tlA << 4);
+        const uint32_t t20B = (tlA >> 12) | (tlB << 4);
+        const uint32_t cnt = __popc(tcA) + __popc(tcB);
+        uint32_t wc;
+        const uint32_t base = warp_excl(cnt, lane, &wc);
+        const uint32_t sh = (out_word + static_cast<uint32_t>(R)) & 3u;
+        uint32_t ws = 0;
+        const bool one = in && (tlA & tlB) == 0xFFFFu && !(wprev & 0x80000000u);
+        if (__all_sync(~0u, one) && static_cast<long long>(R) + kStep <= n) {
+            // one-byte integers only: the bytes themselves, written by the byte
+            // copy-out (two 512-byte halves), with the 4 bytes before them
+            uint8_t *const sb = reinterpret_cast<uint8_t *>(V) + 16;
+            *reinterpret_cast<uint4 *>(sb + 32 * lane) = cur.a;
+            *reinterpret_cast<uint4 *>(sb + 32 * lane + 16) = cur.b;
+            if (lane == 0) reinterpret_cast<uint32_t *>(sb)[-1] = wprev;
+            uint32_t s0 = 0;
+            if (kDelta) {
+                const uint32_t bs = byte_sum4(cur.a) + byte_sum4(cur.b);
+                const uint32_t inc = warp_incl_scan(bs, lane);
+                s0 = __shfl_sync(~0u, inc, 15);   // the first half's sum
+                ws = __shfl_sync(~0u, inc, 31);
+            }
+            __syncwarp();
+            uint32_t *const oq = p.out + (static_cast<long long>(R) - sh);
+            const uint32_t rb = static_cast<uint32_t>(R);
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t *const o = oq + half * (kStep / 2);
+                const uint8_t *const wb = sb + half * (kStep / 2);
+                const uint32_t ad = kDelta ? X + (half ? s0 : 0u) : 0u;
+                const uint32_t r0 = rb + half * (kStep / 2);
+                switch (sh) {
+                case 0: emit_bytes_a<0, kDelta, kRank>(o, wb, ad, r0, lane); break;
+                case 1: emit_bytes_a<1, kDelta, kRank>(o, wb, ad, r0, lane); break;
+                case 2: emit_bytes_a<2, kDelta, kRank>(o, wb, ad, r0, lane); break;
+                default: emit_bytes_a<3, kDelta, kRank>(o, wb, ad, r0, lane); break;
+                }
+            }
+        } else {
+            uint32_t s = sh + base;   // the lane's next position
+            const uint32_t c20A = ~t20A & 0xFFFFFu, c20B = ~t20B & 0xFFFFFu;
+            const bool le2 = !((c20A & (c20A << 1) & 0xFFFF8u) | (c20B & (c20B << 1) & 0xFFFF8u));
+            if (__all_sync(~0u, le2)) {
+                // codes of at most two bytes: the lane's sum by the byte-weight
+                // formula, then the values (running sums) in one SWAR pass
+                uint32_t run = 0;
+                if (kDelta) {
+                    const uint32_t vs = in ? sum_le2_fast(cur.a, wprev) + sum_le2_fast(cur.b, cur.a.w)
+                                           : sum_le2(cur.a, wprev, tcA) + sum_le2(cur.b, cur.a.w, tcB);
+                    run = warp_excl(vs, lane, &ws);
+                }
+                const uint32_t w8[8] = {cur.a.x, cur.a.y, cur.a.z, cur.a.w, cur.b.x, cur.b.y, cur.b.z, cur.b.w};
+                const uint32_t tc = tcA | (tcB << 16);
+                uint32_t wp = wprev;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const Pairs pr = pairs_le2(wp, w8[j]);
+                    uint32_t q01 = prmt(pr.lob, pr.hib, 0x5140u);
+                    uint32_t q23 = prmt(pr.lob, pr.hib, 0x7362u);
+                    q01 -= (q01 & 0xFF00FF00u) >> 1;
+                    q23 -= (q23 & 0xFF00FF00u) >> 1;
+                    const uint32_t v4[4] = {q01 & 0xFFFFu, q01 >> 16, q23 & 0xFFFFu, q23 >> 16};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if ((tc >> (4 * j + i)) & 1u) {
+                            run += v4[i];
+                            V[pidx(s)] = kDelta ? run : v4[i];
+                            ++s;
+                        }
+                    }
+                    wp = w8[j];
+                }
+            } else if (in && !__any_sync(~0u, dense_words(tlA) | dense_words(tlB))) {
+                // codes in separate words: every word's value in registers
+                uint32_t vA[4], vB[4];
+                const uint32_t nz = words4(wprev, cur.a, tlA, t20A, vA) | (words4(cur.a.w, cur.b, tlB, t20B, vB) << 4);
+                const uint32_t v8[8] = {vA[0], vA[1], vA[2], vA[3], vB[0], vB[1], vB[2], vB[3]};
+                uint32_t run = 0;
+                if (kDelta) {
+                    uint32_t vs = 0;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) vs += ((nz >> j) & 1u) ? v8[j] : 0u;
+                    run = warp_excl(vs, lane, &ws);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if ((nz >> j) & 1u) {
+                        run += v8[j];
+                        V[pidx(s)] = kDelta ? run : v8[j];
+                        ++s;
+                    }
+                }
+            } else {
+                // anything else: one terminator at a time, then running sums
+                uint32_t vs = 0;
+                auto put = [&](uint32_t v) {
+                    V[pidx(s)] = v;
+                    ++s;
+                    vs += v;
+                };
+                assemble_regs(wprev, cur.a, tlA, t20A, tcA, put);
+                assemble_regs(cur.a.w, cur.b, tlB, t20B, tcB, put);
+                if (kDelta) {
+                    uint32_t run = warp_excl(vs, lane, &ws);
+                    for (uint32_t q = sh + base; q < s; ++q) {
+                        run += V[pidx(q)];
+                        V[pidx(q)] = run;
+                    }
+                }
+            }
+            __syncwarp();
+            // copy-out: positions [sh, sh + lim) hold ranks [0, lim)
+            const long long room = n - static_cast<long long>(R);
+            const uint32_t lim = room < static_cast<long long>(wc) ? (room > 0 ? static_cast<uint32_t>(room) : 0u)
+                                                                    : wc;
+            const uint32_t np = sh + lim;
+            const uint32_t nq = (np + 3u) >> 2;
+            uint32_t *const oq = p.out + (static_cast<long long>(R) - sh);
+            const uint32_t ad = kDelta ? X : 0u;
+            for (uint32_t q = lane; q < nq; q += kLanes) {
+                uint4 e = *reinterpret_cast<const uint4 *>(V + pidx(4 * q));
+                uint32_t a0 = ad;
+                if (kRank) a0 += static_cast<uint32_t>(R) + 4 * q - sh;
+                e.x += a0;
+                e.y += a0 + (kRank ? 1u : 0u);
+                e.z += a0 + (kRank ? 2u : 0u);
+                e.w += a0 + (kRank ? 3u : 0u);
+                if (4 * q >= sh && 4 * q + 4 <= np) {
+                    st_quad(oq + 4 * q, e);
+                } else {
+                    const uint32_t ev[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (4 * q + j >= sh && 4 * q + j < np) oq[4 * q + j] = ev[j];
+                }
+            }
+        }
+        R += wc;
+        X += ws;
+        __syncwarp();   // the value buffer is free again
+    }
+}
+
 // ---- batched lists as work items (tuned plans)
 //
 // A plan cuts the batch into items: a whole list of at most C bytes, or a
@@ -1138,7 +1374,8 @@ Layout layout(uint64_t nwt, uint64_t G, bool d4)
 
 struct Dev {
     int sms = 0;
-    int occ = 0;
+    int occ = 0;    // resident CTAs per SM of decode_kernel (the count launch's ranges follow it)
+    int occ2 = 0;   // ... of decode2_kernel
 };
 std::mutex g_mu;
 std::map<int, Dev> g_dev;
@@ -1153,9 +1390,22 @@ int dev_info(Dev *out)
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return VBYTE_ECUDA;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ, decode_kernel<true, false>, kThreads, 0);
         d.occ = std::max(d.occ, 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ2, decode2_kernel<true, false>, kThreads2, 0);
+        d.occ2 = std::max(d.occ2, 1);
     }
     *out = d;
     return VBYTE_OK;
+}
+
+// The stream decode launch over warp tiles [tb, te): persistent CTAs, at
+// most one wave.
+template <bool kDelta, bool kRank>
+void launch_decode2(const Params &p, const Dev &di, uint64_t tb, uint64_t te, cudaStream_t s)
+{
+    if (te <= tb) return;
+    const uint64_t want = (te - tb + kW2 - 1) / kW2;
+    const unsigned g = static_cast<unsigned>(std::min<uint64_t>(want, static_cast<uint64_t>(di.sms) * di.occ2));
+    decode2_kernel<kDelta, kRank><<<g, kThreads2, 0, s>>>(p, tb, te);
 }
 
 }  // namespace sp
@@ -1337,10 +1587,11 @@ int decode_host_pipelined(const uint8_t *h_in, size_t nbytes, uint32_t *h_out, s
         if (cudaMemcpyAsync(P->h_after + i, carry, 8, cudaMemcpyDeviceToHost, P->work) != cudaSuccess)
             return VBYTE_ECUDA;
         if (cudaEventRecord(P->ev[K + i], P->work) != cudaSuccess) return VBYTE_ECUDA;
+        const uint64_t tb = r0 * p.T, te = std::min<uint64_t>(r1 * p.T, p.nwt);
         if (delta)
-            sp::decode_kernel<true, false><<<g, sp::kThreads, 0, P->work>>>(p);
+            sp::launch_decode2<true, false>(p, di, tb, te, P->work);
         else
-            sp::decode_kernel<false, false><<<g, sp::kThreads, 0, P->work>>>(p);
+            sp::launch_decode2<false, false>(p, di, tb, te, P->work);
         if (cudaEventRecord(P->ev[2 * K + i], P->work) != cudaSuccess) return VBYTE_ECUDA;
     }
     if (cudaGetLastError() != cudaSuccess) return VBYTE_ECUDA;
@@ -1385,7 +1636,7 @@ int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
     uint64_t T = std::max<uint64_t>(1, (nwt + target - 1) / target);
     T = std::min<uint64_t>(T, sp::kMaxT);
     const uint64_t G = (nwt + T - 1) / T;
-    if (G > sp::max_ranges(nwt)) return VBYTE_EINVAL;
+    if (G > sp::max_ranges(nwt) || nwt >= (uint64_t(1) << 32)) return VBYTE_EINVAL;   // 32-bit tile indices
     const sp::Layout L = sp::layout(nwt, G, d4);
     sp::Params p = {};
     p.in = in;
@@ -1420,16 +1671,16 @@ int enqueue_split(const uint8_t *in, size_t nbytes, uint32_t *out, size_t n, boo
         sp::count_kernel<false, false><<<static_cast<unsigned>(G), sp::kThreads, 0, s>>>(p);
     sp::scan_kernel<<<1, sp::kScanThreads, 0, s>>>(p);
     const unsigned g = static_cast<unsigned>(G);
-    if (rank)
-        sp::decode_kernel<true, true><<<g, sp::kThreads, 0, s>>>(p);
+    if (rank)   // the gaps-minus-one variant: no table-driven instance
+        sp::launch_decode2<true, true>(p, di, 0, nwt, s);
     else if (table && delta)
         sp::decode_kernel<true, false, false, true><<<g, sp::kThreads, sizeof(sp::TableSmem), s>>>(p);
     else if (table)
         sp::decode_kernel<false, false, false, true><<<g, sp::kThreads, sizeof(sp::TableSmem), s>>>(p);
     else if (delta)
-        sp::decode_kernel<true, false><<<g, sp::kThreads, 0, s>>>(p);
+        sp::launch_decode2<true, false>(p, di, 0, nwt, s);
     else
-        sp::decode_kernel<false, false><<<g, sp::kThreads, 0, s>>>(p);
+        sp::launch_decode2<false, false>(p, di, 0, nwt, s);
     return cudaGetLastError() == cudaSuccess ? VBYTE_OK : VBYTE_ECUDA;
 }
 

@@ -168,12 +168,12 @@ def test_plain_c_consumer(tmp_path):
 def test_kernel_choice_by_length_class():
     """The single-stream kernel the library picks (host logic, no GPU): the
     single pass for inputs under 16 MiB, count-then-decode for one-byte codes,
-    the single pass for long differential codes, the split launches else; a
+    the split launches else (long codes too, plain and differential); a
     forced choice wins until it is cleared."""
     M = 1 << 20
     assert vbyte.chosen_passes(4 * M, 3 * M, False) == 1
     assert vbyte.chosen_passes(64 * M, 64 * M, True) == 2
-    assert vbyte.chosen_passes(300 * M, 60 * M, True) == 1
+    assert vbyte.chosen_passes(300 * M, 60 * M, True) == 3
     assert vbyte.chosen_passes(300 * M, 60 * M, False) == 3
     assert vbyte.chosen_passes(96 * M, 64 * M, True) == 3
     try:

@@ -12,11 +12,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(autouse=True, params=[1, 2, 3], ids=["onepass", "twopass", "split"])
+@pytest.fixture(autouse=True, params=[1, 2, 3, 4], ids=["onepass", "twopass", "split", "split_table"])
 def kernel(request):
     """Every test runs on each single-stream kernel: the single pass with a
     decoupled look-back, count-then-decode in one launch, and the split
-    count / scan / decode launches."""
+    count / scan / decode launches (4: the table-driven setting, which this
+    variant must ignore)."""
     vbyte.debug_force_passes(request.param)
     yield request.param
     vbyte.debug_force_passes(0)
