@@ -1074,8 +1074,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE)
-    ap.add_argument("--passes", type=int, choices=[0, 1, 2, 3], default=0,
-                    help="single-stream kernel: 1 single pass, 2 count then decode, 3 split, 0 the library default")
+    ap.add_argument("--passes", type=int, choices=[0, 1, 2, 3, 4], default=0,
+                    help="single-stream kernel: 1 single pass, 2 count then decode, 3 split, "
+                         "4 split with the table-driven step, 0 the library default")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES) + OTHER_PROFILE_CASES, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)

@@ -111,11 +111,14 @@ __device__ __forceinline__ uint32_t term4(uint32_t w)
 // number), and the groups that belong to earlier integers fall off the low
 // end with one funnel shift.  For L = 5 the top of x lands above bit 31 and is
 // dropped: Algorithm 1's b * 2^28 modulo 2^32.
+// The fields joined at each step are disjoint, so they are added rather than
+// or-ed: the additions can run on the multiply-add pipe, the shifts and masks
+// on the integer ALU pipe, which bounds the decoders.
 __device__ __forceinline__ uint32_t assemble(uint32_t lo4, uint32_t x, int L)
 {
-    const uint32_t t = (lo4 & 0x007F007Fu) | ((lo4 >> 1) & 0x3F803F80u);
-    const uint32_t u = (t & 0x00003FFFu) | ((t >> 2) & 0x0FFFC000u);
-    return __funnelshift_r(u | (x << 28), x >> 4, 35 - 7 * L);
+    const uint32_t t = (lo4 & 0x007F007Fu) + ((lo4 >> 1) & 0x3F803F80u);
+    const uint32_t u = (t & 0x00003FFFu) + ((t >> 2) & 0x0FFFC000u);
+    return __funnelshift_r(u + x * (1u << 28), x >> 4, 35 - 7 * L);
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
@@ -290,7 +293,8 @@ __device__ __forceinline__ uint32_t words4(uint32_t wp, uint4 w, uint32_t tl, ui
         const uint32_t nib = (tl >> (4 * j)) & 0xFu;
         const int o4 = 31 - __clz(nib);   // the word's terminator (-1: none)
         const int L = min(4 + o4 - prev, 5);
-        const uint32_t sh = static_cast<uint32_t>(o4) & 3u;
+        // (a word with no terminator, o4 = -1, yields a value that is not used)
+        const uint32_t sh = static_cast<uint32_t>(o4);
         v[j] = assemble(__funnelshift_r(W[j], W[j + 1], 8 * sh), prmt(W[j + 1], 0u, 0x4440u | sh), L);
         nz |= (nib ? 1u : 0u) << j;
         prev = o4;

@@ -960,7 +960,7 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t x, int lane, uint32_t *to
 }
 
 template <bool kDelta, bool kRank>
-__global__ void __launch_bounds__(kThreads2, 8) decode2_kernel(const Params p, uint64_t tb, uint64_t te)
+__global__ void __launch_bounds__(kThreads2, 7) decode2_kernel(const Params p, uint64_t tb, uint64_t te)
 {
     __shared__ __align__(16) uint32_t Vs[kW2][kVals2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1003,8 +1003,11 @@ __global__ void __launch_bounds__(kThreads2, 8) decode2_kernel(const Params p, u
         const uintptr_t va = p.base + (static_cast<uintptr_t>(t) << 11) + h * kStep + lane * 32;
         const uint32_t tlA = term4(cur.a.x) | (term4(cur.a.y) << 4) | (term4(cur.a.z) << 8) | (term4(cur.a.w) << 12);
         const uint32_t tlB = term4(cur.b.x) | (term4(cur.b.y) << 4) | (term4(cur.b.z) << 8) | (term4(cur.b.w) << 12);
-        const uint32_t tcA = in ? tlA : (tlA & slice_valid(va, lo, hi));
-        const uint32_t tcB = in ? tlB : (tlB & slice_valid(va + 16, lo, hi));
+        uint32_t tcA = tlA, tcB = tlB;
+        if (!in) {   // warp-uniform: only the tiles at the stream's ends
+            tcA &= slice_valid(va, lo, hi);
+            tcB &= slice_valid(va + 16, lo, hi);
+        }
         const uint32_t t20A = term4(wprev) | (tlA << 4);
         const uint32_t t20B = (tlA >> 12) | (tlB << 4);
         const uint32_t cnt = __popc(tcA) + __popc(tcB);
@@ -1121,25 +1124,26 @@ __global__ void __launch_bounds__(kThreads2, 8) decode2_kernel(const Params p, u
             const uint32_t lim = room < static_cast<long long>(wc) ? (room > 0 ? static_cast<uint32_t>(room) : 0u)
                                                                     : wc;
             const uint32_t np = sh + lim;
-            const uint32_t nq = (np + 3u) >> 2;
+            const uint32_t qa = sh ? 1u : 0u;   // quads [qa, qb) are whole
+            const uint32_t qb = np >> 2;
             uint32_t *const oq = p.out + (static_cast<long long>(R) - sh);
             const uint32_t ad = kDelta ? X : 0u;
-            for (uint32_t q = lane; q < nq; q += kLanes) {
-                uint4 e = *reinterpret_cast<const uint4 *>(V + pidx(4 * q));
-                uint32_t a0 = ad;
-                if (kRank) a0 += static_cast<uint32_t>(R) + 4 * q - sh;
+            const uint32_t rk = static_cast<uint32_t>(R) - sh;   // kRank: position 0's rank
+            for (uint32_t q = qa + lane; q < qb; q += kLanes) {
+                uint4 e = *reinterpret_cast<const uint4 *>(V + 4 * q + ((q >> 3) << 2));
+                const uint32_t a0 = ad + (kRank ? rk + 4 * q : 0u);
                 e.x += a0;
                 e.y += a0 + (kRank ? 1u : 0u);
                 e.z += a0 + (kRank ? 2u : 0u);
                 e.w += a0 + (kRank ? 3u : 0u);
-                if (4 * q >= sh && 4 * q + 4 <= np) {
-                    st_quad(oq + 4 * q, e);
-                } else {
-                    const uint32_t ev[4] = {e.x, e.y, e.z, e.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (4 * q + j >= sh && 4 * q + j < np) oq[4 * q + j] = ev[j];
-                }
+                st_quad(oq + 4 * q, e);
+            }
+            // the positions outside whole quads: lanes 0..3 the first quad's,
+            // lanes 4..7 the last one's (when it is another quad)
+            if (lane < 8) {
+                const uint32_t ps = lane < 4 ? static_cast<uint32_t>(lane) : 4 * qb + lane - 4;
+                const bool edge = lane < 4 ? ps < 4 * qa || qb < qa : qb >= qa;
+                if (edge && ps >= sh && ps < np) oq[ps] = V[pidx(ps)] + ad + (kRank ? rk + ps : 0u);
             }
         }
         R += wc;
