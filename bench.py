@@ -7,8 +7,9 @@ two single streams of 2^28 uint32 each, resident in HBM --
     the paper's Sec. 2), about 0.375 GiB compressed;
   * uniform full-range uint32 (mostly five-byte codes), about 1.23 GiB --
 each decoded plainly and differentially (the same bytes read as gaps and
-prefix-summed back with uint32 wrap-around): four launches per step.  Inputs
-plus outputs exceed the 129 MB L2, so no flush is needed between steps.
+prefix-summed back with uint32 wrap-around): four decode calls per step,
+each the split decoder's count, scan and decode launches.  Inputs plus
+outputs exceed the 129 MB L2, so no flush is needed between steps.
 
 The same JSON line carries a block per other configuration, each with its own
 roofline and single-core oracle baseline: 10^6 plain values of every code
@@ -363,9 +364,9 @@ def time_streams(streams, steps: int, warmup: int, stream, ws: int = 1, sampler=
 
 
 def roofline_of(streams, launch_ms, peak, peak_source, src_hash, kernel):
-    """The dominant kernel's roofline over a step: algorithmic bytes (input
-    read once + 4 bytes per value written) per launch over its CUDA-event
-    duration, averaged over the step's launches."""
+    """The decoder's roofline over a step: algorithmic bytes (input read once
+    + 4 bytes per value written) per decode call over the call's CUDA-event
+    duration (all its launches), averaged over the step's calls."""
     nl = len(launch_ms)
     per_stream_ms = [sum(row[i] for row in launch_ms) / nl for i in range(len(streams))]
     algo = [int(s["host"].size) + 4 * s["n"] for s in streams]
@@ -387,6 +388,12 @@ def roofline_of(streams, launch_ms, peak, peak_source, src_hash, kernel):
             "frac_of_nominal_8000_gbs": round(achieved / NOMINAL_HBM_GBS, 4), "traffic": traffic,
             "kernel": kernel, "algorithmic_bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": round(avg_ms, 5), "kernel_source_hash": src_hash, "streams": rows}
+
+
+def launches_per_call(vbyte, s) -> int:
+    """Kernels one decode call of stream s launches: the split decoder's count,
+    scan and decode, else one (the workspace clears are memsets, not kernels)."""
+    return 3 if vbyte.chosen_passes(int(s["host"].size), s["n"], s["delta"]) in (3, 4) else 1
 
 
 def kernel_name(vbyte, streams):
@@ -415,6 +422,7 @@ def run_gpu(args):
 
     streams = _gpu_streams(args.workload)
     total_vals = sum(s["n"] for s in streams)
+    launches = sum(launches_per_call(vbyte, s) for s in streams)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.5)
@@ -497,7 +505,7 @@ def run_gpu(args):
         },
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": len(wl) * args.steps,
+        "gpu_launches": launches * args.steps,
         "warm": warm,
         "status": status,
         "clocks": clocks,
