@@ -270,6 +270,27 @@ __device__ __forceinline__ uint32_t sum_any_fast(uint4 w, uint32_t wp, uint32_t 
     return a0 + 127u * (a1 + 128u * (a2 + 128u * (a3 + 128u * a4)));
 }
 
+// One word c of a stream (pv the word before it): adds each byte's 7-bit
+// payload to a[0..k], k its place within its integer (the continuation bytes
+// right before it, at most four), for the bytes marked 0xFF in keep.  Summed
+// over the bytes of some integers, a[0] + 127 (a[1] + 128 (a[2] + 128 (a[3]
+// + 128 a[4]))) is the sum of their values modulo 2^32, since each payload p
+// at place k then counts p (1 + 127 (1 + 128 + ... + 128^(k-1))) = p 128^k.
+__device__ __forceinline__ void place_sums(uint32_t pv, uint32_t c, uint32_t keep, uint32_t (&a)[5])
+{
+    // 0xFF in byte b iff byte b-1 (b-2, b-3, b-4) continues: prmt replicates bit 7
+    const uint32_t m1 = prmt(__funnelshift_l(pv, c, 8), 0u, 0xBA98u);
+    const uint32_t m2 = m1 & prmt(__funnelshift_l(pv, c, 16), 0u, 0xBA98u);
+    const uint32_t m3 = m2 & prmt(__funnelshift_l(pv, c, 24), 0u, 0xBA98u);
+    const uint32_t m4 = m3 & prmt(pv, 0u, 0xBA98u);
+    const uint32_t P = c & keep & 0x7F7F7F7Fu;
+    a[0] = __dp4a(P, 0x01010101u, a[0]);
+    a[1] = __dp4a(P & m1, 0x01010101u, a[1]);
+    a[2] = __dp4a(P & m2, 0x01010101u, a[2]);
+    a[3] = __dp4a(P & m3, 0x01010101u, a[3]);
+    a[4] = __dp4a(P & m4, 0x01010101u, a[4]);
+}
+
 // Nonzero iff some 4-byte word of the slice holds two or more terminators
 // (tl: one bit per byte, four per word).
 __device__ __forceinline__ uint32_t dense_words(uint32_t tl)

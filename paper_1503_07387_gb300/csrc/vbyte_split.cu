@@ -202,6 +202,9 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
     uint32_t before = 0;
     if (lane == 0 && t > 0) before = __ldg(reinterpret_cast<const uint32_t *>(w0 - 4));
     uint32_t cnt = 0, sum = 0;
+    uint32_t wps[kUnits];                          // kDelta: the 4 bytes before each slice
+    uint32_t tl3 = 0;                              // kDelta: terminators of the last slice
+    bool all_le2 = true;                           // kDelta: codes of at most two bytes in every unit
     uint32_t ub = 0;                               // kD4: values of the tile's earlier units
     uint4 s4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
@@ -231,21 +234,44 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
         if (t == p.nwt - 1 && hi - 1 >= va && hi - 1 < va + kBPT && !((tl >> (hi - 1 - va)) & 1u))
             atomicOr(p.status, VBYTE_ERR_TRUNCATED);
         if (kDelta) {
-            // codes of at most two bytes, codes in separate words, any codes
-            // (warp-uniform choices), per-integer assembly at the stream's ends
-            const bool le2 = !(c20 & (c20 << 1) & 0xFFFF8u);
-            if (in && __all_sync(~0u, le2))
-                sum += sum_le2_fast(w[u], wp);
-            else if (in && !__any_sync(~0u, dense_words(tl))) {
-                uint32_t v[4];
-                const uint32_t nz = words4(wp, w[u], tl, t20, v);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) sum += ((nz >> j) & 1u) ? v[j] : 0u;
-            }
-            else if (in)
-                sum += sum_any_fast(w[u], wp, tl, t20);
-            else
+            wps[u] = wp;
+            if (u == kUnits - 1) tl3 = tl;
+            const bool le2 = __all_sync(~0u, !(c20 & (c20 << 1) & 0xFFFF8u));
+            all_le2 = all_le2 && le2;
+            if (!in)   // the stream's end tiles: per-integer assembly
                 assemble_regs(wp, w[u], tl, t20, tc, [&](uint32_t v) { sum += v; });
+        }
+    }
+    if (kDelta && in) {
+        if (all_le2) {
+            // codes of at most two bytes: the byte-weight formula per lane
+#pragma unroll
+            for (int u = 0; u < kUnits; ++u) sum += sum_le2_fast(w[u], wps[u]);
+        } else {
+            // any codes: every byte of the tile weighted by 128^place, with
+            // the bytes after the tile's last terminator (the next tile's
+            // first integer, lane 31's last slice) left out and the bytes
+            // before the tile that start its first integer (after the last
+            // terminator of the 4 bytes before it, lane 0) taken in
+            uint32_t a[5] = {0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int u = 0; u < kUnits; ++u) {
+                uint32_t keep = 0xFFFFu;
+                if (u == kUnits - 1 && lane == kLanes - 1) keep = tl3 ? (2u << (31 - __clz(tl3))) - 1u : 0u;
+                const uint32_t W4[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+                uint32_t pv = wps[u];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    place_sums(pv, W4[j], nibble_to_bytes((keep >> (4 * j)) & 0xFu), a);
+                    pv = W4[j];
+                }
+            }
+            if (lane == 0) {
+                const uint32_t tb = term4(before);
+                const uint32_t head = tb ? 0xFu & ~((2u << (31 - __clz(tb))) - 1u) : 0xFu;
+                place_sums(0u, before, nibble_to_bytes(head), a);
+            }
+            sum += a[0] + 127u * (a[1] + 128u * (a[2] + 128u * (a[3] + 128u * a[4])));
         }
     }
     cnt_out = __reduce_add_sync(~0u, cnt);
