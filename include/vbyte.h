@@ -294,6 +294,9 @@ int vbyte_decode_each(const uint8_t *d_in, const uint64_t *h_byte_off,
  * at most staging_bytes and the batch limits hold; up to max_inflight
  * batches run at once, each on its own stream, so queries that arrive while
  * others are on the GPU start as soon as a slot and arena space free up.
+ * While batches are in flight the scheduler thread polls their completion
+ * (yielding between polls, so it keeps one host core busy); with nothing in
+ * flight it sleeps until a query arrives or arena space is released.
  * per_list = 0: a batch is decoded in place with one set of launches -- its
  * lists become work items (a whole list, or a 32 KiB chunk of a long one)
  * that warps decode straight from the pool into the arena; per_list = 1 (a

@@ -91,6 +91,7 @@ struct vbyte_server {
     std::deque<uint64_t> pending;
     std::mutex mu;
     std::condition_variable cv;
+    std::condition_variable cv_work;   // the scheduler, idle: a query arrived, memory was released, or stop
     std::thread worker;
     std::atomic<bool> stop{false};
     int error = VBYTE_OK;
@@ -137,6 +138,7 @@ struct vbyte_server {
         if (it != blocks.end() && --it->second.refs == 0) {
             arena_free(it->second.off, it->second.size);
             blocks.erase(it);
+            cv_work.notify_one();   // admission may have been waiting for this memory
         }
     }
 
@@ -408,7 +410,20 @@ struct vbyte_server {
                     progress = true;
                 }
             }
-            if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
+            if (!progress) {
+                bool busy = false;
+                for (const Slot &sl : slots) busy = busy || sl.busy;
+                if (busy) {
+                    std::this_thread::yield();   // a batch in flight: poll its event again soon
+                } else {
+                    // nothing in flight: sleep until a query arrives or memory is
+                    // released (bounded, in case admission waits on something else)
+                    std::unique_lock<std::mutex> lk(mu);
+                    cv_work.wait_for(lk, std::chrono::milliseconds(1), [&] {
+                        return stop.load(std::memory_order_relaxed) || !pending.empty();
+                    });
+                }
+            }
         }
     }
 
@@ -431,6 +446,7 @@ struct vbyte_server {
         *qid = queries.size();
         queries.push_back(std::move(q));
         pending.push_back(*qid);
+        cv_work.notify_one();
         return VBYTE_OK;
     }
 };
@@ -595,7 +611,11 @@ int vbyte_server_stats(vbyte_server *srv, uint64_t *batches, uint64_t *queries, 
 void vbyte_server_destroy(vbyte_server *srv)
 {
     if (!srv) return;
-    srv->stop = true;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv_work.notify_all();
+    }
     if (srv->worker.joinable()) srv->worker.join();
     int cur = 0;
     cudaGetDevice(&cur);
