@@ -20,11 +20,13 @@
 //             the total count against n;
 //   decode64: per tile, every integer that ends in it, assembled from its own
 //             bytes (at most nine before its terminator; the 16 bytes staged
-//             ahead of the tile cover them), placed by a block scan of the
-//             per-thread counts into shared memory (one padding slot every
-//             16, so that a warp's stores do not share banks), prefix-summed
-//             there in delta mode, and written out with coalesced 8-byte
-//             stores.
+//             ahead of the tile cover them): codes of at most two bytes by
+//             byte pairs, longer ones from the eight bytes ending at the
+//             terminator compacted into 56 bits with SWAR steps; placed by a
+//             block scan of the per-thread counts into shared memory (one
+//             padding slot every 16, so that a warp's stores do not share
+//             banks), prefix-summed there in delta mode, and written out with
+//             coalesced 8-byte stores.
 // Tiles start at the input address rounded down to 16 bytes, so every
 // staged chunk is one aligned 16-byte load; bytes of a chunk outside the
 // input are staged as zero and never counted.
@@ -35,6 +37,7 @@
 
 #include "vbyte.h"
 #include "vbyte64.h"
+#include "vbyte_device.cuh"
 #include "vbyte_internal.h"
 
 namespace vbk {
@@ -114,44 +117,81 @@ __device__ __forceinline__ void stage(const Params &p, uint64_t t, uint8_t *byte
     }
 }
 
+// Four 7-bit payloads (the bytes of x) compacted into 28 bits, byte i at bit
+// 7 i (the fields are disjoint, so they are added).
+__device__ __forceinline__ uint32_t compact28(uint32_t x)
+{
+    const uint32_t t = (x & 0x007F007Fu) + ((x >> 1) & 0x3F803F80u);
+    return (t & 0x00003FFFu) + ((t >> 2) & 0x0FFFC000u);
+}
+
 // The integers that end in this thread's slice, tile bytes [16 tid, 16 tid +
-// 16), at tile positions in [a, b), in order: f(v) for each.  Each is
-// assembled from the high-bit bytes before its terminator, the first of them
-// possibly in the previous slice (or the halo).  Returns true if the slice
+// 16), at tile positions in [a, b), in order: f(v) for each (kValues).  They
+// come from a 32-byte window (the 16 bytes before the slice, possibly the
+// halo, and the slice) held in registers and masks: codes of at most two
+// bytes by byte pairs, any others one terminator at a time from the eight
+// bytes that end at it (and at most two more).  Returns whether the slice
 // holds a byte that makes a run of ten or more high-bit bytes.
 template <bool kValues, class F>
-__device__ __forceinline__ bool walk(const uint8_t *bytes, int tid, int a, int b, F &&f)
+__device__ __forceinline__ bool values64(const uint8_t *bytes, int tid, int a, int b, F &&f)
 {
-    const uint8_t *s = bytes + kHalo + kSlice * tid;
-    const uint4 q = *reinterpret_cast<const uint4 *>(s);
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-    // the high-bit bytes just before the slice (at most nine): the start of an
-    // integer that ends here; s[-1] holds its highest group of them
-    int r = 0;
-    uint64_t acc = 0;
+    const uint8_t *const wb = bytes + kHalo + kSlice * tid - 16;
+    const uint32_t *const ww = reinterpret_cast<const uint32_t *>(wb);
+    const uint4 pq = reinterpret_cast<const uint4 *>(wb)[0];
+    const uint4 q = reinterpret_cast<const uint4 *>(wb)[1];
+    const uint32_t W[8] = {pq.x, pq.y, pq.z, pq.w, q.x, q.y, q.z, q.w};
+    uint32_t T = 0;   // bit i: window byte i has the high bit clear
 #pragma unroll
-    for (int k = 1; k < kMaxLen; ++k) {
-        const uint32_t c = s[-k];
-        if (r == k - 1 && (c & 0x80u)) {
-            r = k;
-            if (kValues) acc = (acc << 7) | (c & 0x7Fu);
-        }
+    for (int k = 0; k < 8; ++k) T |= term4(W[k]) << (4 * k);
+    const uint32_t Cn = ~T;   // bit i: window byte i continues
+    // a run of ten continuation bytes ending in the slice (window bytes 16..31)
+    const uint32_t r2 = Cn & (Cn << 1), r4 = r2 & (r2 << 2), r8 = r4 & (r4 << 4);
+    const bool bad = (r8 & (r2 << 8) & 0xFFFF0000u) != 0;
+    if (!kValues) return bad;
+    const int s0 = kSlice * tid;
+    uint32_t tc = T >> 16;   // the slice's terminators inside the input
+    if (s0 < a || s0 + kSlice > b) {
+#pragma unroll
+        for (int j = 0; j < kSlice; ++j)
+            if (s0 + j < a || s0 + j >= b) tc &= ~(1u << j);
     }
-    bool bad = false;
+    if (!(r2 & 0xFFFF8000u)) {   // codes of at most two bytes
 #pragma unroll
-    for (int j = 0; j < kSlice; ++j) {
-        const uint32_t c = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-        if (c & 0x80u) {
-            if (kValues && r < kMaxLen) acc |= static_cast<uint64_t>(c & 0x7Fu) << (7 * r);   // shift <= 63
-            ++r;
-            bad |= (r >= kMaxLen);
-        } else {
-            if (kValues && r < kMaxLen) acc |= static_cast<uint64_t>(c) << (7 * r);
-            const int pos = kSlice * tid + j;
-            if (pos >= a && pos < b) f(acc);
-            acc = 0;
-            r = 0;
+        for (int j = 0; j < 4; ++j) {
+            const Pairs pr = pairs_le2(W[3 + j], W[4 + j]);
+            uint32_t q01 = prmt(pr.lob, pr.hib, 0x5140u);
+            uint32_t q23 = prmt(pr.lob, pr.hib, 0x7362u);
+            q01 -= (q01 & 0xFF00FF00u) >> 1;
+            q23 -= (q23 & 0xFF00FF00u) >> 1;
+            const uint32_t v4[4] = {q01 & 0xFFFFu, q01 >> 16, q23 & 0xFFFFu, q23 >> 16};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((tc >> (4 * j + i)) & 1u) f(static_cast<uint64_t>(v4[i]));
         }
+        return bad;
+    }
+    uint32_t m = tc;
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        const int Q = 16 + j;   // the terminator's window byte
+        const uint32_t below = T & ((1u << Q) - 1u);
+        const int L = below ? Q - (31 - __clz(below)) : Q + 1;   // over ten: malformed, the value unspecified
+        const int st = Q - 7;                                    // the first of the eight bytes ending at Q
+        const int w0 = st >> 2, sh = 8 * (st & 3);
+        const uint32_t A = ww[w0], B = ww[w0 + 1];
+        const uint32_t lo = __funnelshift_r(A, B, sh);
+        const uint32_t hi = sh ? __funnelshift_r(B, ww[w0 + 2], sh) : B;
+        // the eight payloads as 56 bits: group g is byte Q - 7 + g
+        const uint64_t c56 = compact28(lo) | (static_cast<uint64_t>(compact28(hi)) << 28);
+        uint64_t v;
+        if (L <= 8) {
+            v = c56 >> (7 * (8 - L));
+        } else {   // nine or ten bytes: the tenth group's top bits fall off (x 2^63 modulo 2^64)
+            v = (c56 << 7) | (wb[Q - 8] & 0x7Fu);
+            if (L >= 10) v = (v << 7) | (wb[Q - 9] & 0x7Fu);
+        }
+        f(v);
     }
     return bad;
 }
@@ -243,10 +283,8 @@ __global__ void __launch_bounds__(kThreads) count64_kernel(Params p)
         tile_range(p, t, &a, &b);
         uint32_t cnt = 0;
         uint64_t sum = 0;
-        const bool bad = walk<kDelta>(S.bytes, tid, a, b, [&](uint64_t v) {
-            ++cnt;
-            if (kDelta) sum += v;
-        });
+        cnt = slice_count(S.bytes, tid, a, b);
+        const bool bad = values64<kDelta>(S.bytes, tid, a, b, [&](uint64_t v) { sum += v; });
         if (bad) atomicOr(p.status, VBYTE_ERR_MALFORMED_LONG);
         if (t + 1 == p.ntiles && b - 1 >= kSlice * tid && b - 1 < kSlice * (tid + 1) &&
             (S.bytes[kHalo + b - 1] & 0x80u))
@@ -257,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) count64_kernel(Params p)
             S.wcnt[warp] = cnt;
             S.wsum[warp] = sum;
         }
-        __syncthreads();   // also: every walk of this tile is done before the next stage
+        __syncthreads();   // also: every slice of this tile is read before the next stage
         if (tid == 0) {
             uint64_t c = 0, s = 0;
 #pragma unroll
@@ -329,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) decode64_kernel(Params p)
         tile_range(p, t, &a, &b);
         uint32_t C = 0;
         uint32_t rank = block_excl<uint32_t>(slice_count(S.bytes, tid, a, b), S.wcnt, &C);
-        walk<true>(S.bytes, tid, a, b, [&](uint64_t v) { S.vals[slot(rank++)] = v; });
+        values64<true>(S.bytes, tid, a, b, [&](uint64_t v) { S.vals[slot(rank++)] = v; });
         __syncthreads();
         if (kDelta) {
             // running sums of the tile's integers from prev + everything before it
