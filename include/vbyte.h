@@ -146,7 +146,11 @@ int vbyte_encode_delta_m1_device(const uint32_t *d_in, size_t n, uint32_t prev,
  * number of values the caller expects (e.g. the posting-list length); a
  * different terminator count sets VBYTE_ERR_COUNT_MISMATCH.  n = 0 with
  * nbytes = 0 is a no-op.  Returns VBYTE_EINVAL for a null pointer with a
- * nonzero size or a d_out that is not 4-byte aligned. */
+ * nonzero size or a d_out that is not 4-byte aligned.  The library picks the
+ * kernel from the input size and mean code length (nbytes / n): a single
+ * launch with a decoupled look-back under 16 MiB, count then decode in one
+ * launch for one-byte codes, else separate count, scan and decode launches;
+ * all give the same values and status bits (vbyte_debug_force_passes). */
 int vbyte_decode(const uint8_t *d_in, size_t nbytes, uint32_t *d_out, size_t n,
                  void *stream);
 

@@ -9,22 +9,26 @@
 //   * The stream is cut into 2 KiB warp tiles aligned to 16 bytes in absolute
 //     address space (tile 0 starts at the input rounded down to 16 bytes).
 //     A warp tile owns the integers whose terminator byte lies in it and in
-//     the stream; it is four 512-byte units, one 16-byte slice per lane.
-//   * CTA c of the count and the decode launch owns the contiguous warp
-//     tiles [c T, (c + 1) T); its warps take every eighth tile.
-//   * count: per warp tile, its integers and (delta) their sum -- a popc of
-//     the terminator mask and, for the sum, the byte-weight formula for codes
-//     of at most two bytes or per-integer assembly.  The CTA scans its range
-//     in shared memory and writes, per tile, the count and sum of the range's
-//     tiles before it, and the range's totals.  The data-error contract is
-//     checked here.
+//     the stream.
+//   * count: CTA c owns the contiguous warp tiles [c T, (c + 1) T) (a range);
+//     its warps take every eighth tile, four 512-byte units of one 16-byte
+//     slice per lane.  Per warp tile, its integers and (delta) their sum -- a
+//     popc of the terminator mask and, for the sum, the byte-weight formula
+//     for codes of at most two bytes, else every byte weighted by 128^place
+//     with the tile's two ends corrected (no assembly).  The CTA scans its
+//     range in shared memory and writes, per tile, the count and sum of the
+//     range's tiles before it, and the range's totals.  The data-error
+//     contract is checked here.
 //   * scan: one CTA turns the range totals into each range's prefix: values
 //     before it and the running x before it (from prev).
-//   * decode: every warp on its own.  Its units travel through a ring of
-//     four shared-memory buffers with cp.async (three units ahead), each
-//     unit is decoded into the warp's value buffer (one-byte units stay as
-//     bytes) and written out with coalesced 16-byte stores.  No CTA barrier
-//     after the start, no wait on another CTA.
+//   * decode (decode2_kernel): persistent CTAs whose warps take warp tiles
+//     round-robin and work alone -- no CTA barrier, no wait on another CTA.
+//     A step is 1 KiB (32 bytes per lane), loaded into registers a step
+//     ahead; values are staged at their output positions in a padded
+//     per-warp buffer and written with coalesced 16-byte stores.  The
+//     blocked-difference and table-driven settings keep the earlier launch
+//     (decode_kernel: 512-byte units through a cp.async ring), whose unit
+//     functions the batched list items also use.
 // The input is read twice (count, decode); the per-tile words add 8 bytes per
 // 2 KiB.
 #include <cuda_runtime.h>
