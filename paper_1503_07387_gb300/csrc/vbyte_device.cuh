@@ -111,14 +111,18 @@ __device__ __forceinline__ uint32_t term4(uint32_t w)
 // number), and the groups that belong to earlier integers fall off the low
 // end with one funnel shift.  For L = 5 the top of x lands above bit 31 and is
 // dropped: Algorithm 1's b * 2^28 modulo 2^32.
-// The fields joined at each step are disjoint, so they are added rather than
-// or-ed: the additions can run on the multiply-add pipe, the shifts and masks
-// on the integer ALU pipe, which bounds the decoders.
+// The compaction runs scaled by 8 (each step moves the lower field up rather
+// than the upper one down), so that its joins are multiply-adds, which run on
+// the multiply-add pipe while the masks and shifts use the integer ALU pipe
+// that bounds the decoders: 2t = 2 (lo4 & 0x007F007F) + (lo4 & 0x7F007F00),
+// 8u = 4 (2t & 0x7FFE) + (2t & 0x7FFE0000) with u the 28-bit compaction, and
+// the 38-bit number 8 (u + x 2^28) is split into its low word
+// 8u + (x & 1) 2^31 (8u < 2^31) and its high word x >> 1.
 __device__ __forceinline__ uint32_t assemble(uint32_t lo4, uint32_t x, int L)
 {
-    const uint32_t t = (lo4 & 0x007F007Fu) + ((lo4 >> 1) & 0x3F803F80u);
-    const uint32_t u = (t & 0x00003FFFu) + ((t >> 2) & 0x0FFFC000u);
-    return __funnelshift_r(u + x * (1u << 28), x >> 4, 35 - 7 * L);
+    const uint32_t t2 = (lo4 & 0x007F007Fu) * 2u + (lo4 & 0x7F007F00u);
+    const uint32_t u8 = (t2 & 0x00007FFEu) * 4u + (t2 & 0x7FFE0000u);
+    return __funnelshift_r(u8 + x * 0x80000000u, x >> 1, 38 - 7 * L);
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane)
@@ -270,25 +274,32 @@ __device__ __forceinline__ uint32_t sum_any_fast(uint4 w, uint32_t wp, uint32_t 
     return a0 + 127u * (a1 + 128u * (a2 + 128u * (a3 + 128u * a4)));
 }
 
-// One word c of a stream (pv the word before it): adds each byte's 7-bit
-// payload to a[0..k], k its place within its integer (the continuation bytes
-// right before it, at most four), for the bytes marked 0xFF in keep.  Summed
-// over the bytes of some integers, a[0] + 127 (a[1] + 128 (a[2] + 128 (a[3]
-// + 128 a[4]))) is the sum of their values modulo 2^32, since each payload p
-// at place k then counts p (1 + 127 (1 + 128 + ... + 128^(k-1))) = p 128^k.
-__device__ __forceinline__ void place_sums(uint32_t pv, uint32_t c, uint32_t keep, uint32_t (&a)[5])
+// 0xFF in each byte of w that has its high bit set (a continuation byte):
+// prmt replicates bit 7 of each byte.
+__device__ __forceinline__ uint32_t cont_bytes(uint32_t w) { return prmt(w, 0u, 0xBA98u); }
+
+// One word c of a stream (cpv = cont_bytes of the word before it): adds each
+// byte's 7-bit payload to a[0..k], k its place within its integer (the
+// continuation bytes right before it, at most four), for the bytes marked
+// 0xFF in keep; returns cont_bytes(c) for the next word.  Summed over the
+// bytes of some integers, a[0] + 127 (a[1] + 128 (a[2] + 128 (a[3] + 128
+// a[4]))) is the sum of their values modulo 2^32, since each payload p at
+// place k then counts p (1 + 127 (1 + 128 + ... + 128^(k-1))) = p 128^k.
+__device__ __forceinline__ uint32_t place_sums(uint32_t cpv, uint32_t c, uint32_t keep, uint32_t (&a)[5])
 {
-    // 0xFF in byte b iff byte b-1 (b-2, b-3, b-4) continues: prmt replicates bit 7
-    const uint32_t m1 = prmt(__funnelshift_l(pv, c, 8), 0u, 0xBA98u);
-    const uint32_t m2 = m1 & prmt(__funnelshift_l(pv, c, 16), 0u, 0xBA98u);
-    const uint32_t m3 = m2 & prmt(__funnelshift_l(pv, c, 24), 0u, 0xBA98u);
-    const uint32_t m4 = m3 & prmt(pv, 0u, 0xBA98u);
+    const uint32_t cc = cont_bytes(c);
+    // 0xFF in byte b iff byte b-1 (b-1 and b-2, ..., b-1 .. b-4) continues
+    const uint32_t m1 = __funnelshift_l(cpv, cc, 8);
+    const uint32_t m2 = m1 & __funnelshift_l(cpv, cc, 16);
+    const uint32_t m3 = m2 & __funnelshift_l(cpv, cc, 24);
+    const uint32_t m4 = m3 & cpv;
     const uint32_t P = c & keep & 0x7F7F7F7Fu;
     a[0] = __dp4a(P, 0x01010101u, a[0]);
     a[1] = __dp4a(P & m1, 0x01010101u, a[1]);
     a[2] = __dp4a(P & m2, 0x01010101u, a[2]);
     a[3] = __dp4a(P & m3, 0x01010101u, a[3]);
     a[4] = __dp4a(P & m4, 0x01010101u, a[4]);
+    return cc;
 }
 
 // Nonzero iff some 4-byte word of the slice holds two or more terminators

@@ -263,12 +263,9 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
                 uint32_t keep = 0xFFFFu;
                 if (u == kUnits - 1 && lane == kLanes - 1) keep = tl3 ? (2u << (31 - __clz(tl3))) - 1u : 0u;
                 const uint32_t W4[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-                uint32_t pv = wps[u];
+                uint32_t cpv = cont_bytes(wps[u]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    place_sums(pv, W4[j], nibble_to_bytes((keep >> (4 * j)) & 0xFu), a);
-                    pv = W4[j];
-                }
+                for (int j = 0; j < 4; ++j) cpv = place_sums(cpv, W4[j], nibble_to_bytes((keep >> (4 * j)) & 0xFu), a);
             }
             if (lane == 0) {
                 const uint32_t tb = term4(before);
