@@ -399,7 +399,7 @@ def launches_per_call(vbyte, s) -> int:
 def kernel_name(vbyte, streams):
     passes = {vbyte.chosen_passes(int(s["host"].size), s["n"], s["delta"]) for s in streams}
     names = {1: "onepass_kernel (single pass, decoupled look-back)", 2: "sdecode_kernel (count then decode)",
-             3: "sp::count_kernel + sp::decode_kernel (split)",
+             3: "sp::count_kernel + sp::scan_kernel + sp::decode2_kernel (split)",
              4: "sp::count_kernel + sp::decode_kernel (split, table-driven step)"}
     return " + ".join(names[p] for p in sorted(passes))
 
