@@ -236,6 +236,9 @@ __device__ __forceinline__ void assemble_regs(uint32_t wp, uint4 w, uint32_t tl,
     }
 }
 
+// 1 in each byte of w that has its high bit set (a continuation byte).
+__device__ __forceinline__ uint32_t cont_flags(uint32_t w) { return (w >> 7) & 0x01010101u; }
+
 // Sum of the values whose terminators lie in a thread's slice, without
 // assembling them, for codes of any length (every byte inside the stream):
 // each byte's 7-bit payload p times 128^k, k = its place within its integer
@@ -244,9 +247,11 @@ __device__ __forceinline__ void assemble_regs(uint32_t wp, uint4 w, uint32_t tl,
 // terminator before the slice through the slice's last terminator.  With
 // a_i = the sum of p over those bytes with k >= i, the sum is
 // a_0 + 127 (a_1 + 128 (a_2 + 128 (a_3 + 128 a_4))) modulo 2^32, since
-// 128^k = 1 + 127 (1 + 128 + ... + 128^(k-1)).  The bytes before the four
-// before the slice count as terminators, which holds in a well-formed
-// stream whenever it matters (a run of five continuation bytes is malformed).
+// 128^k = 1 + 127 (1 + 128 + ... + 128^(k-1)); a_1 + 128 a_2 and
+// a_3 + 128 a_4 are one byte dot product each (weights 0, 1 or 129, see
+// place_sums).  The bytes before the four before the slice count as
+// terminators, which holds in a well-formed stream whenever it matters (a
+// run of five continuation bytes is malformed).
 __device__ __forceinline__ uint32_t sum_any_fast(uint4 w, uint32_t wp, uint32_t tl, uint32_t t20)
 {
     if (!tl) return 0u;
@@ -255,50 +260,48 @@ __device__ __forceinline__ uint32_t sum_any_fast(uint4 w, uint32_t wp, uint32_t 
     const uint32_t st = low ? 32u - __clz(low) : 0u;        // first byte of the first value (t20 bits)
     const uint32_t mem = ((2u << (lt + 4u)) - 1u) & (~0u << st);
     const uint32_t W[5] = {wp, w.x, w.y, w.z, w.w};
-    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    uint32_t a0 = 0, a12 = 0, a34 = 0;
+    uint32_t cpv = 0u;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const uint32_t pv = i ? W[i - 1] : 0u;
         const uint32_t P = W[i] & 0x7F7F7F7Fu & nibble_to_bytes((mem >> (4 * i)) & 0xFu);
-        // 0xFF in byte b iff byte b-1 (b-2, b-3, b-4) continues: prmt replicates bit 7
-        const uint32_t m1 = prmt(__funnelshift_l(pv, W[i], 8), 0u, 0xBA98u);
-        const uint32_t m2 = m1 & prmt(__funnelshift_l(pv, W[i], 16), 0u, 0xBA98u);
-        const uint32_t m3 = m2 & prmt(__funnelshift_l(pv, W[i], 24), 0u, 0xBA98u);
-        const uint32_t m4 = m3 & prmt(pv, 0u, 0xBA98u);
+        const uint32_t cc = cont_flags(W[i]);
+        // 1 in byte b iff byte b-1 (b-1 and b-2, ..., b-1 .. b-4) continues
+        const uint32_t m1 = __funnelshift_l(cpv, cc, 8);
+        const uint32_t m2 = m1 & __funnelshift_l(cpv, cc, 16);
+        const uint32_t m3 = m2 & __funnelshift_l(cpv, cc, 24);
+        const uint32_t m4 = m3 & cpv;
         a0 = __dp4a(P, 0x01010101u, a0);
-        a1 = __dp4a(P & m1, 0x01010101u, a1);
-        a2 = __dp4a(P & m2, 0x01010101u, a2);
-        a3 = __dp4a(P & m3, 0x01010101u, a3);
-        a4 = __dp4a(P & m4, 0x01010101u, a4);
+        a12 = __dp4a(P, m2 * 128u + m1, a12);
+        a34 = __dp4a(P, m4 * 128u + m3, a34);
+        cpv = cc;
     }
-    return a0 + 127u * (a1 + 128u * (a2 + 128u * (a3 + 128u * a4)));
+    return a0 + 127u * (a12 + 16384u * a34);
 }
 
-// 0xFF in each byte of w that has its high bit set (a continuation byte):
-// prmt replicates bit 7 of each byte.
-__device__ __forceinline__ uint32_t cont_bytes(uint32_t w) { return prmt(w, 0u, 0xBA98u); }
-
-// One word c of a stream (cpv = cont_bytes of the word before it): adds each
-// byte's 7-bit payload to a[0..k], k its place within its integer (the
-// continuation bytes right before it, at most four), for the bytes marked
-// 0xFF in keep; returns cont_bytes(c) for the next word.  Summed over the
-// bytes of some integers, a[0] + 127 (a[1] + 128 (a[2] + 128 (a[3] + 128
-// a[4]))) is the sum of their values modulo 2^32, since each payload p at
-// place k then counts p (1 + 127 (1 + 128 + ... + 128^(k-1))) = p 128^k.
-__device__ __forceinline__ uint32_t place_sums(uint32_t cpv, uint32_t c, uint32_t keep, uint32_t (&a)[5])
+// One word c of a stream (cpv = cont_flags of the word before it): adds the
+// 7-bit payloads p of the bytes marked 0xFF in keep to a[0], p [k >= 1] +
+// 128 p [k >= 2] to a[1] and p [k >= 3] + 128 p [k >= 4] to a[2], k the
+// byte's place within its integer (the continuation bytes right before it,
+// at most four); returns cont_flags(c) for the next word.  Summed over the
+// bytes of some integers, a[0] + 127 (a[1] + 16384 a[2]) is the sum of their
+// values modulo 2^32, since each payload p at place k then counts
+// p (1 + 127 (1 + 128 + ... + 128^(k-1))) = p 128^k.  The place flags are
+// 0 or 1 per byte, so each pair of places is one byte dot product with
+// weights 0, 1 or 129 (place k >= 2 implies k >= 1), and the weight words
+// are multiply-adds.
+__device__ __forceinline__ uint32_t place_sums(uint32_t cpv, uint32_t c, uint32_t keep, uint32_t (&a)[3])
 {
-    const uint32_t cc = cont_bytes(c);
-    // 0xFF in byte b iff byte b-1 (b-1 and b-2, ..., b-1 .. b-4) continues
+    const uint32_t cc = cont_flags(c);
+    // 1 in byte b iff byte b-1 (b-1 and b-2, ..., b-1 .. b-4) continues
     const uint32_t m1 = __funnelshift_l(cpv, cc, 8);
     const uint32_t m2 = m1 & __funnelshift_l(cpv, cc, 16);
     const uint32_t m3 = m2 & __funnelshift_l(cpv, cc, 24);
     const uint32_t m4 = m3 & cpv;
     const uint32_t P = c & keep & 0x7F7F7F7Fu;
     a[0] = __dp4a(P, 0x01010101u, a[0]);
-    a[1] = __dp4a(P & m1, 0x01010101u, a[1]);
-    a[2] = __dp4a(P & m2, 0x01010101u, a[2]);
-    a[3] = __dp4a(P & m3, 0x01010101u, a[3]);
-    a[4] = __dp4a(P & m4, 0x01010101u, a[4]);
+    a[1] = __dp4a(P, m2 * 128u + m1, a[1]);
+    a[2] = __dp4a(P, m4 * 128u + m3, a[2]);
     return cc;
 }
 

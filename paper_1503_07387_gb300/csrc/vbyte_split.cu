@@ -257,13 +257,13 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
             // first integer, lane 31's last slice) left out and the bytes
             // before the tile that start its first integer (after the last
             // terminator of the 4 bytes before it, lane 0) taken in
-            uint32_t a[5] = {0u, 0u, 0u, 0u, 0u};
+            uint32_t a[3] = {0u, 0u, 0u};
 #pragma unroll
             for (int u = 0; u < kUnits; ++u) {
                 uint32_t keep = 0xFFFFu;
                 if (u == kUnits - 1 && lane == kLanes - 1) keep = tl3 ? (2u << (31 - __clz(tl3))) - 1u : 0u;
                 const uint32_t W4[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-                uint32_t cpv = cont_bytes(wps[u]);
+                uint32_t cpv = cont_flags(wps[u]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) cpv = place_sums(cpv, W4[j], nibble_to_bytes((keep >> (4 * j)) & 0xFu), a);
             }
@@ -272,7 +272,7 @@ __device__ __forceinline__ void count_wt(const Params &p, uint64_t t, int lane, 
                 const uint32_t head = tb ? 0xFu & ~((2u << (31 - __clz(tb))) - 1u) : 0xFu;
                 place_sums(0u, before, nibble_to_bytes(head), a);
             }
-            sum += a[0] + 127u * (a[1] + 128u * (a[2] + 128u * (a[3] + 128u * a[4])));
+            sum += a[0] + 127u * (a[1] + 16384u * a[2]);
         }
     }
     cnt_out = __reduce_add_sync(~0u, cnt);
